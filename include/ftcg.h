@@ -1,0 +1,194 @@
+/*
+ * ftcg.h -- C ABI of the GB300 (sm_103a) frame theoretic convolutional gridding library.
+ *
+ * The library computes the weighted 2-D adjoint non-uniform Fourier transform at the heart of
+ * frame theoretic convolutional gridding (FTCG, McKay, Gelb, Monga, Raj; Sec. IV, Eq. twodcg,
+ * twodcgmatrix and twodftcg at band r = 1):
+ *
+ *     I_p = sum_j alpha_j v_j exp(+2 pi i lambda_j . p / N),   p in {-N/2 .. N/2-1}^2,
+ *
+ * approximated by convolutional gridding: the weighted samples alpha_j v_j (D_2 f^) are spread
+ * with a width-w window onto a periodic sigma-oversampled G x G grid (Omega_2), G = sigma N,
+ * transformed by an unnormalised inverse 2-D FFT (the sum over l in I_L of exp(2 pi i <l, x>)),
+ * divided by the window's Fourier transform (zeta_n = psi_n / w(x), Eq. newadm) and cropped.
+ *
+ * Conventions shared by every call:
+ *   - lambda: M x 2 float64, interleaved (x, y), cycles per field of view; any real value (the
+ *     grid is periodic, lambda and lambda + N k give the same image).
+ *   - values v: M complex samples in acquisition order, complex64 (interleaved float re, im) or
+ *     bf16x2 (interleaved bfloat16 re, im).
+ *   - image: N x N complex64, row-major, element (p_y + N/2) * N + (p_x + N/2).
+ *   - fine grid: G x G complex64, row-major, element l_y * G + l_x, l in [0, G).
+ *   - the window is the exponential of semicircle (ES) kernel
+ *       phi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)), |t| <= w/2, beta = 0.97 pi (1 - 1/(2 sigma)) w;
+ *     taps are the w cells from ceil(sigma lambda - w/2) (mod G).
+ *   - every call that takes a stream is asynchronous on it unless stated; device pointers must
+ *     stay valid until the stream reaches the call. A plan is used by one stream at a time.
+ *   - no call throws, aborts or traps: errors are returned as ftcg_status_t and a thread-local
+ *     message (ftcg_last_error). Argument errors are detected before any device work is queued.
+ *     Device-side conditions (non-finite coordinates, non-positive weight sums) set a status
+ *     word that ftcg_check reads.
+ */
+#ifndef FTCG_H
+#define FTCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* ftcg_stream_t;
+typedef struct ftcg_plan_s* ftcg_plan_t;
+typedef struct ftcg_batch_s* ftcg_batch_t;
+
+typedef enum {
+    FTCG_SUCCESS = 0,
+    FTCG_ERR_INVALID_VALUE = 1,   /* a bad argument; nothing was queued                       */
+    FTCG_ERR_OUT_OF_MEMORY = 2,   /* a device or pinned-host allocation failed                 */
+    FTCG_ERR_CUDA = 3,            /* a CUDA runtime or cuFFT call failed (see ftcg_last_error) */
+    FTCG_ERR_NOT_SUPPORTED = 4,   /* valid but outside this build's limits                     */
+    FTCG_ERR_NUMERIC = 5,         /* non-finite coordinate or value, or a weight sum <= 0      */
+    FTCG_ERR_TIMEOUT = 6          /* a bounded device wait gave up                             */
+} ftcg_status_t;
+
+/* Value storage for ftcg_adjoint / ftcg_spread. */
+enum { FTCG_VALUES_C64 = 0, FTCG_VALUES_BF16X2 = 1 };
+/* Weight storage for ftcg_set_weights. */
+enum { FTCG_WEIGHTS_F64 = 0, FTCG_WEIGHTS_F32 = 1 };
+/* Plan precision: how the per-sample weight is stored next to the sorted coordinates. */
+enum { FTCG_PREC_FP32 = 0, FTCG_PREC_BF16 = 1 };
+
+typedef struct {
+    int32_t kernel;        /* 0 = ES (the only window of this build)                            */
+    int32_t precision;     /* FTCG_PREC_FP32 (default) or FTCG_PREC_BF16 weight storage        */
+    int32_t tile;          /* fine-grid tile side of the spreading kernel: 0 = auto, 32 or 64 */
+    int32_t weight_width;  /* window width of the FP64 weight construction: 0 = 12, else 4..16 */
+    int32_t reserved[4];   /* must be zero                                                      */
+} ftcg_opts_t;
+
+typedef struct {
+    int64_t M;             /* samples                                                           */
+    int32_t N, G, w, tile; /* image side, grid side, window width, tile side                    */
+    int32_t tiles_x;       /* tiles per grid row (tiles are tile x tile, the last one ragged)    */
+    int64_t entries;       /* (tile, sample) pairs after halo duplication                      */
+    double beta;           /* window shape parameter                                            */
+    int64_t device_bytes;  /* device memory the plan holds                                      */
+} ftcg_plan_info_t;
+
+/*
+ * ftcg_plan -- bin a geometry once (the sparsity of Omega_2, Eq. twodcgmatrix; taps
+ * ceil(sigma lambda - w/2) + {0..w-1}^2 mod G).
+ *   out      [out] receives the plan handle (owned by the caller, release with ftcg_destroy).
+ *   d_lambda device, M x 2 float64 (x, y) interleaved; read during the call, may be freed after.
+ *   M        0 .. 33,554,431 samples (M = 0 gives a plan whose images are zero).
+ *   N        even, >= 2.
+ *   sigma    >= 1; G = sigma N must be an even integer with G >= 2 w.
+ *   w        2 .. 16.
+ *   opts     nullable (NULL = defaults); reserved fields must be zero.
+ *   stream   stream for the planning kernels. This call synchronises the stream once (to size
+ *            the sorted entry array) and is not capturable; the calls that use the plan are.
+ * Errors: INVALID_VALUE for bad arguments; NOT_SUPPORTED for sizes beyond the limits above;
+ * NUMERIC if a coordinate is not finite (that sample is dropped and the plan is still returned);
+ * OUT_OF_MEMORY; CUDA.
+ */
+ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int32_t N,
+                        double sigma, int32_t w, const ftcg_opts_t* opts, ftcg_stream_t stream);
+
+/* Plan sizes; host call, no device work. */
+ftcg_status_t ftcg_plan_info(ftcg_plan_t plan, ftcg_plan_info_t* info);
+
+/*
+ * ftcg_weights -- the exact FTCG diagonal weights at band r = 1 (Eq. difopt, C_2 of Eq.
+ * twodftcg restricted to its diagonal): alpha_k = 1 / S_k with
+ *     S_k = sum_j F_N(lambda_jx - lambda_kx) F_N(lambda_jy - lambda_ky),
+ *     F_N(d) = sin^2(pi d) / (N^2 sin^2(pi d / N))   (normalised Fejer kernel),
+ * i.e. the column-wise least-squares optimum of || T D - I ||_F with T the data-frame Gram matrix
+ * on the N x N pixel lattice. Computed in FP64 on the device by the lag route: a gridded adjoint
+ * of unit strengths at 2 lambda on a 2N lattice, a product with c(d) = prod (N - |d_i|) / N^2, and
+ * a gridded forward transform at 2 lambda (window width opts.weight_width).
+ * The weights are installed in the plan (used by every later ftcg_adjoint) and, if d_alpha_out is
+ * not NULL, written there as M float64 in acquisition order. Temporary device memory (about
+ * 16 (2 sigma N)^2 bytes) is allocated and freed inside the call; the call synchronises.
+ * Errors: NUMERIC if some S_k <= 0 or is not finite (those weights are set to 0); CUDA; OOM.
+ */
+ftcg_status_t ftcg_weights(ftcg_plan_t plan, double* d_alpha_out, ftcg_stream_t stream);
+
+/*
+ * ftcg_set_weights -- install caller-supplied per-sample weights alpha (D_2 of Eq.
+ * twodcgmatrix), M entries in acquisition order, FTCG_WEIGHTS_F64 or FTCG_WEIGHTS_F32.
+ * Passing d_alpha = NULL restores alpha = 1 (plain gridding). Asynchronous.
+ */
+ftcg_status_t ftcg_set_weights(ftcg_plan_t plan, const void* d_alpha, int32_t dtype,
+                               ftcg_stream_t stream);
+
+/*
+ * ftcg_spread -- the spreading step alone: g = Omega_2 D_2 v on the G x G fine grid
+ * (Eq. twodcgmatrix), written to d_grid (G x G complex64, caller-owned, fully overwritten).
+ * d_values: M values in acquisition order, layout given by vdtype. Asynchronous.
+ */
+ftcg_status_t ftcg_spread(ftcg_plan_t plan, const void* d_values, int32_t vdtype, void* d_grid,
+                          ftcg_stream_t stream);
+
+/*
+ * ftcg_adjoint -- the full weighted adjoint (Eq. twodcg with D_2 = diag(alpha)): spread, inverse
+ * 2-D FFT of the plan's fine grid, division by phi^(p_x/G) phi^(p_y/G) (FP64 factors) and crop.
+ * d_image: N x N complex64, caller-owned, fully overwritten. Asynchronous and capturable.
+ */
+ftcg_status_t ftcg_adjoint(ftcg_plan_t plan, const void* d_values, int32_t vdtype, void* d_image,
+                           ftcg_stream_t stream);
+
+/*
+ * ftcg_adjoint_host -- ftcg_adjoint on HOST buffers: copies h_values to the device, runs the
+ * adjoint and copies the image back into h_image, all on `stream`, then synchronises it.
+ * Pinned host memory gives the fastest copies; pageable memory also works.
+ */
+ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t vdtype,
+                                void* h_image, ftcg_stream_t stream);
+
+/*
+ * ftcg_forward -- the gridded transpose of ftcg_adjoint without weights (the data frame of
+ * Eq. twoddataframe applied to an image): f_k ~= sum_p I_p exp(-2 pi i lambda_k . p / N).
+ * d_image: N x N complex64; d_values: M complex64 out, acquisition order. Asynchronous.
+ */
+ftcg_status_t ftcg_forward(ftcg_plan_t plan, const void* d_image, void* d_values,
+                           ftcg_stream_t stream);
+
+/* Synchronise the plan's last stream and report the device status word (NUMERIC if a
+ * non-finite coordinate or weight sum was seen), then clear it. */
+ftcg_status_t ftcg_check(ftcg_plan_t plan);
+
+/* Copy the plan's sorted (tile, sample) entries to host memory, for inspection and tests.
+ * h_tile, h_cx, h_cy: int32 tile index and local first-tap cell of each entry (cx, cy in
+ * [-(w-1), tile-1]); h_sample: int32 sample index; h_dx, h_dy: float32 offset of the sample from
+ * its first tap, sigma lambda - ceil(sigma lambda - w/2). Each array holds info.entries elements.
+ * Any pointer may be NULL. Synchronous. */
+ftcg_status_t ftcg_plan_entries(ftcg_plan_t plan, int32_t* h_tile, int32_t* h_cx, int32_t* h_cy,
+                                int32_t* h_sample, float* h_dx, float* h_dy);
+
+/*
+ * Stage profiling. With enable != 0, every later ftcg_adjoint records CUDA events on its stream
+ * around its three stages (spread, inverse FFT, window division + crop); ftcg_stage_times
+ * synchronises on the last recorded event and returns the mean duration in milliseconds of each
+ * stage (ms[0] spread, ms[1] FFT, ms[2] deapodise + crop) over the calls recorded since the
+ * previous read (count in *calls), then starts a new count. At most 1024 calls are recorded
+ * between reads; later ones are not timed.
+ */
+ftcg_status_t ftcg_profile(ftcg_plan_t plan, int32_t enable);
+ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls);
+
+/* Release a plan and all device memory it holds (synchronises). NULL is accepted. */
+ftcg_status_t ftcg_destroy(ftcg_plan_t plan);
+
+const char* ftcg_status_string(ftcg_status_t status);
+/* Detail of the last error on the calling thread ("" if none). */
+const char* ftcg_last_error(void);
+/* Library version string, e.g. "ftcg 0.1 sm_103a". */
+const char* ftcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTCG_H */

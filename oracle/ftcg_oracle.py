@@ -170,15 +170,13 @@ def spread(lam, c, N, sigma, w, kind=ES, beta=None):
     wy = tap_weights(u[:, 1], org[:, 1], w, beta, kind)
     c = np.asarray(c, np.complex128)
     grid = np.zeros(G * G, np.complex128)
-    for ty in range(w):
+    ix = np.mod(org[:, 0:1] + np.arange(w)[None, :], G)          # M x w columns of the taps
+    for ty in range(w):                                          # one row of taps at a time
         iy = np.mod(org[:, 1] + ty, G)
-        cy = c * wy[:, ty]
-        for tx in range(w):
-            ix = np.mod(org[:, 0] + tx, G)
-            idx = iy * G + ix
-            val = cy * wx[:, tx]
-            grid += np.bincount(idx, weights=val.real, minlength=G * G)
-            grid += 1j * np.bincount(idx, weights=val.imag, minlength=G * G)
+        idx = (iy[:, None] * G + ix).ravel()
+        val = ((c * wy[:, ty])[:, None] * wx).ravel()
+        grid += np.bincount(idx, weights=val.real, minlength=G * G)
+        grid += 1j * np.bincount(idx, weights=val.imag, minlength=G * G)
     return grid.reshape(G, G)
 
 
@@ -243,12 +241,14 @@ def adjoint_pixels(lam, c, N, sigma, w, pix, kind=ES, beta=None):
     wy = tap_weights(u[:, 1], org[:, 1], w, beta, kind)
     t = np.arange(w)
     c = np.asarray(c, np.complex128)
+    # the cell l = c_j + t: exp(2 pi i l p / G) = exp(2 pi i c_j p / G) exp(2 pi i t p / G), and
+    # the wrap l mod G does not change it (p and l are integers)
+    ox = np.mod(org[:, 0], G)
+    oy = np.mod(org[:, 1], G)
     out = np.empty(len(pix), np.complex128)
     for i, (px, py) in enumerate(np.asarray(pix)):
-        lx = np.mod(org[:, 0:1] + t[None, :], G)
-        ly = np.mod(org[:, 1:2] + t[None, :], G)
-        sx = np.sum(wx * np.exp(2j * np.pi * lx * px / G), axis=1)
-        sy = np.sum(wy * np.exp(2j * np.pi * ly * py / G), axis=1)
+        sx = (wx @ np.exp(2j * np.pi * t * px / G)) * np.exp(2j * np.pi * np.mod(ox * px, G) / G)
+        sy = (wy @ np.exp(2j * np.pi * t * py / G)) * np.exp(2j * np.pi * np.mod(oy * py, G) / G)
         den = phi_hat(px / G, w, beta, kind) * phi_hat(py / G, w, beta, kind)
         out[i] = np.sum(c * sx * sy) / den
     return out

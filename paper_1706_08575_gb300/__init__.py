@@ -1,0 +1,7 @@
+"""GB300-native frame theoretic convolutional gridding (weighted 2-D adjoint NUFFT).
+
+The compute lives in libftcg.so (C ABI, include/ftcg.h, CUDA kernels for sm_103a); this package
+only builds it and marshals arguments to it.
+"""
+from .ftcg import (BF16X2, C64, F32, F64, PREC_BF16, PREC_FP32, FtcgError, Plan,  # noqa: F401
+                   lib, lib_path)

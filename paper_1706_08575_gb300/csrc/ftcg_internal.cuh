@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of libftcg (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ftcg.h"
+
+namespace ftcg {
+
+// ---------------------------------------------------------------------------------------------
+// Errors: a thread-local message plus a status code; never exceptions across the ABI.
+// ---------------------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define FTCG_CK(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            ::ftcg::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                              __FILE__, __LINE__);                                          \
+            return e_ == cudaErrorMemoryAllocation ? FTCG_ERR_OUT_OF_MEMORY : FTCG_ERR_CUDA; \
+        }                                                                                   \
+    } while (0)
+
+#define FTCG_CKFFT(call)                                                                    \
+    do {                                                                                    \
+        cufftResult r_ = (call);                                                            \
+        if (r_ != CUFFT_SUCCESS) {                                                          \
+            ::ftcg::set_error("%s failed: cufft error %d (%s:%d)", #call, (int)r_, __FILE__,  \
+                              __LINE__);                                                    \
+            return r_ == CUFFT_ALLOC_FAILED ? FTCG_ERR_OUT_OF_MEMORY : FTCG_ERR_CUDA;       \
+        }                                                                                   \
+    } while (0)
+
+#define FTCG_TRY(expr)                                                                      \
+    do {                                                                                    \
+        ftcg_status_t s_ = (expr);                                                          \
+        if (s_ != FTCG_SUCCESS) return s_;                                                  \
+    } while (0)
+
+// Device status word bits (ftcg_check).
+enum : unsigned {
+    STATUS_NONFINITE_COORD = 1u,
+    STATUS_BAD_WEIGHT_SUM = 2u,
+};
+
+// Packed entry word: sample index in the low 25 bits, (cy + w - 1) in the high 7 bits.
+constexpr int kSampleBits = 25;
+constexpr uint32_t kSampleMask = (1u << kSampleBits) - 1u;
+constexpr int64_t kMaxSamples = (int64_t(1) << kSampleBits) - 1;
+
+// One sorted (tile, sample) entry of the spreading plan: 16 bytes, loaded with one LDG.128.
+//   dx, dy : sigma lambda - first tap, in (w/2 - 1, w/2]   (float32)
+//   alpha  : per-sample weight (float32, or bfloat16 in the low half for FTCG_PREC_BF16)
+//   packed : sample index | (cy_local + w - 1) << 25
+struct __align__(16) Entry {
+    float dx, dy;
+    uint32_t alpha;
+    uint32_t packed;
+};
+
+// The window: ES kernel parameters for one (w, sigma).
+struct Window {
+    int w;
+    double beta;
+};
+
+// A binning of samples into square tiles of a G x G periodic grid.
+struct Binning {
+    int G = 0, T = 0, W = 0;
+    int ntx = 0, ntiles = 0, ncb = 0;   // ncb = T + W - 1 column bins per tile
+    int64_t n_entries = 0;
+    Entry* ent = nullptr;               // n_entries, sorted by (tile, column bin, row)
+    int* colptr = nullptr;              // ntiles * ncb + 1 start offsets
+};
+
+struct Plan {
+    int64_t M = 0;
+    int N = 0, G = 0, w = 0;
+    double sigma = 0;
+    ftcg_opts_t opts{};
+    Window win{};
+    Binning bin;
+    double* lambda = nullptr;           // M x 2 copy (FP64), for the weight construction
+    int4* samp = nullptr;               // per sample: (cx mod G, cy mod G, float dx bits, dy bits)
+    double* deapod = nullptr;           // N factors 1 / phi^(p / G), p = -N/2 .. N/2-1
+    float2* grid = nullptr;             // G x G complex64 work grid
+    cufftHandle fft = 0;
+    bool fft_ok = false;
+    unsigned* status = nullptr;         // device status word
+    void* stage_vals = nullptr;         // ftcg_adjoint_host staging (device)
+    void* stage_img = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int64_t device_bytes = 0;
+    // stage profiling: 4 events per recorded adjoint call
+    bool profiling = false;
+    int prof_calls = 0;
+    cudaEvent_t* prof_ev = nullptr;     // kMaxProfiled * 4, created on first use
+};
+constexpr int kMaxProfiled = 1024;
+
+// ---------------------------------------------------------------------------------------------
+// Launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------------------
+// plan.cu
+ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, double scale,
+                            int G, int T, int W, unsigned* d_status, int4* d_samp,
+                            cudaStream_t s, int64_t* bytes);
+void free_binning(Binning& b);
+ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStream_t s);
+// spread.cu
+ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2* grid,
+                            cudaStream_t s);
+ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s);
+ftcg_status_t launch_pad_apod(const Plan& p, const float2* img, float2* grid, cudaStream_t s);
+ftcg_status_t launch_interp(const Plan& p, const float2* grid, float2* vals, cudaStream_t s);
+ftcg_status_t launch_set_alpha(const Plan& p, const void* alpha, int dtype, cudaStream_t s);
+// window.cu
+ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cudaStream_t s);
+double es_beta(int w, double sigma);
+// weights.cu
+ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s);
+
+}  // namespace ftcg

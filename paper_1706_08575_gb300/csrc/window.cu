@@ -1,0 +1,101 @@
+// The window and its Fourier transform, in FP64 on the device.
+//
+// Division by the window (zeta_n = psi_n / w(x), Eq. newadm) becomes, on the sigma-oversampled
+// grid, division by phi^(p / G) (the m = 0 term of the Poisson sum of Eq. twodcg):
+//     phi^(xi) = int phi(t) exp(-2 pi i xi t) dt = 2 int_0^{pi/2} phi(w/2 sin th) cos(pi w xi sin th)
+//                (w/2) cos th dth,
+// the substitution t = (w/2) sin th removing the square-root edge of the ES window. The integral
+// is taken by Gauss-Legendre quadrature whose nodes are computed here by Newton iteration on the
+// Legendre polynomial P_n (three-term recurrence), then the N reciprocals are evaluated in FP64.
+
+#include <cmath>
+#include <vector>
+
+#include "ftcg_internal.cuh"
+
+namespace ftcg {
+
+namespace {
+
+constexpr int kQuadNodes = 96;
+
+// Gauss-Legendre nodes and weights on [-1, 1].
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt) {
+    x.resize(n);
+    wt.resize(n);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            // p1 = P_n(z), p0 = P_{n-1}(z)
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        wt[i] = wt[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+struct Quad {
+    double th[kQuadNodes];   // angles in [0, pi/2]
+    double wt[kQuadNodes];   // weights including the dth Jacobian
+};
+
+__global__ void k_window_factors(double* __restrict__ out, int N, int G, int W, double beta,
+                                 Quad q) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double pi = 3.14159265358979323846;
+    double xi = (double)(i - N / 2) / (double)G;
+    double half = 0.5 * W;
+    double s = 0.0;
+    for (int k = 0; k < kQuadNodes; ++k) {
+        double sn, cs;
+        sincos(q.th[k], &sn, &cs);
+        double ph = exp(beta * (cs - 1.0));           // ES at t = (w/2) sin th
+        s += q.wt[k] * ph * cos(2.0 * pi * xi * half * sn) * half * cs;
+    }
+    out[i] = 1.0 / (2.0 * s);
+}
+
+}  // namespace
+
+double es_beta(int w, double sigma) {
+    const double pi = 3.14159265358979323846;
+    return 0.97 * pi * (1.0 - 0.5 / sigma) * w;
+}
+
+ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cudaStream_t s) {
+    std::vector<double> x, wt;
+    gauss_legendre(kQuadNodes, x, wt);
+    Quad q;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < kQuadNodes; ++k) {
+        q.th[k] = 0.25 * pi * (x[k] + 1.0);
+        q.wt[k] = 0.25 * pi * wt[k];
+    }
+    k_window_factors<<<(N + 127) / 128, 128, 0, s>>>(d_out, N, G, win.w, win.beta, q);
+    FTCG_CK(cudaGetLastError());
+    return FTCG_SUCCESS;
+}
+
+}  // namespace ftcg

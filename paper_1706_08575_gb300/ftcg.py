@@ -1,0 +1,232 @@
+"""Python binding of libftcg (argument marshalling only; every step runs in the CUDA library).
+
+PyTorch provides device memory and streams: inputs and outputs are torch tensors on a CUDA
+device, the calls are queued on torch's current stream. If the library is not built this module
+raises at import of the library, never falls back to a CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+C64, BF16X2 = 0, 1           # value storage
+F64, F32 = 0, 1              # weight storage
+PREC_FP32, PREC_BF16 = 0, 1  # plan precision
+
+_STATUS = {
+    0: "FTCG_SUCCESS", 1: "FTCG_ERR_INVALID_VALUE", 2: "FTCG_ERR_OUT_OF_MEMORY", 3: "FTCG_ERR_CUDA",
+    4: "FTCG_ERR_NOT_SUPPORTED", 5: "FTCG_ERR_NUMERIC", 6: "FTCG_ERR_TIMEOUT",
+}
+
+
+class FtcgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("weight_width", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int32), ("G", ctypes.c_int32),
+                ("w", ctypes.c_int32), ("tile", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
+                ("entries", ctypes.c_int64), ("beta", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point, mirroring include/ftcg.h.
+_VP, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+SIGNATURES = [
+    ("ftcg_plan", _I32, [ctypes.POINTER(_VP), _VP, _I64, _I32, _D, _I32, ctypes.POINTER(Opts), _VP]),
+    ("ftcg_plan_info", _I32, [_VP, ctypes.POINTER(PlanInfo)]),
+    ("ftcg_weights", _I32, [_VP, _VP, _VP]),
+    ("ftcg_set_weights", _I32, [_VP, _VP, _I32, _VP]),
+    ("ftcg_spread", _I32, [_VP, _VP, _I32, _VP, _VP]),
+    ("ftcg_adjoint", _I32, [_VP, _VP, _I32, _VP, _VP]),
+    ("ftcg_adjoint_host", _I32, [_VP, _VP, _I32, _VP, _VP]),
+    ("ftcg_forward", _I32, [_VP, _VP, _VP, _VP]),
+    ("ftcg_check", _I32, [_VP]),
+    ("ftcg_plan_entries", _I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ftcg_profile", _I32, [_VP, _I32]),
+    ("ftcg_stage_times", _I32, [_VP, _VP, _VP]),
+    ("ftcg_destroy", _I32, [_VP]),
+    ("ftcg_status_string", ctypes.c_char_p, [_I32]),
+    ("ftcg_last_error", ctypes.c_char_p, []),
+    ("ftcg_version", ctypes.c_char_p, []),
+]
+
+
+def lib_path():
+    return _build.LIB_PATH
+
+
+def lib():
+    """Load libftcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libftcg.so is not built ({path}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise FtcgError(status, lib().ftcg_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _values_dtype(v):
+    import torch
+    if v.dtype == torch.complex64:
+        return C64
+    if v.dtype == torch.bfloat16 and v.dim() == 2 and v.shape[1] == 2:
+        return BF16X2
+    raise TypeError("values must be complex64 (M,) or bfloat16 (M, 2)")
+
+
+class Plan:
+    """A binned geometry: ftcg_plan on lam (torch float64, M x 2, CUDA)."""
+
+    def __init__(self, lam, N, sigma=2.0, w=8, tile=0, precision=PREC_FP32, weight_width=0,
+                 stream=None, allow_numeric=False):
+        import torch
+        if lam.dtype != torch.float64 or lam.dim() != 2 or lam.shape[1] != 2 or not lam.is_cuda:
+            raise TypeError("lam must be a CUDA float64 tensor of shape (M, 2)")
+        lam = lam.contiguous()
+        self.M, self.N, self.sigma, self.w = int(lam.shape[0]), int(N), float(sigma), int(w)
+        self.device = lam.device
+        opts = Opts(0, precision, tile, weight_width)
+        h = ctypes.c_void_p()
+        st = lib().ftcg_plan(ctypes.byref(h), _ptr(lam), self.M, self.N, self.sigma, self.w,
+                             ctypes.byref(opts), _stream(stream))
+        self._h = h if h.value else None
+        if st == 5 and allow_numeric:
+            self.numeric_warning = lib().ftcg_last_error().decode()
+        else:
+            _check(st)
+        self.info = self.plan_info()
+        self.G = self.info.G
+
+    # --- plumbing -------------------------------------------------------------------------
+    def plan_info(self):
+        info = PlanInfo()
+        _check(lib().ftcg_plan_info(self._h, ctypes.byref(info)))
+        return info
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ftcg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- the operations --------------------------------------------------------------------
+    def weights(self, out=None, stream=None):
+        """Exact FTCG weights (FP64, acquisition order); also installed in the plan."""
+        import torch
+        if out is None:
+            out = torch.empty(self.M, dtype=torch.float64, device=self.device)
+        _check(lib().ftcg_weights(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def set_weights(self, alpha, stream=None):
+        import torch
+        if alpha is None:
+            _check(lib().ftcg_set_weights(self._h, None, F64, _stream(stream)))
+            return
+        dt = F64 if alpha.dtype == torch.float64 else F32
+        if alpha.dtype not in (torch.float64, torch.float32):
+            raise TypeError("alpha must be float64 or float32")
+        _check(lib().ftcg_set_weights(self._h, _ptr(alpha.contiguous()), dt, _stream(stream)))
+
+    def spread(self, values, out=None, stream=None):
+        import torch
+        vd = _values_dtype(values)
+        if out is None:
+            out = torch.empty((self.G, self.G), dtype=torch.complex64, device=self.device)
+        _check(lib().ftcg_spread(self._h, _ptr(values.contiguous()), vd, _ptr(out), _stream(stream)))
+        return out
+
+    def adjoint(self, values, out=None, stream=None):
+        import torch
+        vd = _values_dtype(values)
+        if out is None:
+            out = torch.empty((self.N, self.N), dtype=torch.complex64, device=self.device)
+        _check(lib().ftcg_adjoint(self._h, _ptr(values.contiguous()), vd, _ptr(out),
+                                  _stream(stream)))
+        return out
+
+    def adjoint_host(self, values_host, image_host, stream=None):
+        """values_host / image_host: torch CPU tensors (pinned for speed)."""
+        vd = _values_dtype(values_host)
+        _check(lib().ftcg_adjoint_host(self._h, _ptr(values_host), vd, _ptr(image_host),
+                                       _stream(stream)))
+        return image_host
+
+    def forward(self, image, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.M, dtype=torch.complex64, device=self.device)
+        _check(lib().ftcg_forward(self._h, _ptr(image.contiguous()), _ptr(out), _stream(stream)))
+        return out
+
+    def check(self):
+        _check(lib().ftcg_check(self._h))
+
+    def profile(self, enable=True):
+        _check(lib().ftcg_profile(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        """Mean (spread, fft, deapod) milliseconds over the adjoint calls since the last read."""
+        ms = (ctypes.c_float * 3)()
+        n = ctypes.c_int32()
+        _check(lib().ftcg_stage_times(self._h, ctypes.cast(ms, ctypes.c_void_p),
+                                      ctypes.byref(n)))
+        return tuple(ms), n.value
+
+    def entries(self):
+        n = int(self.info.entries)
+        arrs = {k: np.empty(n, np.int32) for k in ("tile", "cx", "cy", "sample")}
+        arrs["dx"] = np.empty(n, np.float32)
+        arrs["dy"] = np.empty(n, np.float32)
+        p = {k: arrs[k].ctypes.data_as(ctypes.c_void_p) for k in arrs}
+        _check(lib().ftcg_plan_entries(self._h, p["tile"], p["cx"], p["cy"], p["sample"],
+                                       p["dx"], p["dy"]))
+        return arrs

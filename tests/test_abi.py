@@ -1,0 +1,82 @@
+"""The C-ABI library loads, exports every symbol include/ftcg.h declares, and rejects bad
+arguments before touching the device (runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1706_08575_gb300 import build as b
+    b.build()
+    from paper_1706_08575_gb300 import ftcg
+    return ftcg.lib()
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "ftcg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ftcg_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(L):
+    syms = header_symbols()
+    assert "ftcg_adjoint" in syms and "ftcg_plan" in syms
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_1706_08575_gb300 import ftcg
+    bound = {n for n, _, _ in ftcg.SIGNATURES}
+    assert set(header_symbols()) <= bound
+
+
+def test_version_and_strings(L):
+    assert L.ftcg_version().startswith(b"ftcg")
+    assert L.ftcg_status_string(0) == b"FTCG_SUCCESS"
+    assert L.ftcg_status_string(5) == b"FTCG_ERR_NUMERIC"
+    assert L.ftcg_destroy(None) == 0
+
+
+def _plan(L, M=16, N=16, sigma=2.0, w=8, opts=None, lam=1, out=True):
+    from paper_1706_08575_gb300 import ftcg
+    h = ctypes.c_void_p()
+    o = ctypes.byref(opts) if opts is not None else None
+    return L.ftcg_plan(ctypes.byref(h) if out else None, ctypes.c_void_p(lam) if lam else None,
+                       M, N, sigma, w, o, None)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(N=15), 1), (dict(N=0), 1), (dict(w=1), 1), (dict(w=17), 1), (dict(sigma=0.5), 1),
+    (dict(sigma=1.3, N=16), 1),          # sigma N not an integer
+    (dict(sigma=1.0, N=6, w=4), 1),      # G < 2 w
+    (dict(M=-1), 1), (dict(lam=0), 1), (dict(out=False), 1),
+    (dict(M=1 << 25), 4),                # beyond the packed entry format
+    (dict(N=1 << 16, sigma=2.0), 4),     # G too large
+])
+def test_plan_rejects(L, kw, status):
+    assert _plan(L, **kw) == status
+    assert L.ftcg_last_error() != b""
+
+
+def test_plan_rejects_opts(L):
+    from paper_1706_08575_gb300 import ftcg
+    assert _plan(L, opts=ftcg.Opts(1, 0, 0, 0)) == 4                 # only the ES window
+    assert _plan(L, opts=ftcg.Opts(0, 2, 0, 0)) == 1                 # precision
+    assert _plan(L, opts=ftcg.Opts(0, 0, 48, 0)) == 1                # tile
+    assert _plan(L, opts=ftcg.Opts(0, 0, 0, 3)) == 1                 # weight width
+    o = ftcg.Opts(0, 0, 0, 0)
+    o.reserved[2] = 1
+    assert _plan(L, opts=o) == 1
+
+
+def test_null_plan_calls(L):
+    assert L.ftcg_adjoint(None, None, 0, None, None) == 1
+    assert L.ftcg_weights(None, None, None) == 1
+    assert L.ftcg_check(None) == 1
+    assert L.ftcg_plan_info(None, None) == 1

@@ -1,0 +1,201 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Bars (written here, derived from the arithmetic):
+  * images / grids in FP32 storage: rel-L2 <= 1e-5 against the FP64 oracle given the same inputs;
+  * weights (FP64 on the device): max relative error <= 1e-9 against the brute-force Fejer sum;
+  * plan entries (integer index work): bit-exact.
+"""
+import numpy as np
+import pytest
+
+import sasgen
+from oracle import ftcg_oracle as O
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def F():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1706_08575_gb300 as pkg
+    return pkg
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def c64(v):
+    return np.asarray(v).astype(np.complex64)
+
+
+def expected_entries(lam, N, sigma, w, T):
+    """(tile, cx, cy, sample, dx, dy) for every (tile, wrap copy) a footprint touches: a new run
+    of taps starts at tap 0, at a tile boundary and where the footprint wraps mod G."""
+    G = O.grid_side(N, sigma)
+    c, u = O.tap_origins(lam, N, sigma, w)
+    d = (u - c).astype(np.float32)
+    ntx = -(-G // T)
+    rows = []
+    for j in range(lam.shape[0]):
+        runs = []
+        for ax in (0, 1):
+            cw = int(c[j, ax] % G)
+            r = []
+            for t in range(w):
+                col = (cw + t) % G
+                if t == 0 or col % T == 0:
+                    tile = col // T
+                    r.append((tile, col - tile * T - t))
+            runs.append(r)
+        for ty, cyl in runs[1]:
+            for tx, cxl in runs[0]:
+                rows.append((ty * ntx + tx, cxl, cyl, j, d[j, 0], d[j, 1]))
+    return rows
+
+
+@pytest.mark.parametrize("N,sigma,w,T,spread", [
+    (64, 2.0, 6, 32, 64), (50, 2.0, 8, 32, 150), (40, 1.25, 5, 32, 40), (16, 2.0, 8, 64, 40),
+])
+def test_plan_entries_bit_exact(F, N, sigma, w, T, spread):
+    lam, _ = sasgen.random_case(3, 900, N, sigma, w, spread)
+    lam[:5] = np.array([[3.0, -2.5], [0.25, 7.0], [N / 2, -N / 2], [-N / 2, N / 2 - 1e-12],
+                        [0.0, 0.0]])          # ties and wrap edges
+    with F.Plan(dev(lam), N, sigma, w, tile=T) as p:
+        e = p.entries()
+        ncb = T + w - 1
+        key = (e["tile"].astype(np.int64) * ncb + e["cx"] + w - 1) * ncb + e["cy"] + w - 1
+        assert np.all(np.diff(key) >= 0), "entries not sorted by (tile, column, row)"
+        got = sorted(zip(e["tile"].tolist(), e["cx"].tolist(), e["cy"].tolist(),
+                         e["sample"].tolist(), e["dx"].tolist(), e["dy"].tolist()))
+        exp = sorted((a, b, c, d, float(x), float(y))
+                     for a, b, c, d, x, y in expected_entries(lam, N, sigma, w, T))
+        assert len(got) == len(exp)
+        assert got == exp
+
+
+def _run_adjoint(F, lam, v, N, sigma, w, alpha=None, T=0):
+    with F.Plan(dev(lam), N, sigma, w, tile=T) as p:
+        if alpha is not None:
+            p.set_weights(dev(alpha))
+        img = p.adjoint(dev(c64(v)))
+        grid = p.spread(dev(c64(v)))
+        p.check()
+        return img.cpu().numpy(), grid.cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,sigma,w,spread,T", [
+    (4096, 64, 2.0, 6, 150, 0), (3000, 50, 2.0, 8, 150, 32), (2000, 40, 1.25, 5, 40, 32),
+    (5000, 96, 2.0, 7, 96, 64), (3000, 40, 2.0, 10, 120, 32), (1500, 32, 2.0, 13, 32, 32),
+    (2500, 48, 1.5, 16, 60, 32), (3000, 64, 2.0, 4, 64, 64), (1, 32, 2.0, 8, 32, 0),
+])
+def test_adjoint_and_spread_vs_oracle(F, M, N, sigma, w, spread, T):
+    lam, v = sasgen.random_case(11 + M, M, N, sigma, w, spread)
+    alpha = np.random.default_rng(M).uniform(0.2, 2.0, M)
+    vc = c64(v).astype(np.complex128)
+    img, grid = _run_adjoint(F, lam, v, N, sigma, w, alpha, T)
+    ref = O.adjoint(lam, alpha.astype(np.float32) * vc, N, sigma, w)
+    assert O.rel_l2(img, ref) < TOL
+    gref = O.spread(lam, alpha.astype(np.float32) * vc, N, sigma, w)
+    assert O.rel_l2(grid, gref) < TOL
+
+
+def test_tiny_config(F):
+    """The 4096-sample polar raster: weights, weighted image vs O2 and vs the direct sum."""
+    p = sasgen.tiny()
+    v = sasgen.values_for(p)
+    with F.Plan(dev(p.lam), p.N, p.sigma, p.w) as pl:
+        a = pl.weights().cpu().numpy()
+        img = pl.adjoint(dev(c64(v))).cpu().numpy()
+        pl.check()
+    ab, _ = O.weights_brute(p.lam, p.N)
+    assert np.max(np.abs(a - ab) / ab) < 1e-9
+    vc = c64(v).astype(np.complex128)
+    ref = O.adjoint(p.lam, ab * vc, p.N, p.sigma, p.w)
+    assert O.rel_l2(img, ref) < TOL
+    direct = O.direct_adjoint(p.lam, ab * vc, p.N)
+    assert O.rel_l2(img, direct) < 1.2e-5 + TOL    # the w = 6 window's own bound plus FP32
+
+
+def test_empty_plan(F):
+    import torch
+    lam = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+    with F.Plan(lam, 32, 2.0, 8) as p:
+        v = torch.zeros(0, dtype=torch.complex64, device="cuda")
+        img = p.adjoint(v)
+        assert torch.count_nonzero(img).item() == 0
+        p.weights()
+        p.check()
+
+
+def test_collisions_one_cell(F):
+    """Every sample in the same cell: maximal shared-atomic contention."""
+    rng = np.random.default_rng(4)
+    M, N = 3000, 32
+    lam = np.tile([[1.3, -2.7]], (M, 1)) + 1e-3 * rng.random((M, 2))
+    v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    img, _ = _run_adjoint(F, lam, v, N, 2.0, 8)
+    ref = O.adjoint(lam, c64(v).astype(np.complex128), N, 2.0, 8)
+    assert O.rel_l2(img, ref) < TOL
+
+
+def test_forward_and_adjointness(F):
+    lam, c = sasgen.random_case(21, 3000, 48, spread=100)
+    rng = np.random.default_rng(22)
+    img = (rng.standard_normal((48, 48)) + 1j * rng.standard_normal((48, 48))).astype(np.complex64)
+    with F.Plan(dev(lam), 48, 2.0, 8) as p:
+        f = p.forward(dev(img)).cpu().numpy()
+        a = p.adjoint(dev(c64(c))).cpu().numpy()
+    ref = O.forward(lam, img.astype(np.complex128), 48, 2.0, 8)
+    assert O.rel_l2(f, ref) < TOL
+    lhs = np.vdot(img.astype(np.complex128), a.astype(np.complex128))
+    rhs = np.vdot(f.astype(np.complex128), c64(c).astype(np.complex128))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_weights_random(F):
+    lam, _ = sasgen.random_case(31, 3000, 40, spread=30)
+    with F.Plan(dev(lam), 40, 2.0, 8) as p:
+        a = p.weights().cpu().numpy()
+    ab, _ = O.weights_brute(lam, 40)
+    assert np.max(np.abs(a - ab) / ab) < 1e-9
+
+
+def test_weights_uniform_grid(F):
+    N = 32
+    g = np.arange(-N // 2, N // 2)
+    X, Y = np.meshgrid(g, g)
+    lam = np.stack([X.ravel(), Y.ravel()], 1).astype(np.float64)
+    with F.Plan(dev(lam), N, 2.0, 8) as p:
+        a = p.weights().cpu().numpy()
+    assert np.max(np.abs(a - 1.0)) < 1e-9
+
+
+def test_nonfinite_coordinate_reported(F):
+    from paper_1706_08575_gb300 import FtcgError
+    lam, v = sasgen.random_case(41, 100, 32)
+    lam[7, 0] = np.nan
+    with pytest.raises(FtcgError) as ei:
+        F.Plan(dev(lam), 32, 2.0, 8)
+    assert ei.value.status == 5
+    p = F.Plan(dev(lam), 32, 2.0, 8, allow_numeric=True)
+    img = p.adjoint(dev(c64(v))).cpu().numpy()
+    keep = np.ones(100, bool)
+    keep[7] = False
+    ref = O.adjoint(lam[keep], c64(v[keep]).astype(np.complex128), 32, 2.0, 8)
+    assert O.rel_l2(img, ref) < TOL
+    p.close()
+
+
+def test_adjoint_host_matches_device(F):
+    import torch
+    lam, v = sasgen.random_case(51, 2000, 64, spread=64)
+    with F.Plan(dev(lam), 64, 2.0, 8) as p:
+        a = p.adjoint(dev(c64(v))).cpu()
+        hv = torch.from_numpy(c64(v)).pin_memory()
+        himg = torch.empty((64, 64), dtype=torch.complex64).pin_memory()
+        p.adjoint_host(hv, himg)
+    assert O.rel_l2(himg.numpy(), a.numpy()) < 1e-6   # same kernels; atomics order may differ
