@@ -22,6 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # fast single-precision exp/sqrt; FP64 code (weights, window transform, planning) is unaffected.
 EXTRA = {
     "spread.cu": ["--use_fast_math"],
+    "batch.cu": ["--use_fast_math"],
 }
 
 

@@ -37,7 +37,11 @@ ftcg_status_t invalid(const char* msg) {
 
 int auto_tile(int G) { return G <= 512 ? 32 : 64; }
 
-void release(Plan* p) {
+}  // namespace
+
+namespace ftcg {
+
+void release_plan(Plan* p) {
     if (!p) return;
     cudaDeviceSynchronize();
     free_binning(p->bin);
@@ -56,7 +60,7 @@ void release(Plan* p) {
     delete p;
 }
 
-ftcg_status_t plan_impl(Plan* p, const double* d_lambda, cudaStream_t s) {
+ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool own_grid) {
     int64_t bytes = 0;
     const int64_t M = p->M;
     FTCG_CK(cudaMalloc(&p->status, sizeof(unsigned)));
@@ -69,16 +73,19 @@ ftcg_status_t plan_impl(Plan* p, const double* d_lambda, cudaStream_t s) {
         bytes += (int64_t)M * (2 * sizeof(double) + sizeof(int4));
     }
     FTCG_CK(cudaMalloc(&p->deapod, (size_t)p->N * sizeof(double)));
-    FTCG_CK(cudaMalloc(&p->grid, (size_t)p->G * p->G * sizeof(float2)));
-    bytes += (int64_t)p->N * sizeof(double) + (int64_t)p->G * p->G * sizeof(float2);
+    bytes += (int64_t)p->N * sizeof(double);
     FTCG_TRY(window_factors(p->deapod, p->N, p->G, p->win, s));
     FTCG_TRY(build_binning(p->bin, p->lambda, M, p->sigma, p->G, p->opts.tile, p->w, p->status,
                            p->samp, s, &bytes));
-    FTCG_CKFFT(cufftPlan2d(&p->fft, p->G, p->G, CUFFT_C2C));
-    p->fft_ok = true;
-    size_t ws = 0;
-    cufftGetSize(p->fft, &ws);
-    bytes += (int64_t)ws;
+    if (own_grid) {
+        FTCG_CK(cudaMalloc(&p->grid, (size_t)p->G * p->G * sizeof(float2)));
+        bytes += (int64_t)p->G * p->G * sizeof(float2);
+        FTCG_CKFFT(cufftPlan2d(&p->fft, p->G, p->G, CUFFT_C2C));
+        p->fft_ok = true;
+        size_t ws = 0;
+        cufftGetSize(p->fft, &ws);
+        bytes += (int64_t)ws;
+    }
     p->device_bytes = bytes;
     unsigned st = 0;
     FTCG_CK(cudaMemcpyAsync(&st, p->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -91,6 +98,50 @@ ftcg_status_t plan_impl(Plan* p, const double* d_lambda, cudaStream_t s) {
     }
     return FTCG_SUCCESS;
 }
+
+ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, ftcg_opts_t* po) {
+    if (M < 0) return invalid("ftcg_plan: M < 0");
+    if (N < 2 || (N & 1)) return invalid("ftcg_plan: N must be even and >= 2");
+    if (!(sigma >= 1.0) || !std::isfinite(sigma)) return invalid("ftcg_plan: sigma must be >= 1");
+    if (w < 2 || w > 16) return invalid("ftcg_plan: w must be in 2..16");
+    const double Gd = sigma * N;
+    const long long G = std::llround(Gd);
+    if (std::fabs(Gd - (double)G) > 1e-9 * Gd || (G & 1))
+        return invalid("ftcg_plan: sigma * N must be an even integer");
+    if (G < 2 * w) return invalid("ftcg_plan: the grid must hold at least two windows (G >= 2 w)");
+    ftcg_opts_t& o = *po;
+    for (int i = 0; i < 4; ++i)
+        if (o.reserved[i] != 0) return invalid("ftcg_plan: opts.reserved must be zero");
+    if (o.kernel != 0) {
+        set_error("ftcg_plan: only the ES window (kernel 0) is built");
+        return FTCG_ERR_NOT_SUPPORTED;
+    }
+    if (o.precision != FTCG_PREC_FP32 && o.precision != FTCG_PREC_BF16)
+        return invalid("ftcg_plan: opts.precision must be 0 (FP32) or 1 (BF16)");
+    if (o.tile == 0) o.tile = auto_tile((int)G);
+    if (o.tile != 32 && o.tile != 64) return invalid("ftcg_plan: opts.tile must be 0, 32 or 64");
+    if (o.weight_width != 0 && (o.weight_width < 4 || o.weight_width > 16))
+        return invalid("ftcg_plan: opts.weight_width must be 0 or 4..16");
+    if (M > kMaxSamples) {
+        set_error("ftcg_plan: M > %lld is beyond this build's entry format", (long long)kMaxSamples);
+        return FTCG_ERR_NOT_SUPPORTED;
+    }
+    if (G > 65536) {
+        set_error("ftcg_plan: G = sigma N > 65536 is not supported");
+        return FTCG_ERR_NOT_SUPPORTED;
+    }
+    const long long ntx = (G + o.tile - 1) / o.tile;
+    const long long ncb = o.tile + w - 1;
+    if (ntx * ntx * ncb * ncb >= (1LL << 31)) {
+        set_error("ftcg_plan: the binning key space is too large for G = %lld", G);
+        return FTCG_ERR_NOT_SUPPORTED;
+    }
+    return FTCG_SUCCESS;
+}
+
+}  // namespace ftcg
+
+namespace {
 
 ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* img, cudaStream_t s) {
     p->last_stream = s;
@@ -129,46 +180,11 @@ ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int
     clear_error();
     if (!out) return invalid("ftcg_plan: out is NULL");
     *out = nullptr;
-    if (M < 0) return invalid("ftcg_plan: M < 0");
     if (M > 0 && !d_lambda) return invalid("ftcg_plan: d_lambda is NULL");
-    if (N < 2 || (N & 1)) return invalid("ftcg_plan: N must be even and >= 2");
-    if (!(sigma >= 1.0) || !std::isfinite(sigma)) return invalid("ftcg_plan: sigma must be >= 1");
-    if (w < 2 || w > 16) return invalid("ftcg_plan: w must be in 2..16");
-    const double Gd = sigma * N;
-    const long long G = std::llround(Gd);
-    if (std::fabs(Gd - (double)G) > 1e-9 * Gd || (G & 1))
-        return invalid("ftcg_plan: sigma * N must be an even integer");
-    if (G < 2 * w) return invalid("ftcg_plan: the grid must hold at least two windows (G >= 2 w)");
     ftcg_opts_t o{};
     if (opts) o = *opts;
-    for (int i = 0; i < 4; ++i)
-        if (o.reserved[i] != 0) return invalid("ftcg_plan: opts.reserved must be zero");
-    if (o.kernel != 0) {
-        set_error("ftcg_plan: only the ES window (kernel 0) is built");
-        return FTCG_ERR_NOT_SUPPORTED;
-    }
-    if (o.precision != FTCG_PREC_FP32 && o.precision != FTCG_PREC_BF16)
-        return invalid("ftcg_plan: opts.precision must be 0 (FP32) or 1 (BF16)");
-    if (o.tile == 0) o.tile = auto_tile((int)G);
-    if (o.tile != 32 && o.tile != 64) return invalid("ftcg_plan: opts.tile must be 0, 32 or 64");
-    if (o.weight_width != 0 && (o.weight_width < 4 || o.weight_width > 16))
-        return invalid("ftcg_plan: opts.weight_width must be 0 or 4..16");
-    if (M > kMaxSamples) {
-        set_error("ftcg_plan: M > %lld is beyond this build's entry format", (long long)kMaxSamples);
-        return FTCG_ERR_NOT_SUPPORTED;
-    }
-    if (G > 65536) {
-        set_error("ftcg_plan: G = sigma N > 65536 is not supported");
-        return FTCG_ERR_NOT_SUPPORTED;
-    }
-    {
-        const long long ntx = (G + o.tile - 1) / o.tile;
-        const long long ncb = o.tile + w - 1;
-        if (ntx * ntx * ncb * ncb >= (1LL << 31)) {
-            set_error("ftcg_plan: the binning key space is too large for G = %lld", G);
-            return FTCG_ERR_NOT_SUPPORTED;
-        }
-    }
+    FTCG_TRY(validate_plan_args(M, N, sigma, w, &o));
+    const long long G = std::llround(sigma * N);
     Plan* p = new (std::nothrow) Plan();
     if (!p) {
         set_error("ftcg_plan: host allocation failed");
@@ -183,9 +199,9 @@ ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int
     p->win = Window{w, es_beta(w, sigma)};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
-    ftcg_status_t st = plan_impl(p, d_lambda, s);
+    ftcg_status_t st = make_plan(p, d_lambda, s, true);
     if (st != FTCG_SUCCESS && st != FTCG_ERR_NUMERIC) {
-        release(p);
+        release_plan(p);
         return st;
     }
     *out = reinterpret_cast<ftcg_plan_t>(p);
@@ -396,7 +412,7 @@ ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls) {
 
 ftcg_status_t ftcg_destroy(ftcg_plan_t plan) {
     clear_error();
-    release(reinterpret_cast<Plan*>(plan));
+    release_plan(reinterpret_cast<Plan*>(plan));
     return FTCG_SUCCESS;
 }
 

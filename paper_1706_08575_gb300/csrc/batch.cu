@@ -1,0 +1,557 @@
+// Batched pings: many independent geometries, sample counts and image sides gridded together.
+//
+// Each ping keeps its own binning (plan.cu) and window factors. One persistent spreading launch
+// covers every (ping, tile) work item: CTAs (one per resident slot of the GPU) take items from an
+// atomic counter, heaviest items first, and run the same tile body as the single-ping kernel.
+// The fine grids of pings with the same side G are contiguous, so one batched cuFFT per distinct
+// G follows, then one window-division + crop launch for all pings. The whole sequence is
+// stream-ordered with no host synchronisation and can be captured once in a CUDA graph.
+//
+// The tile side of each ping is chosen by a small autotuner: for every (G, w, precision,
+// half-octave bucket of samples per cell) it times both tile sides on the first ping that needs
+// it and keeps the faster for the life of the process.
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "spread_tile.cuh"
+
+namespace ftcg {
+
+namespace {
+
+struct PingDesc {
+    const Entry* ent;
+    const int* colptr;
+    const void* vals;
+    float2* grid;
+    float2* img;
+    const double* deapod;
+    int G, ntx, T, N;
+};
+
+template <int GW, int WT, bool VBF, bool ABF>
+__global__ void __launch_bounds__(tile::kSpreadThreads)
+    k_spread_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items, int nitems,
+                   int* __restrict__ counter, int Wrt, float beta, float inv_hw) {
+    extern __shared__ float smem[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();   // the previous item's tile is stored and s_item consumed
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) return;
+        const int2 pt = items[it];
+        const PingDesc d = desc[pt.x];
+        if (d.T == 64)
+            tile::spread_tile<GW, WT, 64, VBF, ABF>(d.ent, d.colptr, d.vals, d.grid, d.G, d.ntx,
+                                                    Wrt, beta, inv_hw, pt.y, smem);
+        else
+            tile::spread_tile<GW, WT, 32, VBF, ABF>(d.ent, d.colptr, d.vals, d.grid, d.G, d.ntx,
+                                                    Wrt, beta, inv_hw, pt.y, smem);
+    }
+}
+
+__global__ void k_deapod_batch(const PingDesc* __restrict__ desc) {
+    const PingDesc d = desc[blockIdx.y];
+    const int N = d.N, G = d.G;
+    const int64_t total = (int64_t)N * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int iy = (int)(i / N), ix = (int)(i - (int64_t)iy * N);
+        int qy = iy - N / 2, qx = ix - N / 2;
+        if (qy < 0) qy += G;
+        if (qx < 0) qx += G;
+        const float2 h = d.grid[(int64_t)qy * G + qx];
+        const double f = d.deapod[iy] * d.deapod[ix];
+        d.img[i] = make_float2((float)((double)h.x * f), (float)((double)h.y * f));
+    }
+}
+
+size_t spread_smem(int T, int W) {
+    return (size_t)(2 * T * (T + 1)) * sizeof(float) + (size_t)(T + W) * sizeof(int);
+}
+
+// ---- autotuner ----------------------------------------------------------------------------
+struct TuneKey {
+    int G, w, prec, bucket;
+    bool operator<(const TuneKey& o) const {
+        if (G != o.G) return G < o.G;
+        if (w != o.w) return w < o.w;
+        if (prec != o.prec) return prec < o.prec;
+        return bucket < o.bucket;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+int density_bucket(int64_t M, int G) {
+    const double d = (double)M / ((double)G * G);
+    return d <= 0 ? -100 : (int)std::lround(2.0 * std::log2(d));
+}
+
+// Time the spreading kernel of a plan (values are irrelevant to the cost: zeros).
+ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaStream_t s,
+                          float* ms) {
+    cudaEvent_t a, b;
+    FTCG_CK(cudaEventCreate(&a));
+    FTCG_CK(cudaEventCreate(&b));
+    FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s));   // warm-up
+    FTCG_CK(cudaEventRecord(a, s));
+    for (int r = 0; r < 3; ++r) FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s));
+    FTCG_CK(cudaEventRecord(b, s));
+    FTCG_CK(cudaEventSynchronize(b));
+    FTCG_CK(cudaEventElapsedTime(ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
+                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out) {
+    const int G = (int)std::llround(sigma * N);
+    const TuneKey key{G, w, opts.precision, density_bucket(M, G)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *T_out = it->second;
+            return FTCG_SUCCESS;
+        }
+    }
+    void* zeros = nullptr;
+    float2* grid = nullptr;
+    FTCG_CK(cudaMalloc(&zeros, (size_t)std::max<int64_t>(M, 1) * sizeof(float2)));
+    FTCG_CK(cudaMemsetAsync(zeros, 0, (size_t)std::max<int64_t>(M, 1) * sizeof(float2), s));
+    FTCG_CK(cudaMalloc(&grid, (size_t)G * G * sizeof(float2)));
+    int best = 64;
+    float best_ms = 1e30f;
+    ftcg_status_t st = FTCG_SUCCESS;
+    for (int T : {32, 64}) {
+        Plan* p = new (std::nothrow) Plan();
+        if (!p) { st = FTCG_ERR_OUT_OF_MEMORY; break; }
+        p->M = M; p->N = N; p->G = G; p->w = w; p->sigma = sigma;
+        p->opts = opts;
+        p->opts.tile = T;
+        p->win = Window{w, es_beta(w, sigma)};
+        st = make_plan(p, d_lambda, s, false);
+        float ms = 1e30f;
+        if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC) st = time_spread(*p, zeros, grid, s, &ms);
+        release_plan(p);
+        if (st != FTCG_SUCCESS) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = T;
+        }
+    }
+    cudaFree(zeros);
+    cudaFree(grid);
+    if (st != FTCG_SUCCESS) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best;
+    }
+    *T_out = best;
+    return FTCG_SUCCESS;
+}
+
+struct Batch {
+    int n = 0, w = 0;
+    double sigma = 0;
+    ftcg_opts_t opts{};
+    std::vector<Plan*> pings;
+    struct Class {
+        int G = 0, count = 0;
+        float2* grids = nullptr;
+        cufftHandle fft = 0;
+        bool fft_ok = false;
+    };
+    std::vector<Class> classes;
+    std::vector<int> cls_of, slot_of;
+    PingDesc* h_desc = nullptr;   // pinned
+    PingDesc* d_desc = nullptr;
+    int2* d_items = nullptr;
+    int nitems = 0;
+    int* d_counter = nullptr;
+    int max_N = 0;
+    int persistent_ctas = 0;
+    int64_t entries = 0, device_bytes = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t last = nullptr;
+};
+
+void release_batch(Batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    for (Plan* p : b->pings) release_plan(p);
+    for (auto& c : b->classes) {
+        if (c.grids) cudaFree(c.grids);
+        if (c.fft_ok) cufftDestroy(c.fft);
+    }
+    if (b->h_desc) cudaFreeHost(b->h_desc);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_counter) cudaFree(b->d_counter);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    delete b;
+}
+
+template <int GW, int WT, bool VBF, bool ABF>
+ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
+    auto kern = k_spread_batch<GW, WT, VBF, ABF>;
+    const size_t smem = spread_smem(64, b.w);
+    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (b.persistent_ctas == 0) {
+        int dev = 0, sms = 0, per = 0;
+        FTCG_CK(cudaGetDevice(&dev));
+        FTCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FTCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, tile::kSpreadThreads,
+                                                              smem));
+        b.persistent_ctas = std::max(1, sms * std::max(1, per));
+    }
+    const float beta = (float)es_beta(b.w, b.sigma);
+    const float inv_hw = (float)(2.0 / b.w);
+    kern<<<b.persistent_ctas, tile::kSpreadThreads, smem, s>>>(b.d_desc, b.d_items, b.nitems,
+                                                                b.d_counter, b.w, beta, inv_hw);
+    FTCG_CK(cudaGetLastError());
+    return FTCG_SUCCESS;
+}
+
+template <bool VBF, bool ABF>
+ftcg_status_t launch_batch_spread_w(Batch& b, cudaStream_t s) {
+    switch (b.w) {
+        case 6: return launch_batch_spread_t<8, 6, VBF, ABF>(b, s);
+        case 8: return launch_batch_spread_t<8, 8, VBF, ABF>(b, s);
+        default:
+            if (b.w <= 4) return launch_batch_spread_t<4, 0, VBF, ABF>(b, s);
+            if (b.w <= 8) return launch_batch_spread_t<8, 0, VBF, ABF>(b, s);
+            return launch_batch_spread_t<16, 0, VBF, ABF>(b, s);
+    }
+}
+
+ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, void* const* imgs,
+                            cudaStream_t s) {
+    for (int i = 0; i < b.n; ++i) {
+        b.h_desc[i].vals = vals[i];
+        b.h_desc[i].img = reinterpret_cast<float2*>(imgs[i]);
+    }
+    FTCG_CK(cudaMemcpyAsync(b.d_desc, b.h_desc, b.n * sizeof(PingDesc), cudaMemcpyHostToDevice, s));
+    FTCG_CK(cudaMemsetAsync(b.d_counter, 0, sizeof(int), s));
+    const bool vbf = vdtype == FTCG_VALUES_BF16X2;
+    const bool abf = b.opts.precision == FTCG_PREC_BF16;
+    if (b.nitems > 0) {
+        if (vbf && abf) FTCG_TRY((launch_batch_spread_w<true, true>(b, s)));
+        else if (vbf) FTCG_TRY((launch_batch_spread_w<true, false>(b, s)));
+        else if (abf) FTCG_TRY((launch_batch_spread_w<false, true>(b, s)));
+        else FTCG_TRY((launch_batch_spread_w<false, false>(b, s)));
+    }
+    for (auto& c : b.classes) {
+        FTCG_CKFFT(cufftSetStream(c.fft, s));
+        FTCG_CKFFT(cufftExecC2C(c.fft, reinterpret_cast<cufftComplex*>(c.grids),
+                                reinterpret_cast<cufftComplex*>(c.grids), CUFFT_INVERSE));
+    }
+    const int64_t maxpix = (int64_t)b.max_N * b.max_N;
+    const unsigned bx = (unsigned)std::min<int64_t>(std::max<int64_t>((maxpix + 255) / 256, 1), 64);
+    k_deapod_batch<<<dim3(bx, b.n), 256, 0, s>>>(b.d_desc);
+    FTCG_CK(cudaGetLastError());
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int64_t* M,
+                              const int32_t* N, cudaStream_t s) {
+    // per-ping plans (tile side autotuned unless given)
+    std::vector<int> Gs(b.n);
+    for (int i = 0; i < b.n; ++i) {
+        const int G = (int)std::llround(b.sigma * N[i]);
+        Gs[i] = G;
+        int T = b.opts.tile;
+        if (T == 0) FTCG_TRY(tune_tile(d_lambda[i], M[i], N[i], b.sigma, b.w, b.opts, s, &T));
+        Plan* p = new (std::nothrow) Plan();
+        if (!p) {
+            set_error("ftcg_plan_batch: host allocation failed");
+            return FTCG_ERR_OUT_OF_MEMORY;
+        }
+        p->M = M[i]; p->N = N[i]; p->G = G; p->w = b.w; p->sigma = b.sigma;
+        p->opts = b.opts;
+        p->opts.tile = T;
+        p->win = Window{b.w, es_beta(b.w, b.sigma)};
+        b.pings.push_back(p);
+        ftcg_status_t st = make_plan(p, d_lambda[i], s, false);
+        if (st != FTCG_SUCCESS && st != FTCG_ERR_NUMERIC) return st;
+        b.entries += p->bin.n_entries;
+        b.device_bytes += p->device_bytes;
+        b.max_N = std::max(b.max_N, N[i]);
+    }
+    // size classes: contiguous grids and one batched FFT per distinct G
+    std::vector<int> uniq(Gs);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    b.classes.resize(uniq.size());
+    b.cls_of.resize(b.n);
+    b.slot_of.resize(b.n);
+    for (size_t c = 0; c < uniq.size(); ++c) b.classes[c].G = uniq[c];
+    for (int i = 0; i < b.n; ++i) {
+        const int c = (int)(std::lower_bound(uniq.begin(), uniq.end(), Gs[i]) - uniq.begin());
+        b.cls_of[i] = c;
+        b.slot_of[i] = b.classes[c].count++;
+    }
+    for (auto& c : b.classes) {
+        const size_t per = (size_t)c.G * c.G;
+        FTCG_CK(cudaMalloc(&c.grids, per * c.count * sizeof(float2)));
+        b.device_bytes += (int64_t)(per * c.count * sizeof(float2));
+        int dims[2] = {c.G, c.G};
+        FTCG_CKFFT(cufftPlanMany(&c.fft, 2, dims, nullptr, 1, (int)per, nullptr, 1, (int)per,
+                                 CUFFT_C2C, c.count));
+        c.fft_ok = true;
+        size_t ws = 0;
+        cufftGetSize(c.fft, &ws);
+        b.device_bytes += (int64_t)ws;
+    }
+    // descriptors and the heaviest-first work list over (ping, tile)
+    FTCG_CK(cudaMallocHost(&b.h_desc, b.n * sizeof(PingDesc)));
+    FTCG_CK(cudaMalloc(&b.d_desc, b.n * sizeof(PingDesc)));
+    struct Item {
+        int cnt, ping, tile;
+    };
+    std::vector<Item> items;
+    for (int i = 0; i < b.n; ++i) {
+        Plan* p = b.pings[i];
+        const Binning& bn = p->bin;
+        auto& c = b.classes[b.cls_of[i]];
+        PingDesc& d = b.h_desc[i];
+        d.ent = bn.ent;
+        d.colptr = bn.colptr;
+        d.vals = nullptr;
+        d.grid = c.grids + (size_t)b.slot_of[i] * c.G * c.G;
+        d.img = nullptr;
+        d.deapod = p->deapod;
+        d.G = p->G;
+        d.ntx = bn.ntx;
+        d.T = bn.T;
+        d.N = p->N;
+        std::vector<int> cp((size_t)bn.ntiles * bn.ncb + 1);
+        FTCG_CK(cudaMemcpy(cp.data(), bn.colptr, cp.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int t = 0; t < bn.ntiles; ++t)
+            items.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const Item& x, const Item& y) { return x.cnt > y.cnt; });
+    b.nitems = (int)items.size();
+    std::vector<int2> it2(items.size());
+    for (size_t k = 0; k < items.size(); ++k) it2[k] = make_int2(items[k].ping, items[k].tile);
+    FTCG_CK(cudaMalloc(&b.d_items, std::max<size_t>(1, it2.size()) * sizeof(int2)));
+    if (!it2.empty())
+        FTCG_CK(cudaMemcpy(b.d_items, it2.data(), it2.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    FTCG_CK(cudaMalloc(&b.d_counter, sizeof(int)));
+    b.device_bytes += (int64_t)(it2.size() * sizeof(int2) + b.n * sizeof(PingDesc));
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t check_ptr_array(const void* const* a, int n, const char* what) {
+    if (!a) {
+        set_error("%s: pointer array is NULL", what);
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!a[i]) {
+            set_error("%s: pointer %d is NULL", what, i);
+            return FTCG_ERR_INVALID_VALUE;
+        }
+    return FTCG_SUCCESS;
+}
+
+}  // namespace
+}  // namespace ftcg
+
+using namespace ftcg;
+
+extern "C" {
+
+ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const* d_lambda,
+                              const int64_t* M, const int32_t* N, double sigma, int32_t w,
+                              const ftcg_opts_t* opts, ftcg_stream_t stream) {
+    clear_error();
+    if (!out) {
+        set_error("ftcg_plan_batch: out is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    *out = nullptr;
+    if (n < 1 || !d_lambda || !M || !N) {
+        set_error("ftcg_plan_batch: n >= 1 and non-NULL arrays are required");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    ftcg_opts_t o{};
+    if (opts) o = *opts;
+    for (int i = 0; i < n; ++i) {
+        if (M[i] < 0 || (M[i] > 0 && !d_lambda[i])) {
+            set_error("ftcg_plan_batch: ping %d has a bad sample count or NULL coordinates", i);
+            return FTCG_ERR_INVALID_VALUE;
+        }
+        ftcg_opts_t oi = o;                    // the checks of ftcg_plan, ping by ping
+        ftcg_status_t st = validate_plan_args(M[i], N[i], sigma, w, &oi);
+        if (st != FTCG_SUCCESS) return st;
+    }
+    Batch* b = new (std::nothrow) Batch();
+    if (!b) {
+        set_error("ftcg_plan_batch: host allocation failed");
+        return FTCG_ERR_OUT_OF_MEMORY;
+    }
+    b->n = n;
+    b->w = w;
+    b->sigma = sigma;
+    b->opts = o;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    b->last = s;
+    ftcg_status_t st = plan_batch_impl(*b, d_lambda, M, N, s);
+    if (st != FTCG_SUCCESS) {
+        release_batch(b);
+        return st;
+    }
+    *out = reinterpret_cast<ftcg_batch_t>(b);
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t ftcg_batch_set_weights(ftcg_batch_t batch, const void* const* d_alpha,
+                                     int32_t dtype, ftcg_stream_t stream) {
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_batch_set_weights: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    if (dtype != FTCG_WEIGHTS_F64 && dtype != FTCG_WEIGHTS_F32) {
+        set_error("ftcg_batch_set_weights: bad dtype");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    b->last = s;
+    for (int i = 0; i < b->n; ++i)
+        FTCG_TRY(launch_set_alpha(*b->pings[i], d_alpha ? d_alpha[i] : nullptr, dtype, s));
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t ftcg_batch_weights(ftcg_batch_t batch, double* const* d_alpha_out,
+                                 ftcg_stream_t stream) {
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_batch_weights: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    b->last = s;
+    ftcg_status_t worst = FTCG_SUCCESS;
+    for (int i = 0; i < b->n; ++i) {
+        ftcg_status_t st = compute_weights(*b->pings[i], d_alpha_out ? d_alpha_out[i] : nullptr, s);
+        if (st == FTCG_ERR_NUMERIC) worst = st;
+        else if (st != FTCG_SUCCESS) return st;
+    }
+    return worst;
+}
+
+ftcg_status_t ftcg_adjoint_batch(ftcg_batch_t batch, const void* const* d_values, int32_t vdtype,
+                                 void* const* d_images, ftcg_stream_t stream) {
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_adjoint_batch: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    if (vdtype != FTCG_VALUES_C64 && vdtype != FTCG_VALUES_BF16X2) {
+        set_error("ftcg_adjoint_batch: unknown value dtype %d", vdtype);
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    FTCG_TRY(check_ptr_array(d_images, b->n, "ftcg_adjoint_batch images"));
+    if (!d_values) {
+        set_error("ftcg_adjoint_batch: values pointer array is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    for (int i = 0; i < b->n; ++i)
+        if (b->pings[i]->M > 0 && !d_values[i]) {
+            set_error("ftcg_adjoint_batch: values pointer %d is NULL", i);
+            return FTCG_ERR_INVALID_VALUE;
+        }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    b->last = s;
+    return batch_enqueue(*b, d_values, vdtype, d_images, s);
+}
+
+ftcg_status_t ftcg_batch_capture(ftcg_batch_t batch, const void* const* d_values, int32_t vdtype,
+                                 void* const* d_images, ftcg_stream_t stream) {
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_batch_capture: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!s) {
+        set_error("ftcg_batch_capture: capture needs a non-default stream");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    // first a plain run: sets the kernel attributes and the persistent grid size outside capture
+    FTCG_TRY(ftcg_adjoint_batch(batch, d_values, vdtype, d_images, stream));
+    FTCG_CK(cudaStreamSynchronize(s));
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    FTCG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ftcg_status_t st = batch_enqueue(*b, d_values, vdtype, d_images, s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != FTCG_SUCCESS) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    FTCG_CK(e);
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    FTCG_CK(e);
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t ftcg_batch_launch(ftcg_batch_t batch, ftcg_stream_t stream) {
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_batch_launch: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    if (!b->gexec) {
+        set_error("ftcg_batch_launch: no captured graph (call ftcg_batch_capture first)");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    b->last = s;
+    FTCG_CK(cudaGraphLaunch(b->gexec, s));
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t ftcg_batch_info(ftcg_batch_t batch, int32_t* tiles, int64_t* entries,
+                              int64_t* device_bytes) {
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_batch_info: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    if (tiles)
+        for (int i = 0; i < b->n; ++i) tiles[i] = b->pings[i]->bin.T;
+    if (entries) *entries = b->entries;
+    if (device_bytes) *device_bytes = b->device_bytes;
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t ftcg_batch_destroy(ftcg_batch_t batch) {
+    clear_error();
+    release_batch(reinterpret_cast<Batch*>(batch));
+    return FTCG_SUCCESS;
+}
+
+}  // extern "C"

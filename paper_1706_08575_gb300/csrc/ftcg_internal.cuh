@@ -78,6 +78,7 @@ struct Binning {
     int64_t n_entries = 0;
     Entry* ent = nullptr;               // n_entries, sorted by (tile, column bin, row)
     int* colptr = nullptr;              // ntiles * ncb + 1 start offsets
+    int* tile_order = nullptr;          // tiles by decreasing entry count (launch order)
 };
 
 struct Plan {
@@ -104,6 +105,11 @@ struct Plan {
     cudaEvent_t* prof_ev = nullptr;     // kMaxProfiled * 4, created on first use
 };
 constexpr int kMaxProfiled = 1024;
+
+// api.cu: argument checks of ftcg_plan (fills the default tile) and plan construction.
+ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, ftcg_opts_t* o);
+ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool own_grid);
+void release_plan(Plan* p);
 
 // ---------------------------------------------------------------------------------------------
 // Launchers (defined in the .cu files)

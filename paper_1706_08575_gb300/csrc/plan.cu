@@ -10,7 +10,10 @@
 // (one wide radix digit: the whole key). Keys are few enough (tiles * (T + w - 1)^2) that one
 // histogram + one exclusive scan + one scatter replace a multi-pass radix sort.
 
+#include <algorithm>
 #include <cstdio>
+#include <numeric>
+#include <vector>
 
 #include "ftcg_internal.cuh"
 
@@ -243,9 +246,31 @@ ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStr
 void free_binning(Binning& b) {
     if (b.ent) cudaFree(b.ent);
     if (b.colptr) cudaFree(b.colptr);
+    if (b.tile_order) cudaFree(b.tile_order);
     b.ent = nullptr;
     b.colptr = nullptr;
+    b.tile_order = nullptr;
     b.n_entries = 0;
+}
+
+// Launch order of the tiles: decreasing entry count, so that the heaviest tiles start first and
+// the light (often empty) ones fill the tail.
+static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
+    const int64_t nbins = (int64_t)b.ntiles * b.ncb;
+    std::vector<int> cp(nbins + 1);
+    FTCG_CK(cudaMemcpyAsync(cp.data(), b.colptr, (nbins + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                            s));
+    FTCG_CK(cudaStreamSynchronize(s));
+    std::vector<int> order(b.ntiles);
+    std::iota(order.begin(), order.end(), 0);
+    auto cnt = [&](int t) { return cp[(int64_t)(t + 1) * b.ncb] - cp[(int64_t)t * b.ncb]; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cnt(x) > cnt(y); });
+    FTCG_CK(cudaMalloc(&b.tile_order, b.ntiles * sizeof(int)));
+    *bytes += b.ntiles * sizeof(int);
+    FTCG_CK(cudaMemcpyAsync(b.tile_order, order.data(), b.ntiles * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    FTCG_CK(cudaStreamSynchronize(s));
+    return FTCG_SUCCESS;
 }
 
 ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, double scale, int G,
@@ -292,7 +317,7 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
     }
     FTCG_CK(cudaFreeAsync(hist, s));
     FTCG_CK(cudaFreeAsync(offs, s));
-    return FTCG_SUCCESS;
+    return order_tiles(b, s, bytes);
 }
 
 }  // namespace ftcg

@@ -3,130 +3,35 @@
 // installation of per-sample weights.
 //
 // Spreading: one CTA owns one T x T tile of the periodic G x G grid and accumulates it in shared
-// memory. It reads the tile's sorted entries (every (tile, sample) pair whose w x w footprint
-// touches the tile, built by plan.cu), splits them into equal contiguous chunks, one per group of
-// GW lanes (GW = 4, 8 or 16 >= w), and for each entry the group's lane l handles tap column l: it
-// evaluates phi(dx - l) and phi(dy - l) in FP32, broadcasts the w row factors with shuffles, and
-// adds c phi(dx - l) phi(dy - r) to the cells it owns with shared-memory atomics (taps outside
-// the tile are another tile's). The tile is then stored once, coalesced, so every grid cell is
-// written exactly once and no zero-fill or global atomics are needed.
+// memory; tiles are launched heaviest first. The tile's sorted entries (every (tile, sample) pair
+// whose w x w footprint touches the tile, ordered by first-tap column then first-tap row, built
+// by plan.cu) are split into equal contiguous chunks, one per group of GW lanes (GW = 4, 8 or
+// 16 >= w). Lane l of a group owns tap column l of the current column bin and keeps a rolling
+// window of w rows of its column in registers: an entry adds c phi(dx - l) phi(dy - r) to window
+// row r (the w row factors are computed one per lane and broadcast by shuffles); when the next
+// entry starts on a later row, the rows it can no longer reach leave the window with one
+// shared-memory atomic each. A row thus receives one atomic per (column bin, chunk) instead of
+// one per entry. The tile is then stored once, coalesced: every grid cell is written exactly
+// once, with no zero-fill and no global atomics.
 
-#include "ftcg_internal.cuh"
+#include "spread_tile.cuh"
 
 namespace ftcg {
 
 namespace {
 
-constexpr int kSpreadThreads = 256;
+using tile::kSpreadThreads;
+using tile::es32;
 
-__device__ __forceinline__ float es32(float t, float inv_hw, float beta) {
-    float z = t * inv_hw;
-    float q = fmaf(-z, z, 1.0f);
-    return q >= 0.0f ? __expf(beta * (sqrtf(q) - 1.0f)) : 0.0f;
-}
-
-__device__ __forceinline__ float bf16_bits_to_float(uint32_t bits) {
-    return __uint_as_float((bits & 0xffffu) << 16);
-}
-
-template <bool VBF>
-__device__ __forceinline__ float2 load_value(const void* __restrict__ vals, uint32_t j) {
-    if (VBF) {
-        __nv_bfloat162 b = reinterpret_cast<const __nv_bfloat162*>(vals)[j];
-        return __bfloat1622float2(b);
-    } else {
-        return reinterpret_cast<const float2*>(vals)[j];
-    }
-}
-
-// GW: lanes per entry (power of two >= w); WT: compile-time w (0 = runtime w <= GW).
 template <int GW, int WT, int T, bool VBF, bool ABF>
-__global__ void __launch_bounds__(kSpreadThreads)
+__global__ void __launch_bounds__(tile::kSpreadThreads)
     k_spread(const Entry* __restrict__ ent, const int* __restrict__ colptr,
-             const void* __restrict__ vals, float2* __restrict__ grid, int G, int ntx, int Wrt,
-             float beta, float inv_hw) {
-    constexpr int LD = T + 1;
-    constexpr int NG = kSpreadThreads / GW;
-    const int W = WT > 0 ? WT : Wrt;
-    const int ncb = T + W - 1;
+             const int* __restrict__ tile_order, const void* __restrict__ vals,
+             float2* __restrict__ grid, int G, int ntx, int Wrt, float beta, float inv_hw) {
     extern __shared__ float smem[];
-    float* s_re = smem;
-    float* s_im = smem + T * LD;
-    int* s_col = reinterpret_cast<int*>(smem + 2 * T * LD);
-
-    const int tile = blockIdx.x;
-    const int tyi = tile / ntx, txi = tile - tyi * ntx;
-    const int X0 = txi * T, Y0 = tyi * T;
-    const int Tw = min(T, G - X0), Th = min(T, G - Y0);
-
-    for (int i = threadIdx.x; i < 2 * T * LD; i += kSpreadThreads) smem[i] = 0.0f;
-    for (int i = threadIdx.x; i <= ncb; i += kSpreadThreads) s_col[i] = colptr[(int64_t)tile * ncb + i];
-    __syncthreads();
-
-    const int e0 = s_col[0], e1 = s_col[ncb];
-    const int n = e1 - e0;
-    const int g = threadIdx.x / GW, l = threadIdx.x % GW;
-    const unsigned gmask = (GW == 32 ? 0xffffffffu : ((1u << GW) - 1u)) << ((threadIdx.x & 31) & ~(GW - 1));
-    const int per = (n + NG - 1) / NG;
-    const int a = e0 + g * per;
-    const int b = min(e1, a + per);
-
-    for (int base = a; base < b; base += GW) {
-        const int idx = base + l;
-        float dx = 0.f, dy = 0.f, cre = 0.f, cim = 0.f;
-        int cxl = 0, cyl = 0;
-        if (idx < b) {
-            Entry e = ent[idx];
-            const uint32_t j = e.packed & kSampleMask;
-            cyl = (int)(e.packed >> kSampleBits) - (W - 1);
-            int lo = 0, hi = ncb - 1;             // column bin: last k with s_col[k] <= idx
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_col[mid] <= idx) lo = mid; else hi = mid - 1;
-            }
-            cxl = lo - (W - 1);
-            const float al = ABF ? bf16_bits_to_float(e.alpha) : __uint_as_float(e.alpha);
-            const float2 v = load_value<VBF>(vals, j);
-            cre = al * v.x;
-            cim = al * v.y;
-            dx = e.dx;
-            dy = e.dy;
-        }
-        const int cnt = min(GW, b - base);
-        for (int k = 0; k < cnt; ++k) {
-            const float kdx = __shfl_sync(gmask, dx, k, GW);
-            const float kdy = __shfl_sync(gmask, dy, k, GW);
-            const float kre = __shfl_sync(gmask, cre, k, GW);
-            const float kim = __shfl_sync(gmask, cim, k, GW);
-            const int kcx = __shfl_sync(gmask, cxl, k, GW);
-            const int kcy = __shfl_sync(gmask, cyl, k, GW);
-            const bool lane_tap = l < W;
-            const float fx = lane_tap ? es32(kdx - (float)l, inv_hw, beta) : 0.0f;
-            const float fy = lane_tap ? es32(kdy - (float)l, inv_hw, beta) : 0.0f;
-            const int col = kcx + l;
-            const bool okx = lane_tap && col >= 0 && col < Tw;
-            const float ar = kre * fx, ai = kim * fx;
-            float* pre = s_re + col;
-            float* pim = s_im + col;
-#pragma unroll
-            for (int r = 0; r < (WT > 0 ? WT : GW); ++r) {
-                if (WT == 0 && r >= W) break;
-                const float py = __shfl_sync(gmask, fy, r, GW);
-                const int row = kcy + r;
-                if (okx && row >= 0 && row < Th) {
-                    atomicAdd(pre + row * LD, ar * py);
-                    atomicAdd(pim + row * LD, ai * py);
-                }
-            }
-        }
-    }
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int y = warp; y < Th; y += kSpreadThreads / 32) {
-        float2* dst = grid + (int64_t)(Y0 + y) * G + X0;
-        for (int x = lane; x < Tw; x += 32) dst[x] = make_float2(s_re[y * LD + x], s_im[y * LD + x]);
-    }
+    const int t = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
+    tile::spread_tile<GW, WT, T, VBF, ABF>(ent, colptr, vals, grid, G, ntx, Wrt, beta, inv_hw, t,
+                                           smem);
 }
 
 template <int GW, int WT, int T, bool VBF, bool ABF>
@@ -137,8 +42,8 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const float beta = (float)p.win.beta;
     const float inv_hw = (float)(2.0 / p.win.w);
-    kern<<<b.ntiles, kSpreadThreads, smem, s>>>(b.ent, b.colptr, vals, grid, b.G, b.ntx, b.W, beta,
-                                                inv_hw);
+    kern<<<b.ntiles, kSpreadThreads, smem, s>>>(b.ent, b.colptr, b.tile_order, vals, grid, b.G,
+                                                b.ntx, b.W, beta, inv_hw);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
 }

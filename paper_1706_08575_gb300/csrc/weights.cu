@@ -52,23 +52,27 @@ __device__ __forceinline__ int wrapi(long long c, int G) {
     return (int)(r < 0 ? r + G : r);
 }
 
-// W1: g_l += phi(u_x - l_x) phi(u_y - l_y) (real, unit strengths), one 16-lane group per sample,
-// lane l = tap column l; FP64 global atomics on the real part of a complex128 grid.
+// W1: g_l += phi(u_x - l_x) phi(u_y - l_y) (real, unit strengths), one 16-lane group per sample:
+// lane l evaluates tap l of both axes once, the row factors are broadcast by shuffles, and lane l
+// adds its column with FP64 global atomics on the real part of a complex128 grid.
 __global__ void __launch_bounds__(256)
     k_w1_spread(const double* __restrict__ lam, int64_t M, double scale, int G, int W,
                 double beta, double inv_hw, double* __restrict__ grid) {
     const int l = threadIdx.x & 15;
+    const unsigned gmask = 0xffffu << ((threadIdx.x & 31) & 16);
     const int64_t ngr = (int64_t)gridDim.x * (blockDim.x / 16);
-    for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / 16) + threadIdx.x / 16; j < M; j += ngr) {
+    const int64_t j0 = blockIdx.x * (int64_t)(blockDim.x / 16) + threadIdx.x / 16;
+    for (int64_t j = j0; j < M; j += ngr) {
         Origin64 ox = origin64(lam[2 * j], scale, W);
         Origin64 oy = origin64(lam[2 * j + 1], scale, W);
-        if (!ox.ok || !oy.ok || l >= W) continue;
-        const double fx = es64(ox.d - l, inv_hw, beta);
-        int col = wrapi(ox.c + l, G);
+        if (!ox.ok || !oy.ok) continue;                       // uniform within the group
+        const double fx = l < W ? es64(ox.d - l, inv_hw, beta) : 0.0;
+        const double fyl = l < W ? es64(oy.d - l, inv_hw, beta) : 0.0;
+        const int col = wrapi(ox.c + l, G);
         int row = wrapi(oy.c, G);
         for (int r = 0; r < W; ++r) {
-            const double fy = es64(oy.d - r, inv_hw, beta);
-            atomicAdd(grid + 2 * ((int64_t)row * G + col), fx * fy);
+            const double fy = __shfl_sync(gmask, fyl, r, 16);
+            if (l < W) atomicAdd(grid + 2 * ((int64_t)row * G + col), fx * fy);
             if (++row == G) row = 0;
         }
     }
@@ -111,15 +115,16 @@ __global__ void __launch_bounds__(256)
     for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / 16) + threadIdx.x / 16; j < M; j += ngr) {
         Origin64 ox = origin64(lam[2 * j], scale, W);
         Origin64 oy = origin64(lam[2 * j + 1], scale, W);
-        const bool ok = ox.ok && oy.ok;
+        const bool ok = ox.ok && oy.ok;                       // uniform within the group
         double sr = 0.0;
-        if (ok && l < W) {
-            const double fx = es64(ox.d - l, inv_hw, beta);
+        if (ok) {
+            const double fx = l < W ? es64(ox.d - l, inv_hw, beta) : 0.0;
+            const double fyl = l < W ? es64(oy.d - l, inv_hw, beta) : 0.0;
             const int col = wrapi(ox.c + l, G);
             int row = wrapi(oy.c, G);
             for (int r = 0; r < W; ++r) {
-                const double fy = es64(oy.d - r, inv_hw, beta);
-                sr += fy * grid[(int64_t)row * G + col].x;
+                const double fy = __shfl_sync(gmask, fyl, r, 16);
+                if (l < W) sr += fy * grid[(int64_t)row * G + col].x;
                 if (++row == G) row = 0;
             }
             sr *= fx;
