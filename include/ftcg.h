@@ -178,6 +178,27 @@ ftcg_status_t ftcg_plan_entries(ftcg_plan_t plan, int32_t* h_tile, int32_t* h_cx
 ftcg_status_t ftcg_profile(ftcg_plan_t plan, int32_t enable);
 ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls);
 
+/*
+ * ftcg_adjoint_small_noalloc -- the weighted adjoint of ftcg_adjoint, without a plan and without
+ * any allocation, for small images. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory, such as code running while a stream is captured
+ * into a CUDA graph, real-time processing loops that fix their memory at start-up, or frameworks
+ * that own the device memory pool.
+ *   d_lambda  device, M x 2 float64 (x, y); d_values device, M complex64; d_alpha device, M
+ *             float64 weights or NULL (alpha = 1); d_image device, N x N complex64 (output, fully
+ *             overwritten); all owned by the caller.
+ *   N, sigma, w as in ftcg_plan, with the grid side G = sigma N limited to 512: larger sizes
+ *             return FTCG_ERR_NOT_SUPPORTED before any work is queued.
+ * Scratch lives in fixed device arrays inside the library (about 4 MiB per GPU that loads it,
+ * held until the process exits). The first call on a device looks up their addresses (it must
+ * come before any stream capture on that device). Every call reuses the same arrays, so calls
+ * that overlap on the GPU (different streams or unordered threads) race; calls on one stream are
+ * safe. Samples with non-finite coordinates are skipped. Asynchronous on `stream`.
+ */
+ftcg_status_t ftcg_adjoint_small_noalloc(const double* d_lambda, const void* d_values,
+                                         const double* d_alpha, int64_t M, int32_t N, double sigma,
+                                         int32_t w, void* d_image, ftcg_stream_t stream);
+
 /* Release a plan and all device memory it holds (synchronises). NULL is accepted. */
 ftcg_status_t ftcg_destroy(ftcg_plan_t plan);
 

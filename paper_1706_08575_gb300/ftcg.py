@@ -59,6 +59,7 @@ SIGNATURES = [
     ("ftcg_plan_entries", _I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ftcg_profile", _I32, [_VP, _I32]),
     ("ftcg_stage_times", _I32, [_VP, _VP, _VP]),
+    ("ftcg_adjoint_small_noalloc", _I32, [_VP, _VP, _VP, _I64, _I32, _D, _I32, _VP, _VP]),
     ("ftcg_destroy", _I32, [_VP]),
     ("ftcg_status_string", ctypes.c_char_p, [_I32]),
     ("ftcg_last_error", ctypes.c_char_p, []),
