@@ -236,6 +236,94 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # the GPU leg
 # ---------------------------------------------------------------------------------------------
+def learned_vs_plain(device, n_pings=64, train_geos=24, train_steps=1500, seed=5):
+    """Pings of the uneven batch recipe, per-ping end to end (geometry changes every ping):
+    plain  = per ping: plan, exact FP64 FTCG weights, FP32 adjoint;
+    learned + batched = one batched plan, kNN features + MLP weights per ping, one batched adjoint.
+    The network is trained here on exact weights of random jittered polar geometries."""
+    import numpy as np
+    import torch
+
+    import paper_1706_08575_gb300 as F
+    import sasgen
+    from paper_1706_08575_gb300 import learn
+
+    rng = np.random.default_rng(seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    geos, Ns = [], []
+    for _ in range(train_geos):
+        lam, N, kr = sasgen.random_geometry(rng, N_choices=(256, 512), M_range=(20_000, 60_000))
+        geos.append((lam, kr))
+        Ns.append(N)
+    feats, targ = learn.build_dataset(geos, Ns)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    mlp = F.Mlp(learn.init_params(0))
+    t0 = time.perf_counter()
+    hist = learn.train(mlp, feats, targ, steps=train_steps, batch=8192, lr=2e-3, log_every=500)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del feats, targ
+
+    pings = [sasgen.batch_ping(b) for b in range(n_pings)]
+    lams = [torch.from_numpy(p.lam).to(device) for p in pings]
+    auxs = [torch.from_numpy(learn.kr_feature(p.kr)).to(device) for p in pings]
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    vals = [torch.randn(p.M, dtype=torch.complex64, device=device, generator=g) for p in pings]
+    M_tot = sum(p.M for p in pings)
+    # warm the tile autotuner cache and the kernels
+    with F.Plan(lams[0], pings[0].N, 2.0, 8) as pl:
+        pl.weights()
+        pl.adjoint(vals[0])
+    # plain: one ping after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_imgs = []
+    for lam, v, p in zip(lams, vals, pings):
+        with F.Plan(lam, p.N, 2.0, 8) as pl:
+            pl.weights()
+            plain_imgs.append(pl.adjoint(v))
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    # learned + batched
+    t0 = time.perf_counter()
+    with F.Batch(lams, [p.N for p in pings], 2.0, 8) as b:
+        alphas = [mlp.predict(F.features(lam, aux)) for lam, aux in zip(lams, auxs)]
+        b.set_weights(alphas)
+        imgs = b.adjoint(vals)
+        torch.cuda.synchronize()
+        t_learned = time.perf_counter() - t0
+        # the same batch, adjoint only, replayed from a CUDA graph
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            gi = b.capture(vals)
+            s.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(5):
+                b.launch()
+            e1.record(s)
+            s.synchronize()
+            t_graph = e0.elapsed_time(e1) / 5e3
+        errs = [float(torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r))
+                for a, r in zip(imgs, plain_imgs)]
+        tiles, entries, _ = b.info()
+    mlp.close()
+    return {"pings": n_pings, "samples": M_tot,
+            "plain_single_ping_fp32": {"value": M_tot / t_plain, "unit": UNIT, "s": t_plain},
+            "learned_batched": {"value": M_tot / t_learned, "unit": UNIT, "s": t_learned},
+            "speedup": t_plain / t_learned,
+            "batched_adjoint_graph": {"value": M_tot / t_graph, "unit": UNIT, "ms": 1e3 * t_graph},
+            "image_rel_l2_learned_vs_exact": {"median": float(np.median(errs)),
+                                              "max": float(np.max(errs))},
+            "train": {"geometries": train_geos, "samples": int(sum(len(gg[0]) for gg in geos)),
+                      "steps": train_steps, "batch": 8192, "s": t_train, "data_s": t_data,
+                      "loss_first_last": [hist[0][1], hist[-1][1]]},
+            "tiles_chosen": sorted(set(tiles))}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -352,6 +440,12 @@ def run_ours(args):
     value = world * p.M * args.steps / total_max
 
     if rank == 0:
+        extras = None
+        if not args.no_extras:
+            try:
+                extras = learned_vs_plain(device, n_pings=args.extras_pings)
+            except Exception as e:       # the headline line must still print
+                extras = {"error": f"{type(e).__name__}: {e}"}
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             alpha = plan.weights().cpu().numpy()
@@ -380,6 +474,7 @@ def run_ours(args):
             "wall_s_timed_region": wall,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "learned_vs_plain_per_ping": extras,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -395,6 +490,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras-pings", type=int, default=64)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

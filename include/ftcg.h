@@ -179,6 +179,96 @@ ftcg_status_t ftcg_profile(ftcg_plan_t plan, int32_t enable);
 ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls);
 
 /*
+ * Batched pings. Many independent pings (each its own geometry, sample count and image side N)
+ * are gridded together: one persistent spreading launch over every (ping, tile) work item, one
+ * batched inverse FFT per distinct grid side, one window division + crop launch (Eq. twodcg per
+ * ping). The sequence has no host synchronisation and can be captured once in a CUDA graph.
+ *
+ * ftcg_plan_batch -- plan n pings. d_lambda, M, N: host arrays of n entries (d_lambda[i] a device
+ * M[i] x 2 float64 array, read during the call); sigma, w, opts shared, with the checks of
+ * ftcg_plan per ping. opts->tile = 0 lets the built-in autotuner pick the tile side of each ping:
+ * it times both tile sides once per (grid side, w, precision, half-octave bucket of samples per
+ * grid cell) and keeps the faster for the life of the process. Synchronises.
+ */
+ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const* d_lambda,
+                              const int64_t* M, const int32_t* N, double sigma, int32_t w,
+                              const ftcg_opts_t* opts, ftcg_stream_t stream);
+
+/* Per-ping weights: d_alpha is a host array of n device pointers (M[i] entries each, dtype as in
+ * ftcg_set_weights) or NULL for alpha = 1 everywhere. Asynchronous. */
+ftcg_status_t ftcg_batch_set_weights(ftcg_batch_t batch, const void* const* d_alpha, int32_t dtype,
+                                     ftcg_stream_t stream);
+
+/* Exact FTCG weights of every ping (ftcg_weights ping by ping); d_alpha_out: NULL or a host array
+ * of n device pointers to M[i] float64 outputs. Synchronises. */
+ftcg_status_t ftcg_batch_weights(ftcg_batch_t batch, double* const* d_alpha_out,
+                                 ftcg_stream_t stream);
+
+/* Weighted adjoints of all pings: d_values[i] (M[i] values, vdtype) -> d_images[i] (N[i] x N[i]
+ * complex64); host arrays of n device pointers. Asynchronous, no host synchronisation. */
+ftcg_status_t ftcg_adjoint_batch(ftcg_batch_t batch, const void* const* d_values, int32_t vdtype,
+                                 void* const* d_images, ftcg_stream_t stream);
+
+/* Run ftcg_adjoint_batch once, then capture it on `stream` (which must not be the legacy default
+ * stream) into a CUDA graph bound to these buffers; ftcg_batch_launch replays it. */
+ftcg_status_t ftcg_batch_capture(ftcg_batch_t batch, const void* const* d_values, int32_t vdtype,
+                                 void* const* d_images, ftcg_stream_t stream);
+ftcg_status_t ftcg_batch_launch(ftcg_batch_t batch, ftcg_stream_t stream);
+
+/* tiles: NULL or n int32 (the tile side chosen for each ping); totals of entries and device
+ * bytes held. Host call. */
+ftcg_status_t ftcg_batch_info(ftcg_batch_t batch, int32_t* tiles, int64_t* entries,
+                              int64_t* device_bytes);
+ftcg_status_t ftcg_batch_destroy(ftcg_batch_t batch);
+
+/*
+ * Learned weights. A small MLP predicts each sample's FTCG weight (Eq. difopt at r = 1) from its
+ * local k-space neighbourhood, so that pings with fresh jittered geometry need not run the exact
+ * construction; ftcg_weights provides the labels and remains the reference.
+ *
+ * ftcg_features -- per sample k, 48 bfloat16: the offsets lambda_j - lambda_k (x, y) of the 16
+ * nearest other samples in Euclidean distance (ties by smaller index), then d_aux[k] (a
+ * caller-chosen scalar such as the normalised range wavenumber; NULL = 0), then 15 zeros.
+ * d_lambda: device M x 2 float64; d_features: device M x 48 bfloat16 (out); d_neighbors: NULL or
+ * device M x 16 int32 (out, -1 where fewer than 16 other samples exist). The neighbour sets are
+ * exact (a spatial hash with a ring search that stops only when no unvisited sample can be
+ * closer). Allocates temporaries and synchronises.
+ */
+ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t M,
+                            void* d_features, int32_t* d_neighbors, ftcg_stream_t stream);
+
+typedef struct ftcg_mlp_s* ftcg_mlp_t;
+enum { FTCG_MLP_PARAMS = 10561 };
+/*
+ * The network: 33 -> 64 -> 64 -> 64 -> 1, GELU (tanh form) on the hidden layers, output
+ * y = log alpha; BF16 tensor-core matrix products with FP32 accumulation, FP32 master parameters.
+ * Parameters are packed FP32 in this order: W1 [33][64], b1 [64], W2 [64][64], b2, W3 [64][64],
+ * b3, w4 [64], b4 [1], each W as [input][output], row-major.
+ */
+ftcg_status_t ftcg_mlp_create(ftcg_mlp_t* out, const float* h_params);
+/* Read (set = 0) or write (set = 1) the parameters, the Adam moments and the step count (any
+ * pointer may be NULL); host buffers of FTCG_MLP_PARAMS floats. Synchronises. */
+ftcg_status_t ftcg_mlp_state(ftcg_mlp_t mlp, float* h_params, float* h_m, float* h_v,
+                             int64_t* step, int32_t set);
+/* alpha_k = exp(y_k) for M feature rows, written as float64 (installable with
+ * ftcg_set_weights). Asynchronous. */
+ftcg_status_t ftcg_mlp_predict(ftcg_mlp_t mlp, const void* d_features, int64_t M,
+                               double* d_alpha_out, ftcg_stream_t stream);
+/* Gradients of the mean squared error of y against d_target (log alpha, float64) over a batch
+ * of B rows: row r is feature/target row d_index[r] (or r when d_index is NULL). h_grads: NULL
+ * or FTCG_MLP_PARAMS floats (packed like the parameters); h_loss: NULL or one float.
+ * Synchronises. */
+ftcg_status_t ftcg_mlp_grads(ftcg_mlp_t mlp, const void* d_features, const double* d_target,
+                             const int32_t* d_index, int64_t B, float* h_grads, float* h_loss,
+                             ftcg_stream_t stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on such a batch; h_loss
+ * (NULL or one float) receives the batch loss before the step and then synchronises. */
+ftcg_status_t ftcg_mlp_train_step(ftcg_mlp_t mlp, const void* d_features, const double* d_target,
+                                  const int32_t* d_index, int64_t B, float lr, float* h_loss,
+                                  ftcg_stream_t stream);
+ftcg_status_t ftcg_mlp_destroy(ftcg_mlp_t mlp);
+
+/*
  * ftcg_adjoint_small_noalloc -- the weighted adjoint of ftcg_adjoint, without a plan and without
  * any allocation, for small images. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, such as code running while a stream is captured

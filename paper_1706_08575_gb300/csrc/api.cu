@@ -35,8 +35,6 @@ ftcg_status_t invalid(const char* msg) {
     return FTCG_ERR_INVALID_VALUE;
 }
 
-int auto_tile(int G) { return G <= 512 ? 32 : 64; }
-
 }  // namespace
 
 namespace ftcg {
@@ -118,20 +116,21 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
     }
     if (o.precision != FTCG_PREC_FP32 && o.precision != FTCG_PREC_BF16)
         return invalid("ftcg_plan: opts.precision must be 0 (FP32) or 1 (BF16)");
-    if (o.tile == 0) o.tile = auto_tile((int)G);
-    if (o.tile != 32 && o.tile != 64) return invalid("ftcg_plan: opts.tile must be 0, 32 or 64");
+    if (o.tile != 0 && o.tile != 32 && o.tile != 64)
+        return invalid("ftcg_plan: opts.tile must be 0, 32 or 64");
     if (o.weight_width != 0 && (o.weight_width < 4 || o.weight_width > 16))
         return invalid("ftcg_plan: opts.weight_width must be 0 or 4..16");
     if (M > kMaxSamples) {
         set_error("ftcg_plan: M > %lld is beyond this build's entry format", (long long)kMaxSamples);
         return FTCG_ERR_NOT_SUPPORTED;
     }
-    if (G > 65536) {
-        set_error("ftcg_plan: G = sigma N > 65536 is not supported");
+    if (G > 65536 || N > 32768) {
+        set_error("ftcg_plan: G = sigma N > 65536 or N > 32768 is not supported");
         return FTCG_ERR_NOT_SUPPORTED;
     }
-    const long long ntx = (G + o.tile - 1) / o.tile;
-    const long long ncb = o.tile + w - 1;
+    const int tmin = o.tile ? o.tile : 32;      // the smallest tile the autotuner may pick
+    const long long ntx = (G + tmin - 1) / tmin;
+    const long long ncb = (o.tile ? o.tile : 64) + w - 1;
     if (ntx * ntx * ncb * ncb >= (1LL << 31)) {
         set_error("ftcg_plan: the binning key space is too large for G = %lld", G);
         return FTCG_ERR_NOT_SUPPORTED;
@@ -199,6 +198,13 @@ ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int
     p->win = Window{w, es_beta(w, sigma)};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
+    if (o.tile == 0) {
+        ftcg_status_t tst = tune_tile(d_lambda, M, N, sigma, w, o, s, &p->opts.tile);
+        if (tst != FTCG_SUCCESS) {
+            delete p;
+            return tst;
+        }
+    }
     ftcg_status_t st = make_plan(p, d_lambda, s, true);
     if (st != FTCG_SUCCESS && st != FTCG_ERR_NUMERIC) {
         release_plan(p);

@@ -35,7 +35,7 @@ struct PingDesc {
 };
 
 template <int GW, int WT, bool VBF, bool ABF>
-__global__ void __launch_bounds__(tile::kSpreadThreads)
+__global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
     k_spread_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items, int nitems,
                    int* __restrict__ counter, int Wrt, float beta, float inv_hw) {
     extern __shared__ float smem[];
@@ -58,19 +58,17 @@ __global__ void __launch_bounds__(tile::kSpreadThreads)
 }
 
 __global__ void k_deapod_batch(const PingDesc* __restrict__ desc) {
-    const PingDesc d = desc[blockIdx.y];
+    const PingDesc d = desc[blockIdx.z];
     const int N = d.N, G = d.G;
-    const int64_t total = (int64_t)N * N;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int iy = (int)(i / N), ix = (int)(i - (int64_t)iy * N);
-        int qy = iy - N / 2, qx = ix - N / 2;
-        if (qy < 0) qy += G;
-        if (qx < 0) qx += G;
-        const float2 h = d.grid[(int64_t)qy * G + qx];
-        const double f = d.deapod[iy] * d.deapod[ix];
-        d.img[i] = make_float2((float)((double)h.x * f), (float)((double)h.y * f));
-    }
+    const int iy = blockIdx.y;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (iy >= N || ix >= N) return;
+    int qy = iy - N / 2, qx = ix - N / 2;
+    if (qy < 0) qy += G;
+    if (qx < 0) qx += G;
+    const float2 h = d.grid[(int64_t)qy * G + qx];
+    const float f = (float)(d.deapod[iy] * d.deapod[ix]);
+    d.img[(int64_t)iy * N + ix] = make_float2(h.x * f, h.y * f);
 }
 
 size_t spread_smem(int T, int W) {
@@ -111,6 +109,8 @@ ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaSt
     cudaEventDestroy(b);
     return FTCG_SUCCESS;
 }
+
+}  // namespace
 
 ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
                         const ftcg_opts_t& opts, cudaStream_t s, int* T_out) {
@@ -160,6 +160,8 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
     return FTCG_SUCCESS;
 }
 
+namespace {
+
 struct Batch {
     int n = 0, w = 0;
     double sigma = 0;
@@ -206,6 +208,8 @@ ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
     auto kern = k_spread_batch<GW, WT, VBF, ABF>;
     const size_t smem = spread_smem(64, b.w);
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
     if (b.persistent_ctas == 0) {
         int dev = 0, sms = 0, per = 0;
         FTCG_CK(cudaGetDevice(&dev));
@@ -255,9 +259,7 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
         FTCG_CKFFT(cufftExecC2C(c.fft, reinterpret_cast<cufftComplex*>(c.grids),
                                 reinterpret_cast<cufftComplex*>(c.grids), CUFFT_INVERSE));
     }
-    const int64_t maxpix = (int64_t)b.max_N * b.max_N;
-    const unsigned bx = (unsigned)std::min<int64_t>(std::max<int64_t>((maxpix + 255) / 256, 1), 64);
-    k_deapod_batch<<<dim3(bx, b.n), 256, 0, s>>>(b.d_desc);
+    k_deapod_batch<<<dim3((b.max_N + 255) / 256, b.max_N, b.n), 256, 0, s>>>(b.d_desc);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
 }

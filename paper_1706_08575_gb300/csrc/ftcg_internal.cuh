@@ -57,7 +57,7 @@ constexpr int64_t kMaxSamples = (int64_t(1) << kSampleBits) - 1;
 
 // One sorted (tile, sample) entry of the spreading plan: 16 bytes, loaded with one LDG.128.
 //   dx, dy : sigma lambda - first tap, in (w/2 - 1, w/2]   (float32)
-//   alpha  : per-sample weight (float32, or bfloat16 in the low half for FTCG_PREC_BF16)
+//   alpha  : per-sample weight, float32 (FTCG_PREC_BF16: rounded to bfloat16, low 16 bits zero)
 //   packed : sample index | (cy_local + w - 1) << 25
 struct __align__(16) Entry {
     float dx, dy;
@@ -109,6 +109,9 @@ constexpr int kMaxProfiled = 1024;
 // api.cu: argument checks of ftcg_plan (fills the default tile) and plan construction.
 ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, ftcg_opts_t* o);
 ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool own_grid);
+// batch.cu: the tile-side autotuner (cached per grid side, w, precision and density bucket).
+ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
+                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out);
 void release_plan(Plan* p);
 
 // ---------------------------------------------------------------------------------------------

@@ -24,7 +24,7 @@ using tile::kSpreadThreads;
 using tile::es32;
 
 template <int GW, int WT, int T, bool VBF, bool ABF>
-__global__ void __launch_bounds__(tile::kSpreadThreads)
+__global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
     k_spread(const Entry* __restrict__ ent, const int* __restrict__ colptr,
              const int* __restrict__ tile_order, const void* __restrict__ vals,
              float2* __restrict__ grid, int G, int ntx, int Wrt, float beta, float inv_hw) {
@@ -40,6 +40,8 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
     const size_t smem = (size_t)(2 * T * (T + 1)) * sizeof(float) + (size_t)(b.ncb + 1) * sizeof(int);
     auto kern = k_spread<GW, WT, T, VBF, ABF>;
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
     const float beta = (float)p.win.beta;
     const float inv_hw = (float)(2.0 / p.win.w);
     kern<<<b.ntiles, kSpreadThreads, smem, s>>>(b.ent, b.colptr, b.tile_order, vals, grid, b.G,
@@ -66,20 +68,21 @@ ftcg_status_t dispatch_t(const Plan& p, const void* vals, float2* grid, cudaStre
     return dispatch_w<64, VBF, ABF>(p, vals, grid, s);
 }
 
-// ---- deapodisation and crop: I_p = h_{p mod G} / (phi^(p_x/G) phi^(p_y/G)), FP64 factors ----
+// ---- deapodisation and crop: I_p = h_{p mod G} / (phi^(p_x/G) phi^(p_y/G)) -------------------
+// The factors are FP64; their product for a pixel is formed in FP64 and rounded once to FP32
+// (relative 6e-8), then applied to the FP32 grid value. One thread per pixel, a 2-D launch over
+// (columns, rows); each row reads two contiguous runs of the grid (p_x >= 0 and p_x < 0).
 __global__ void k_deapod_crop(const float2* __restrict__ grid, float2* __restrict__ img,
                               const double* __restrict__ r, int N, int G) {
-    const int64_t total = (int64_t)N * N;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int iy = (int)(i / N), ix = (int)(i - (int64_t)iy * N);
-        int qy = iy - N / 2, qx = ix - N / 2;
-        if (qy < 0) qy += G;
-        if (qx < 0) qx += G;
-        const float2 h = grid[(int64_t)qy * G + qx];
-        const double f = r[iy] * r[ix];
-        img[i] = make_float2((float)((double)h.x * f), (float)((double)h.y * f));
-    }
+    const int iy = blockIdx.y;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ix >= N) return;
+    int qy = iy - N / 2, qx = ix - N / 2;
+    if (qy < 0) qy += G;
+    if (qx < 0) qx += G;
+    const float2 h = grid[(int64_t)qy * G + qx];
+    const float f = (float)(r[iy] * r[ix]);
+    img[(int64_t)iy * N + ix] = make_float2(h.x * f, h.y * f);
 }
 
 // ---- forward: zero grid, place I_p / (phi^ phi^) at p mod G -----------------------------------
@@ -149,7 +152,7 @@ __global__ void k_set_alpha(Entry* __restrict__ ent, int64_t n, const void* __re
             a = dtype == FTCG_WEIGHTS_F64 ? (float)reinterpret_cast<const double*>(alpha)[j]
                                           : reinterpret_cast<const float*>(alpha)[j];
         }
-        ent[i].alpha = bf16 ? (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a))
+        ent[i].alpha = bf16 ? (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) << 16
                             : __float_as_uint(a);
     }
 }
@@ -178,8 +181,7 @@ ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2*
 }
 
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s) {
-    const int64_t n = (int64_t)p.N * p.N;
-    k_deapod_crop<<<blocks_for(n, 256), 256, 0, s>>>(grid, img, p.deapod, p.N, p.G);
+    k_deapod_crop<<<dim3((p.N + 255) / 256, p.N), 256, 0, s>>>(grid, img, p.deapod, p.N, p.G);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
 }

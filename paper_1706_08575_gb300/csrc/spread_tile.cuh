@@ -7,7 +7,20 @@
 namespace ftcg {
 namespace tile {
 
-constexpr int kSpreadThreads = 256;
+// Build-time knobs of the spreading kernels (the defaults are the tuned values):
+//   FTCG_SPREAD_THREADS  threads per CTA; FTCG_SPREAD_MINB  minimum resident CTAs per SM requested
+//   from the register allocator; FTCG_SPREAD_WINDOW  1 = rolling row window, 0 = one shared
+//   atomic per tap.
+#ifndef FTCG_SPREAD_THREADS
+#define FTCG_SPREAD_THREADS 256
+#endif
+#ifndef FTCG_SPREAD_MINB
+#define FTCG_SPREAD_MINB 1
+#endif
+#ifndef FTCG_SPREAD_WINDOW
+#define FTCG_SPREAD_WINDOW 1
+#endif
+constexpr int kSpreadThreads = FTCG_SPREAD_THREADS;
 
 // ES window in FP32: exp(beta (sqrt(1 - z^2) - 1)) written as exp(-beta z^2 / (1 + sqrt(1 - z^2)))
 // so that no cancellation occurs near the centre (sqrt(1 - z^2) - 1 loses all its digits there).
@@ -18,8 +31,10 @@ __device__ __forceinline__ float es32(float t, float inv_hw, float beta) {
     return q >= 0.0f ? __expf(__fdividef(-beta * z2, 1.0f + sqrtf(q))) : 0.0f;
 }
 
+// A BF16-stored weight is a float32 whose low 16 bits are zero (the bfloat16 rounding of the
+// weight); masking also reads an unrounded float32 (such as the plan's default 1.0) as bfloat16.
 __device__ __forceinline__ float bf16_bits_to_float(uint32_t bits) {
-    return __uint_as_float((bits & 0xffffu) << 16);
+    return __uint_as_float(bits & 0xffff0000u);
 }
 
 template <bool VBF>
@@ -87,41 +102,39 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
         }
     };
 
-    for (int base = a; base < b; base += GW) {
-        const int idx = base + l;
-        float dx = 0.f, dy = 0.f, cre = 0.f, cim = 0.f;
-        int cxl = 0, cyl = 0;
-        if (idx < b) {
-            Entry e = ent[idx];
-            const uint32_t j = e.packed & kSampleMask;
-            cyl = (int)(e.packed >> kSampleBits) - (W - 1);
-            int lo = 0, hi = ncb - 1;             // column bin: last k with s_col[k] <= idx
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_col[mid] <= idx) lo = mid; else hi = mid - 1;
-            }
-            cxl = lo - (W - 1);
-            const float al = ABF ? bf16_bits_to_float(e.alpha) : __uint_as_float(e.alpha);
-            const float2 v = load_value<VBF>(vals, j);
-            cre = al * v.x;
-            cim = al * v.y;
-            dx = e.dx;
-            dy = e.dy;
+    if (a < b) {
+        // the column bin of the first entry (last k with s_col[k] <= a), then walk the bins
+        int lo = 0, hi = ncb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_col[mid] <= a) lo = mid; else hi = mid - 1;
         }
-        const int cnt = min(GW, b - base);
-        for (int k = 0; k < cnt; ++k) {
-            const float kdx = __shfl_sync(gmask, dx, k, GW);
-            const float kdy = __shfl_sync(gmask, dy, k, GW);
-            const float kre = __shfl_sync(gmask, cre, k, GW);
-            const float kim = __shfl_sync(gmask, cim, k, GW);
-            const int kcx = __shfl_sync(gmask, cxl, k, GW);
-            const int kcy = __shfl_sync(gmask, cyl, k, GW);
-            if (kcx != cur_cx || kcy - yb >= W) {
+        int bin = lo;
+        int bin_end = s_col[bin + 1];
+        cur_cx = bin - (W - 1);
+        // every lane of the group reads the same entry (one broadcast load per group); entries
+        // are prefetched two ahead and values one ahead
+        Entry ec = ent[a];
+        float2 vc = load_value<VBF>(vals, ec.packed & kSampleMask);
+        Entry en = a + 1 < b ? ent[a + 1] : ec;
+        yb = (int)(ec.packed >> kSampleBits) - (W - 1);
+        for (int idx = a; idx < b; ++idx) {
+            const Entry e2 = idx + 2 < b ? ent[idx + 2] : en;
+            const float2 vn = idx + 1 < b ? load_value<VBF>(vals, en.packed & kSampleMask) : vc;
+            const int cyl = (int)(ec.packed >> kSampleBits) - (W - 1);
+            if (idx >= bin_end) {                // the next column bin (empty bins skipped)
                 flush_all();
-                cur_cx = kcx;
-                yb = kcy;
+                do {
+                    ++bin;
+                } while (s_col[bin + 1] <= idx);
+                bin_end = s_col[bin + 1];
+                cur_cx = bin - (W - 1);
+                yb = cyl;
+            } else if (cyl - yb >= W) {
+                flush_all();
+                yb = cyl;
             } else {
-                while (yb < kcy) {               // rows below kcy are final for this column bin
+                while (yb < cyl) {               // rows below cyl are final for this column bin
                     const int col = cur_cx + l;
                     if (lane_tap && col >= 0 && col < Tw && yb >= 0 && yb < Th) {
                         atomicAdd(s_re + yb * LD + col, ar[0]);
@@ -136,15 +149,36 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
                     ++yb;
                 }
             }
-            const float fx = lane_tap ? es32(kdx - (float)l, inv_hw, beta) : 0.0f;
-            const float fy = lane_tap ? es32(kdy - (float)l, inv_hw, beta) : 0.0f;
-            const float xr = kre * fx, xi = kim * fx;
+            const float al = ABF ? bf16_bits_to_float(ec.alpha) : __uint_as_float(ec.alpha);
+            const float fx = lane_tap ? es32(ec.dx - (float)l, inv_hw, beta) : 0.0f;
+            const float fy = lane_tap ? es32(ec.dy - (float)l, inv_hw, beta) : 0.0f;
+            const float ax = al * fx;
+            const float xr = vc.x * ax, xi = vc.y * ax;
+#if FTCG_SPREAD_WINDOW
 #pragma unroll
             for (int r = 0; r < WMAX; ++r) {
                 const float py = __shfl_sync(gmask, fy, r, GW);   // zero for r >= W
                 ar[r] = fmaf(xr, py, ar[r]);
                 ai[r] = fmaf(xi, py, ai[r]);
             }
+#else
+            {
+                const int col = cur_cx + l;
+                const bool okx = lane_tap && col >= 0 && col < Tw;
+#pragma unroll
+                for (int r = 0; r < WMAX; ++r) {
+                    const float py = __shfl_sync(gmask, fy, r, GW);
+                    const int row = cyl + r;
+                    if (okx && r < W && row >= 0 && row < Th) {
+                        atomicAdd(s_re + row * LD + col, xr * py);
+                        atomicAdd(s_im + row * LD + col, xi * py);
+                    }
+                }
+            }
+#endif
+            ec = en;
+            vc = vn;
+            en = e2;
         }
     }
     flush_all();

@@ -59,6 +59,22 @@ SIGNATURES = [
     ("ftcg_plan_entries", _I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ftcg_profile", _I32, [_VP, _I32]),
     ("ftcg_stage_times", _I32, [_VP, _VP, _VP]),
+    ("ftcg_plan_batch", _I32, [ctypes.POINTER(_VP), _I32, _VP, _VP, _VP, _D, _I32,
+                                ctypes.POINTER(Opts), _VP]),
+    ("ftcg_batch_set_weights", _I32, [_VP, _VP, _I32, _VP]),
+    ("ftcg_batch_weights", _I32, [_VP, _VP, _VP]),
+    ("ftcg_adjoint_batch", _I32, [_VP, _VP, _I32, _VP, _VP]),
+    ("ftcg_batch_capture", _I32, [_VP, _VP, _I32, _VP, _VP]),
+    ("ftcg_batch_launch", _I32, [_VP, _VP]),
+    ("ftcg_batch_info", _I32, [_VP, _VP, _VP, _VP]),
+    ("ftcg_batch_destroy", _I32, [_VP]),
+    ("ftcg_features", _I32, [_VP, _VP, _I64, _VP, _VP, _VP]),
+    ("ftcg_mlp_create", _I32, [ctypes.POINTER(_VP), _VP]),
+    ("ftcg_mlp_state", _I32, [_VP, _VP, _VP, _VP, _VP, _I32]),
+    ("ftcg_mlp_predict", _I32, [_VP, _VP, _I64, _VP, _VP]),
+    ("ftcg_mlp_grads", _I32, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    ("ftcg_mlp_train_step", _I32, [_VP, _VP, _VP, _VP, _I64, ctypes.c_float, _VP, _VP]),
+    ("ftcg_mlp_destroy", _I32, [_VP]),
     ("ftcg_adjoint_small_noalloc", _I32, [_VP, _VP, _VP, _I64, _I32, _D, _I32, _VP, _VP]),
     ("ftcg_destroy", _I32, [_VP]),
     ("ftcg_status_string", ctypes.c_char_p, [_I32]),
@@ -231,3 +247,183 @@ class Plan:
         _check(lib().ftcg_plan_entries(self._h, p["tile"], p["cx"], p["cy"], p["sample"],
                                        p["dx"], p["dy"]))
         return arrs
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = t.data_ptr() if t is not None else None
+    return arr
+
+
+class Batch:
+    """Many pings gridded together: ftcg_plan_batch on a list of (M_i, 2) float64 CUDA tensors."""
+
+    def __init__(self, lams, Ns, sigma=2.0, w=8, tile=0, precision=PREC_FP32, stream=None):
+        import torch
+        self.n = len(lams)
+        self.lams = [l.contiguous() for l in lams]
+        for l in self.lams:
+            if l.dtype != torch.float64 or l.dim() != 2 or l.shape[1] != 2 or not l.is_cuda:
+                raise TypeError("every lam must be a CUDA float64 tensor of shape (M, 2)")
+        self.Ms = [int(l.shape[0]) for l in self.lams]
+        self.Ns = [int(n) for n in Ns]
+        self.device = self.lams[0].device
+        M_arr = (ctypes.c_int64 * self.n)(*self.Ms)
+        N_arr = (ctypes.c_int32 * self.n)(*self.Ns)
+        opts = Opts(0, precision, tile, 0)
+        h = ctypes.c_void_p()
+        st = lib().ftcg_plan_batch(ctypes.byref(h), self.n, _ptr_array(self.lams), M_arr, N_arr,
+                                   float(sigma), int(w), ctypes.byref(opts), _stream(stream))
+        self._h = h if h.value else None
+        _check(st)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ftcg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self):
+        tiles = (ctypes.c_int32 * self.n)()
+        ent = ctypes.c_int64()
+        by = ctypes.c_int64()
+        _check(lib().ftcg_batch_info(self._h, ctypes.cast(tiles, ctypes.c_void_p),
+                                     ctypes.byref(ent), ctypes.byref(by)))
+        return list(tiles), ent.value, by.value
+
+    def set_weights(self, alphas, stream=None):
+        import torch
+        if alphas is None:
+            _check(lib().ftcg_batch_set_weights(self._h, None, F64, _stream(stream)))
+            return
+        dt = F64 if alphas[0].dtype == torch.float64 else F32
+        self._alphas = [a.contiguous() for a in alphas]
+        _check(lib().ftcg_batch_set_weights(self._h, _ptr_array(self._alphas), dt,
+                                            _stream(stream)))
+
+    def weights(self, stream=None):
+        import torch
+        outs = [torch.empty(m, dtype=torch.float64, device=self.device) for m in self.Ms]
+        _check(lib().ftcg_batch_weights(self._h, _ptr_array(outs), _stream(stream)))
+        return outs
+
+    def _io(self, values, images):
+        import torch
+        vd = _values_dtype(values[0])
+        if images is None:
+            images = [torch.empty((n, n), dtype=torch.complex64, device=self.device)
+                      for n in self.Ns]
+        self._keep = ([v.contiguous() for v in values], images)
+        return vd, self._keep[0], images
+
+    def adjoint(self, values, images=None, stream=None):
+        vd, vals, images = self._io(values, images)
+        _check(lib().ftcg_adjoint_batch(self._h, _ptr_array(vals), vd, _ptr_array(images),
+                                        _stream(stream)))
+        return images
+
+    def capture(self, values, images=None, stream=None):
+        """Capture the batched adjoint into a CUDA graph bound to these buffers."""
+        vd, vals, images = self._io(values, images)
+        _check(lib().ftcg_batch_capture(self._h, _ptr_array(vals), vd, _ptr_array(images),
+                                        _stream(stream)))
+        return images
+
+    def launch(self, stream=None):
+        _check(lib().ftcg_batch_launch(self._h, _stream(stream)))
+
+
+MLP_PARAMS = 10561
+FEAT_WIDTH = 48
+
+
+def features(lam, aux=None, neighbors=False, stream=None):
+    """kNN features (M x 48 bfloat16) of a CUDA float64 (M, 2) raster; optionally the neighbour
+    indices (M x 16 int32)."""
+    import torch
+    M = int(lam.shape[0])
+    lam = lam.contiguous()
+    out = torch.empty((M, FEAT_WIDTH), dtype=torch.bfloat16, device=lam.device)
+    nb = torch.empty((M, 16), dtype=torch.int32, device=lam.device) if neighbors else None
+    a = aux.contiguous().to(torch.float64) if aux is not None else None
+    _check(lib().ftcg_features(_ptr(lam), _ptr(a), M, _ptr(out), _ptr(nb), _stream(stream)))
+    return (out, nb) if neighbors else out
+
+
+class Mlp:
+    """The weight-predicting network; params: packed FP32 numpy array of MLP_PARAMS values."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters")
+        h = ctypes.c_void_p()
+        _check(lib().ftcg_mlp_create(ctypes.byref(h), p.ctypes.data_as(ctypes.c_void_p)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ftcg_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state(self):
+        P = np.empty(MLP_PARAMS, np.float32)
+        m = np.empty(MLP_PARAMS, np.float32)
+        v = np.empty(MLP_PARAMS, np.float32)
+        step = ctypes.c_int64()
+        _check(lib().ftcg_mlp_state(self._h, P.ctypes.data_as(ctypes.c_void_p),
+                                    m.ctypes.data_as(ctypes.c_void_p),
+                                    v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(step), 0))
+        return {"params": P, "m": m, "v": v, "step": step.value}
+
+    def load_state(self, st):
+        P = np.ascontiguousarray(st["params"], np.float32)
+        m = np.ascontiguousarray(st["m"], np.float32)
+        v = np.ascontiguousarray(st["v"], np.float32)
+        step = ctypes.c_int64(int(st["step"]))
+        _check(lib().ftcg_mlp_state(self._h, P.ctypes.data_as(ctypes.c_void_p),
+                                    m.ctypes.data_as(ctypes.c_void_p),
+                                    v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(step), 1))
+
+    def predict(self, feats, out=None, stream=None):
+        import torch
+        M = int(feats.shape[0])
+        if out is None:
+            out = torch.empty(M, dtype=torch.float64, device=feats.device)
+        _check(lib().ftcg_mlp_predict(self._h, _ptr(feats), M, _ptr(out), _stream(stream)))
+        return out
+
+    def grads(self, feats, target, index=None, stream=None):
+        B = int(index.shape[0]) if index is not None else int(feats.shape[0])
+        g = np.empty(MLP_PARAMS, np.float32)
+        loss = ctypes.c_float()
+        _check(lib().ftcg_mlp_grads(self._h, _ptr(feats), _ptr(target), _ptr(index), B,
+                                    g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss),
+                                    _stream(stream)))
+        return g, loss.value
+
+    def train_step(self, feats, target, index, lr, want_loss=False, stream=None):
+        loss = ctypes.c_float()
+        _check(lib().ftcg_mlp_train_step(self._h, _ptr(feats), _ptr(target), _ptr(index),
+                                         int(index.shape[0]), float(lr),
+                                         ctypes.byref(loss) if want_loss else None,
+                                         _stream(stream)))
+        return loss.value if want_loss else None

@@ -43,6 +43,7 @@ class Ping:
     seed: int
     name: str
     bright_pixels: np.ndarray | None = None   # B x 2 int (px, py) pixel offsets of bright targets
+    kr: np.ndarray | None = None              # M range wavenumbers |k| (rad/m)
 
     @property
     def M(self) -> int:
@@ -135,7 +136,7 @@ def tiny(seed=BASE_SEED + 0):
     L = 2.0
     lam = baseband(kx, ky, L)
     scene = point_scene(rng, 5, L, half_extent=1.0)
-    return Ping(lam, 64, 2.0, 6, scene, 30.0, seed, "tiny-4096")
+    return Ping(lam, 64, 2.0, 6, scene, 30.0, seed, "tiny-4096", kr=np.hypot(kx, ky))
 
 
 def large_ping(seed=BASE_SEED + 1, n_kr=2048, n_theta=1024, N=1024, L=10.0, w=8):
@@ -145,7 +146,8 @@ def large_ping(seed=BASE_SEED + 1, n_kr=2048, n_theta=1024, N=1024, L=10.0, w=8)
     kx, ky = polar_raster(rng, n_kr, n_theta, 30.0, kr_scale=1.01, theta_jitter_deg=0.02)
     lam = baseband(kx, ky, L)
     scene, bp = speckle_scene(rng, 2000, 20, L, N)
-    return Ping(lam, N, 2.0, w, scene, None, seed, f"large-ping-{n_kr * n_theta}", bp)
+    return Ping(lam, N, 2.0, w, scene, None, seed, f"large-ping-{n_kr * n_theta}", bp,
+                np.hypot(kx, ky))
 
 
 def precision_sweep(seed=BASE_SEED + 2):
@@ -172,7 +174,7 @@ def batch_ping(b, seed_base=BASE_SEED + 3):
     L = 0.9 * 2 * np.pi * N / kspan
     lam = baseband(kx, ky, L)
     scene, bp = speckle_scene(rng, 500, 5, L, N)
-    return Ping(lam, N, 2.0, 8, scene, None, seed, f"batch-ping-{b}", bp)
+    return Ping(lam, N, 2.0, 8, scene, None, seed, f"batch-ping-{b}", bp, np.hypot(kx, ky))
 
 
 def random_geometry(rng, N_choices=(256, 512), M_range=(2_000, 20_000)):

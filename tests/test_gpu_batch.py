@@ -1,0 +1,110 @@
+"""Batched pings through the C ABI: one persistent spreading launch, batched FFTs per grid side,
+one window-division launch; with and without CUDA-graph capture. Every image is compared with
+the FP64 oracle (and with the single-ping path) element by element."""
+import numpy as np
+import pytest
+
+import sasgen
+from oracle import ftcg_oracle as O
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def F():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1706_08575_gb300 as pkg
+    return pkg
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def small_batch(seed=0):
+    rng = np.random.default_rng(seed)
+    cases = []
+    for i, N in enumerate([32, 64, 48, 64, 32, 96, 40]):
+        M = int(rng.integers(200, 6000)) if i != 4 else 0
+        lam, v = sasgen.random_case(seed * 100 + i, M, N, 2.0, 8, spread=1.5 * N)
+        alpha = rng.uniform(0.3, 1.7, M)
+        cases.append((lam, v.astype(np.complex64), alpha, N))
+    return cases
+
+
+def test_batch_vs_oracle_and_single(F):
+    cases = small_batch(1)
+    lams = [dev(c[0]) for c in cases]
+    vals = [dev(c[1]) for c in cases]
+    alphas = [dev(c[2]) for c in cases]
+    with F.Batch(lams, [c[3] for c in cases], 2.0, 8) as b:
+        tiles, entries, _ = b.info()
+        assert set(tiles) <= {32, 64}
+        b.set_weights(alphas)
+        imgs = [x.cpu().numpy() for x in b.adjoint(vals)]
+    for (lam, v, a, N), img in zip(cases, imgs):
+        ref = O.adjoint(lam, a.astype(np.float32) * v.astype(np.complex128), N, 2.0, 8)
+        if lam.shape[0] == 0:
+            assert np.count_nonzero(img) == 0
+            continue
+        assert O.rel_l2(img, ref) < TOL
+        with F.Plan(dev(lam), N, 2.0, 8) as p:
+            p.set_weights(dev(a))
+            single = p.adjoint(dev(v)).cpu().numpy()
+        assert O.rel_l2(img, single) < 1e-6
+
+
+def test_batch_graph_replay(F):
+    import torch
+    cases = [c for c in small_batch(2) if c[0].shape[0] > 0]
+    lams = [dev(c[0]) for c in cases]
+    vals = [dev(c[1]) for c in cases]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s), F.Batch(lams, [c[3] for c in cases], 2.0, 8, tile=32) as b:
+        imgs = b.capture(vals)
+        for x in imgs:
+            x.zero_()
+        b.launch()
+        b.launch()
+        s.synchronize()
+        got = [x.cpu().numpy() for x in imgs]
+    for (lam, v, a, N), img in zip(cases, got):
+        ref = O.adjoint(lam, v.astype(np.complex128), N, 2.0, 8)
+        assert O.rel_l2(img, ref) < TOL
+
+
+def test_batch_bf16_values_and_weights(F):
+    import torch
+    cases = [c for c in small_batch(3) if c[0].shape[0] > 0][:4]
+    lams = [dev(c[0]) for c in cases]
+    vb = [torch.view_as_real(torch.from_numpy(c[1])).to(torch.bfloat16).cuda() for c in cases]
+    with F.Batch(lams, [c[3] for c in cases], 2.0, 8, precision=F.PREC_BF16) as b:
+        alphas = b.weights()
+        imgs = [x.cpu().numpy() for x in b.adjoint(vb)]
+        alphas = [a.cpu().numpy() for a in alphas]
+    for (lam, v, _, N), img, a, vbt in zip(cases, imgs, alphas, vb):
+        ab, _ = O.weights_brute(lam, N)
+        assert np.max(np.abs(a - ab) / ab) < 1e-9
+        vr = vbt.cpu().to(torch.float64).numpy()
+        vr = vr[:, 0] + 1j * vr[:, 1]
+        a_r = torch.from_numpy(ab.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+        ref = O.adjoint(lam, a_r * vr, N, 2.0, 8)
+        assert O.rel_l2(img, ref) < TOL
+
+
+def test_batch_of_sas_pings_sampled(F):
+    """Eight pings of the uneven SAS batch recipe (20k-400k samples, N in {256, 512, 1024}):
+    sampled pixels against the oracle one by one."""
+    pings = [sasgen.batch_ping(b) for b in range(8)]
+    vals = [sasgen.values_for(p, device="cuda").astype(np.complex64) for p in pings]
+    with F.Batch([dev(p.lam) for p in pings], [p.N for p in pings], 2.0, 8) as b:
+        imgs = [x.cpu().numpy() for x in b.adjoint([dev(v) for v in vals])]
+    rng = np.random.default_rng(4)
+    for p, v, img in zip(pings, vals, imgs):
+        pix = np.concatenate([rng.integers(-p.N // 2, p.N // 2, size=(6, 2)), p.bright_pixels])
+        ref = O.adjoint_pixels(p.lam, v.astype(np.complex128), p.N, 2.0, 8, pix)
+        got = img[pix[:, 1] + p.N // 2, pix[:, 0] + p.N // 2]
+        assert O.rel_l2(got, ref) < TOL

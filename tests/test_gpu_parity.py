@@ -87,6 +87,16 @@ def _run_adjoint(F, lam, v, N, sigma, w, alpha=None, T=0):
         return img.cpu().numpy(), grid.cpu().numpy()
 
 
+def image_tol(N, sigma, w):
+    """FP32 bound of an image: 1e-5, or 5e-8 A when the window division amplifies FP32 grid
+    rounding by A = rms over pixels of r(p_x)^2 r(p_y)^2 / r(0)^4 (r = 1/phi^): A = 2.4 at
+    sigma = 2, w = 8, but 413 at sigma = 1.5, w = 16, where the image edge is divided by a window
+    transform 83 times smaller than at the centre."""
+    r = O.deapod_factors(N, sigma, w)
+    A = float(np.sqrt(np.mean(np.multiply.outer(r, r) ** 2)) / r[N // 2] ** 2)
+    return max(TOL, 5e-8 * A)
+
+
 @pytest.mark.parametrize("M,N,sigma,w,spread,T", [
     (4096, 64, 2.0, 6, 150, 0), (3000, 50, 2.0, 8, 150, 32), (2000, 40, 1.25, 5, 40, 32),
     (5000, 96, 2.0, 7, 96, 64), (3000, 40, 2.0, 10, 120, 32), (1500, 32, 2.0, 13, 32, 32),
@@ -98,7 +108,7 @@ def test_adjoint_and_spread_vs_oracle(F, M, N, sigma, w, spread, T):
     vc = c64(v).astype(np.complex128)
     img, grid = _run_adjoint(F, lam, v, N, sigma, w, alpha, T)
     ref = O.adjoint(lam, alpha.astype(np.float32) * vc, N, sigma, w)
-    assert O.rel_l2(img, ref) < TOL
+    assert O.rel_l2(img, ref) < image_tol(N, sigma, w)
     gref = O.spread(lam, alpha.astype(np.float32) * vc, N, sigma, w)
     assert O.rel_l2(grid, gref) < TOL
 

@@ -63,6 +63,15 @@ def test_bf16_storage_parity_and_error(F, M, N, w, spread):
     assert e < BF16_BOUND, e
 
 
+def test_bf16_plan_default_weights(F):
+    """A BF16 plan without installed weights grids with alpha = 1."""
+    lam, v = sasgen.random_case(75, 2000, 32, 2.0, 8, 32)
+    vc = v.astype(np.complex64)
+    with F.Plan(dev(lam), 32, 2.0, 8, precision=F.PREC_BF16) as p:
+        img = p.adjoint(dev(vc)).cpu().numpy()
+    assert O.rel_l2(img, O.adjoint(lam, vc.astype(np.complex128), 32, 2.0, 8)) < TOL
+
+
 def test_mixed_storage_modes(F):
     """BF16 values with FP32 weights, and FP32 values with BF16 weights."""
     lam, v = sasgen.random_case(80, 3000, 64, 2.0, 8, 64)
