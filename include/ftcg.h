@@ -59,20 +59,29 @@ enum { FTCG_VALUES_C64 = 0, FTCG_VALUES_BF16X2 = 1 };
 enum { FTCG_WEIGHTS_F64 = 0, FTCG_WEIGHTS_F32 = 1 };
 /* Plan precision: how the per-sample weight is stored next to the sorted coordinates. */
 enum { FTCG_PREC_FP32 = 0, FTCG_PREC_BF16 = 1 };
+/* How footprints that cross a tile edge are handled by the spreading kernel:
+ *   DUPLICATE: a sample is listed in every tile its footprint touches; each tile keeps its cells.
+ *   HALO:      a sample is listed once, in the tile of its first tap; the tile accumulates a
+ *              (tile + w - 1)^2 padded block, stores its own cells and hands the overflow strips to
+ *              a second kernel that adds them to the neighbouring tiles' cells.
+ * AUTO lets the autotuner choose, together with the tile side. */
+enum { FTCG_LAYOUT_AUTO = 0, FTCG_LAYOUT_DUPLICATE = 1, FTCG_LAYOUT_HALO = 2 };
 
 typedef struct {
     int32_t kernel;        /* 0 = ES (the only window of this build)                            */
     int32_t precision;     /* FTCG_PREC_FP32 (default) or FTCG_PREC_BF16 weight storage        */
     int32_t tile;          /* fine-grid tile side of the spreading kernel: 0 = auto, 32 or 64 */
     int32_t weight_width;  /* window width of the FP64 weight construction: 0 = 12, else 4..16 */
-    int32_t reserved[4];   /* must be zero                                                      */
+    int32_t layout;        /* FTCG_LAYOUT_AUTO (default), _DUPLICATE or _HALO                  */
+    int32_t reserved[3];   /* must be zero                                                      */
 } ftcg_opts_t;
 
 typedef struct {
     int64_t M;             /* samples                                                           */
     int32_t N, G, w, tile; /* image side, grid side, window width, tile side                    */
     int32_t tiles_x;       /* tiles per grid row (tiles are tile x tile, the last one ragged)    */
-    int64_t entries;       /* (tile, sample) pairs after halo duplication                      */
+    int32_t layout;        /* FTCG_LAYOUT_DUPLICATE or FTCG_LAYOUT_HALO                         */
+    int64_t entries;       /* sorted (tile, sample) entries                                     */
     double beta;           /* window shape parameter                                            */
     int64_t device_bytes;  /* device memory the plan holds                                      */
 } ftcg_plan_info_t;
@@ -161,7 +170,7 @@ ftcg_status_t ftcg_check(ftcg_plan_t plan);
 
 /* Copy the plan's sorted (tile, sample) entries to host memory, for inspection and tests.
  * h_tile, h_cx, h_cy: int32 tile index and local first-tap cell of each entry (cx, cy in
- * [-(w-1), tile-1]); h_sample: int32 sample index; h_dx, h_dy: float32 offset of the sample from
+ * [-(w-1), tile-1] with FTCG_LAYOUT_DUPLICATE, in [0, tile-1] with FTCG_LAYOUT_HALO); h_sample: int32 sample index; h_dx, h_dy: float32 offset of the sample from
  * its first tap, sigma lambda - ceil(sigma lambda - w/2). Each array holds info.entries elements.
  * Any pointer may be NULL. Synchronous. */
 ftcg_status_t ftcg_plan_entries(ftcg_plan_t plan, int32_t* h_tile, int32_t* h_cx, int32_t* h_cy,

@@ -73,8 +73,8 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
     FTCG_CK(cudaMalloc(&p->deapod, (size_t)p->N * sizeof(double)));
     bytes += (int64_t)p->N * sizeof(double);
     FTCG_TRY(window_factors(p->deapod, p->N, p->G, p->win, s));
-    FTCG_TRY(build_binning(p->bin, p->lambda, M, p->sigma, p->G, p->opts.tile, p->w, p->status,
-                           p->samp, s, &bytes));
+    FTCG_TRY(build_binning(p->bin, p->lambda, M, p->sigma, p->G, p->opts.tile, p->w,
+                           p->opts.layout == FTCG_LAYOUT_HALO, p->status, p->samp, s, &bytes));
     if (own_grid) {
         FTCG_CK(cudaMalloc(&p->grid, (size_t)p->G * p->G * sizeof(float2)));
         bytes += (int64_t)p->G * p->G * sizeof(float2);
@@ -108,8 +108,10 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
         return invalid("ftcg_plan: sigma * N must be an even integer");
     if (G < 2 * w) return invalid("ftcg_plan: the grid must hold at least two windows (G >= 2 w)");
     ftcg_opts_t& o = *po;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) return invalid("ftcg_plan: opts.reserved must be zero");
+    if (o.layout < FTCG_LAYOUT_AUTO || o.layout > FTCG_LAYOUT_HALO)
+        return invalid("ftcg_plan: opts.layout must be 0, 1 or 2");
     if (o.kernel != 0) {
         set_error("ftcg_plan: only the ES window (kernel 0) is built");
         return FTCG_ERR_NOT_SUPPORTED;
@@ -198,8 +200,9 @@ ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int
     p->win = Window{w, es_beta(w, sigma)};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
-    if (o.tile == 0) {
-        ftcg_status_t tst = tune_tile(d_lambda, M, N, sigma, w, o, s, &p->opts.tile);
+    if (o.tile == 0 || o.layout == FTCG_LAYOUT_AUTO) {
+        ftcg_status_t tst =
+            tune_tile(d_lambda, M, N, sigma, w, o, s, &p->opts.tile, &p->opts.layout);
         if (tst != FTCG_SUCCESS) {
             delete p;
             return tst;
@@ -224,6 +227,7 @@ ftcg_status_t ftcg_plan_info(ftcg_plan_t plan, ftcg_plan_info_t* info) {
     info->w = p->w;
     info->tile = p->bin.T;
     info->tiles_x = p->bin.ntx;
+    info->layout = p->bin.halo ? FTCG_LAYOUT_HALO : FTCG_LAYOUT_DUPLICATE;
     info->entries = p->bin.n_entries;
     info->beta = p->win.beta;
     info->device_bytes = p->device_bytes;

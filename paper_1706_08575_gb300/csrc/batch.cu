@@ -31,7 +31,9 @@ struct PingDesc {
     float2* grid;
     float2* img;
     const double* deapod;
+    float2* halo_buf;
     int G, ntx, T, N;
+    int halo, halo_cells, ncb, W;
 };
 
 template <int GW, int WT, bool VBF, bool ABF>
@@ -48,13 +50,36 @@ __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
         if (it >= nitems) return;
         const int2 pt = items[it];
         const PingDesc d = desc[pt.x];
-        if (d.T == 64)
-            tile::spread_tile<GW, WT, 64, VBF, ABF>(d.ent, d.colptr, d.vals, d.grid, d.G, d.ntx,
-                                                    Wrt, beta, inv_hw, pt.y, smem);
-        else
-            tile::spread_tile<GW, WT, 32, VBF, ABF>(d.ent, d.colptr, d.vals, d.grid, d.G, d.ntx,
-                                                    Wrt, beta, inv_hw, pt.y, smem);
+        if (d.halo) {
+            if (d.T == 64)
+                tile::spread_tile<GW, WT, 64, VBF, ABF, true>(d.ent, d.colptr, d.vals, d.grid, d.G,
+                                                              d.ntx, Wrt, beta, inv_hw, pt.y, smem,
+                                                              d.halo_buf, d.halo_cells);
+            else
+                tile::spread_tile<GW, WT, 32, VBF, ABF, true>(d.ent, d.colptr, d.vals, d.grid, d.G,
+                                                              d.ntx, Wrt, beta, inv_hw, pt.y, smem,
+                                                              d.halo_buf, d.halo_cells);
+        } else {
+            if (d.T == 64)
+                tile::spread_tile<GW, WT, 64, VBF, ABF, false>(d.ent, d.colptr, d.vals, d.grid,
+                                                               d.G, d.ntx, Wrt, beta, inv_hw, pt.y,
+                                                               smem, nullptr, 0);
+            else
+                tile::spread_tile<GW, WT, 32, VBF, ABF, false>(d.ent, d.colptr, d.vals, d.grid,
+                                                               d.G, d.ntx, Wrt, beta, inv_hw, pt.y,
+                                                               smem, nullptr, 0);
+        }
     }
+}
+
+// the overflow strips of every halo-layout (ping, tile) item, after the spreading launch
+__global__ void __launch_bounds__(256)
+    k_halo_add_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items) {
+    const int2 pt = items[blockIdx.x];
+    const PingDesc d = desc[pt.x];
+    if (!d.halo) return;
+    tile::halo_add_tile(d.halo_buf, d.halo_cells, d.colptr, d.ncb, d.grid, d.G, d.T, d.W, d.ntx,
+                        pt.y);
 }
 
 __global__ void k_deapod_batch(const PingDesc* __restrict__ desc) {
@@ -71,22 +96,27 @@ __global__ void k_deapod_batch(const PingDesc* __restrict__ desc) {
     d.img[(int64_t)iy * N + ix] = make_float2(h.x * f, h.y * f);
 }
 
-size_t spread_smem(int T, int W) {
-    return (size_t)(2 * T * (T + 1)) * sizeof(float) + (size_t)(T + W) * sizeof(int);
+template <int WMAX>
+size_t spread_smem() {
+    return std::max(std::max(tile::tile_smem_bytes<64, WMAX, true>(),
+                             tile::tile_smem_bytes<64, WMAX, false>()),
+                    tile::tile_smem_bytes<32, WMAX, true>());
 }
 
 // ---- autotuner ----------------------------------------------------------------------------
 struct TuneKey {
-    int G, w, prec, bucket;
+    int G, w, prec, bucket, tile, layout;   // tile / layout: the caller's fixed choices (0 = free)
     bool operator<(const TuneKey& o) const {
         if (G != o.G) return G < o.G;
         if (w != o.w) return w < o.w;
         if (prec != o.prec) return prec < o.prec;
-        return bucket < o.bucket;
+        if (bucket != o.bucket) return bucket < o.bucket;
+        if (tile != o.tile) return tile < o.tile;
+        return layout < o.layout;
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune;
+std::map<TuneKey, std::pair<int, int>> g_tune;
 
 int density_bucket(int64_t M, int G) {
     const double d = (double)M / ((double)G * G);
@@ -113,50 +143,67 @@ ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaSt
 }  // namespace
 
 ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
-                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out) {
+                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out) {
     const int G = (int)std::llround(sigma * N);
-    const TuneKey key{G, w, opts.precision, density_bucket(M, G)};
+    const TuneKey key{G, w, opts.precision, density_bucket(M, G), opts.tile, opts.layout};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            *T_out = it->second;
+            *T_out = it->second.first;
+            *layout_out = it->second.second;
             return FTCG_SUCCESS;
         }
+    }
+    std::vector<int> tiles, layouts;
+    if (opts.tile) tiles.push_back(opts.tile); else tiles = {32, 64};
+    if (opts.layout) layouts.push_back(opts.layout);
+    else layouts = {FTCG_LAYOUT_DUPLICATE, FTCG_LAYOUT_HALO};
+    if (tiles.size() * layouts.size() == 1) {
+        *T_out = tiles[0];
+        *layout_out = layouts[0];
+        return FTCG_SUCCESS;
     }
     void* zeros = nullptr;
     float2* grid = nullptr;
     FTCG_CK(cudaMalloc(&zeros, (size_t)std::max<int64_t>(M, 1) * sizeof(float2)));
     FTCG_CK(cudaMemsetAsync(zeros, 0, (size_t)std::max<int64_t>(M, 1) * sizeof(float2), s));
     FTCG_CK(cudaMalloc(&grid, (size_t)G * G * sizeof(float2)));
-    int best = 64;
+    int best_T = tiles[0], best_L = layouts[0];
     float best_ms = 1e30f;
     ftcg_status_t st = FTCG_SUCCESS;
-    for (int T : {32, 64}) {
-        Plan* p = new (std::nothrow) Plan();
-        if (!p) { st = FTCG_ERR_OUT_OF_MEMORY; break; }
-        p->M = M; p->N = N; p->G = G; p->w = w; p->sigma = sigma;
-        p->opts = opts;
-        p->opts.tile = T;
-        p->win = Window{w, es_beta(w, sigma)};
-        st = make_plan(p, d_lambda, s, false);
-        float ms = 1e30f;
-        if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC) st = time_spread(*p, zeros, grid, s, &ms);
-        release_plan(p);
-        if (st != FTCG_SUCCESS) break;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = T;
+    for (int T : tiles) {
+        for (int layout : layouts) {
+            Plan* p = new (std::nothrow) Plan();
+            if (!p) { st = FTCG_ERR_OUT_OF_MEMORY; break; }
+            p->M = M; p->N = N; p->G = G; p->w = w; p->sigma = sigma;
+            p->opts = opts;
+            p->opts.tile = T;
+            p->opts.layout = layout;
+            p->win = Window{w, es_beta(w, sigma)};
+            st = make_plan(p, d_lambda, s, false);
+            float ms = 1e30f;
+            if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC)
+                st = time_spread(*p, zeros, grid, s, &ms);
+            release_plan(p);
+            if (st != FTCG_SUCCESS) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_T = T;
+                best_L = layout;
+            }
         }
+        if (st != FTCG_SUCCESS) break;
     }
     cudaFree(zeros);
     cudaFree(grid);
     if (st != FTCG_SUCCESS) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = best;
+        g_tune[key] = {best_T, best_L};
     }
-    *T_out = best;
+    *T_out = best_T;
+    *layout_out = best_L;
     return FTCG_SUCCESS;
 }
 
@@ -181,6 +228,7 @@ struct Batch {
     int nitems = 0;
     int* d_counter = nullptr;
     int max_N = 0;
+    bool any_halo = false;
     int persistent_ctas = 0;
     int64_t entries = 0, device_bytes = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -206,7 +254,7 @@ void release_batch(Batch* b) {
 template <int GW, int WT, bool VBF, bool ABF>
 ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
     auto kern = k_spread_batch<GW, WT, VBF, ABF>;
-    const size_t smem = spread_smem(64, b.w);
+    const size_t smem = spread_smem<(WT > 0 ? WT : GW)>();
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
@@ -254,6 +302,10 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
         else if (abf) FTCG_TRY((launch_batch_spread_w<false, true>(b, s)));
         else FTCG_TRY((launch_batch_spread_w<false, false>(b, s)));
     }
+    if (b.nitems > 0 && b.any_halo) {
+        k_halo_add_batch<<<b.nitems, 256, 0, s>>>(b.d_desc, b.d_items);
+        FTCG_CK(cudaGetLastError());
+    }
     for (auto& c : b.classes) {
         FTCG_CKFFT(cufftSetStream(c.fft, s));
         FTCG_CKFFT(cufftExecC2C(c.fft, reinterpret_cast<cufftComplex*>(c.grids),
@@ -271,8 +323,9 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
     for (int i = 0; i < b.n; ++i) {
         const int G = (int)std::llround(b.sigma * N[i]);
         Gs[i] = G;
-        int T = b.opts.tile;
-        if (T == 0) FTCG_TRY(tune_tile(d_lambda[i], M[i], N[i], b.sigma, b.w, b.opts, s, &T));
+        int T = b.opts.tile, layout = b.opts.layout;
+        if (T == 0 || layout == 0)
+            FTCG_TRY(tune_tile(d_lambda[i], M[i], N[i], b.sigma, b.w, b.opts, s, &T, &layout));
         Plan* p = new (std::nothrow) Plan();
         if (!p) {
             set_error("ftcg_plan_batch: host allocation failed");
@@ -281,6 +334,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         p->M = M[i]; p->N = N[i]; p->G = G; p->w = b.w; p->sigma = b.sigma;
         p->opts = b.opts;
         p->opts.tile = T;
+        p->opts.layout = layout;
         p->win = Window{b.w, es_beta(b.w, b.sigma)};
         b.pings.push_back(p);
         ftcg_status_t st = make_plan(p, d_lambda[i], s, false);
@@ -336,6 +390,12 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         d.ntx = bn.ntx;
         d.T = bn.T;
         d.N = p->N;
+        d.halo = bn.halo ? 1 : 0;
+        d.halo_buf = bn.halo_buf;
+        d.halo_cells = bn.halo_cells;
+        d.ncb = bn.ncb;
+        d.W = bn.W;
+        b.any_halo = b.any_halo || bn.halo;
         std::vector<int> cp((size_t)bn.ntiles * bn.ncb + 1);
         FTCG_CK(cudaMemcpy(cp.data(), bn.colptr, cp.size() * sizeof(int), cudaMemcpyDeviceToHost));
         for (int t = 0; t < bn.ntiles; ++t)

@@ -79,6 +79,9 @@ struct Binning {
     Entry* ent = nullptr;               // n_entries, sorted by (tile, column bin, row)
     int* colptr = nullptr;              // ntiles * ncb + 1 start offsets
     int* tile_order = nullptr;          // tiles by decreasing entry count (launch order)
+    bool halo = false;                  // FTCG_LAYOUT_HALO: one entry per sample + halo strips
+    int halo_cells = 0;                 // halo cells per tile
+    float2* halo_buf = nullptr;         // ntiles * halo_cells overflow values (halo layout)
 };
 
 struct Plan {
@@ -111,7 +114,7 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
 ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool own_grid);
 // batch.cu: the tile-side autotuner (cached per grid side, w, precision and density bucket).
 ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
-                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out);
+                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out);
 void release_plan(Plan* p);
 
 // ---------------------------------------------------------------------------------------------
@@ -119,7 +122,7 @@ void release_plan(Plan* p);
 // ---------------------------------------------------------------------------------------------
 // plan.cu
 ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, double scale,
-                            int G, int T, int W, unsigned* d_status, int4* d_samp,
+                            int G, int T, int W, bool halo, unsigned* d_status, int4* d_samp,
                             cudaStream_t s, int64_t* bytes);
 void free_binning(Binning& b);
 ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStream_t s);

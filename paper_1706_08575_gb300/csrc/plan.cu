@@ -60,9 +60,15 @@ struct Runs {
     int local[3];   // local column of tap 0 of this run's entry, in [-(w-1), T-1]
 };
 
-__device__ __forceinline__ Runs axis_runs(int cw, int G, int T, int W) {
+__device__ __forceinline__ Runs axis_runs(int cw, int G, int T, int W, bool halo) {
     Runs r;
     r.n = 0;
+    if (halo) {                       // listed once, in the tile of the first tap
+        r.n = 1;
+        r.tile[0] = cw / T;
+        r.local[0] = cw - r.tile[0] * T;
+        return r;
+    }
     for (int t = 0; t < W; ++t) {
         int col = cw + t;
         if (col >= G) col -= G;
@@ -79,7 +85,7 @@ __device__ __forceinline__ Runs axis_runs(int cw, int G, int T, int W) {
 }
 
 __global__ void k_bin_count(const double* __restrict__ lam, int64_t M, double scale, int G, int T,
-                            int W, int ntx, int ncb, int* __restrict__ hist,
+                            int W, int ntx, int ncb, bool halo, int* __restrict__ hist,
                             unsigned* __restrict__ status, int4* __restrict__ samp) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -94,8 +100,8 @@ __global__ void k_bin_count(const double* __restrict__ lam, int64_t M, double sc
         if (samp)
             samp[j] = make_int4(cxw, cyw, __float_as_int(__double2float_rn(ox.d)),
                                 __float_as_int(__double2float_rn(oy.d)));
-        Runs rx = axis_runs(cxw, G, T, W);
-        Runs ry = axis_runs(cyw, G, T, W);
+        Runs rx = axis_runs(cxw, G, T, W, halo);
+        Runs ry = axis_runs(cyw, G, T, W, halo);
         for (int a = 0; a < ry.n; ++a)
             for (int b = 0; b < rx.n; ++b) {
                 int64_t tile = (int64_t)ry.tile[a] * ntx + rx.tile[b];
@@ -106,8 +112,8 @@ __global__ void k_bin_count(const double* __restrict__ lam, int64_t M, double sc
 }
 
 __global__ void k_bin_scatter(const double* __restrict__ lam, int64_t M, double scale, int G,
-                              int T, int W, int ntx, int ncb, int* __restrict__ cursor,
-                              Entry* __restrict__ ent) {
+                              int T, int W, int ntx, int ncb, bool halo,
+                              int* __restrict__ cursor, Entry* __restrict__ ent) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
          j += (int64_t)gridDim.x * blockDim.x) {
         TapOrigin ox = tap_origin(lam[2 * j], scale, W);
@@ -118,8 +124,8 @@ __global__ void k_bin_scatter(const double* __restrict__ lam, int64_t M, double 
         e.dx = __double2float_rn(ox.d);
         e.dy = __double2float_rn(oy.d);
         e.alpha = __float_as_uint(1.0f);
-        Runs rx = axis_runs(cxw, G, T, W);
-        Runs ry = axis_runs(cyw, G, T, W);
+        Runs rx = axis_runs(cxw, G, T, W, halo);
+        Runs ry = axis_runs(cyw, G, T, W, halo);
         for (int a = 0; a < ry.n; ++a)
             for (int b = 0; b < rx.n; ++b) {
                 int64_t tile = (int64_t)ry.tile[a] * ntx + rx.tile[b];
@@ -247,6 +253,8 @@ void free_binning(Binning& b) {
     if (b.ent) cudaFree(b.ent);
     if (b.colptr) cudaFree(b.colptr);
     if (b.tile_order) cudaFree(b.tile_order);
+    if (b.halo_buf) cudaFree(b.halo_buf);
+    b.halo_buf = nullptr;
     b.ent = nullptr;
     b.colptr = nullptr;
     b.tile_order = nullptr;
@@ -274,11 +282,12 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
 }
 
 ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, double scale, int G,
-                            int T, int W, unsigned* d_status, int4* d_samp, cudaStream_t s,
-                            int64_t* bytes) {
+                            int T, int W, bool halo, unsigned* d_status, int4* d_samp,
+                            cudaStream_t s, int64_t* bytes) {
     b.G = G;
     b.T = T;
     b.W = W;
+    b.halo = halo;
     b.ntx = (G + T - 1) / T;
     b.ntiles = b.ntx * b.ntx;
     b.ncb = T + W - 1;
@@ -296,8 +305,8 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
     FTCG_CK(cudaMallocAsync(&hist, nkeys * sizeof(int), s));
     FTCG_CK(cudaMallocAsync(&offs, nkeys * sizeof(int), s));
     FTCG_CK(cudaMemsetAsync(hist, 0, nkeys * sizeof(int), s));
-    k_bin_count<<<grid_for(M), kThreads, 0, s>>>(d_lambda, M, scale, G, T, W, b.ntx, b.ncb, hist,
-                                                 d_status, d_samp);
+    k_bin_count<<<grid_for(M), kThreads, 0, s>>>(d_lambda, M, scale, G, T, W, b.ntx, b.ncb, halo,
+                                                 hist, d_status, d_samp);
     FTCG_CK(cudaGetLastError());
     FTCG_TRY(exclusive_scan_i32(hist, offs, nkeys, s));
     int last_off = 0, last_cnt = 0;
@@ -312,11 +321,18 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
         FTCG_CK(cudaMalloc(&b.ent, (size_t)total * sizeof(Entry)));
         *bytes += (int64_t)total * sizeof(Entry);
         k_bin_scatter<<<grid_for(M), kThreads, 0, s>>>(d_lambda, M, scale, G, T, W, b.ntx, b.ncb,
-                                                       offs, b.ent);
+                                                       halo, offs, b.ent);
         FTCG_CK(cudaGetLastError());
     }
     FTCG_CK(cudaFreeAsync(hist, s));
     FTCG_CK(cudaFreeAsync(offs, s));
+    if (halo) {
+        // per tile: the right strip (T + w - 1) x (w - 1) and the bottom strip (w - 1) x T
+        b.halo_cells = (T + W - 1) * (W - 1) + (W - 1) * T;
+        const size_t hb = (size_t)b.ntiles * b.halo_cells * sizeof(float2);
+        FTCG_CK(cudaMalloc(&b.halo_buf, hb));
+        *bytes += (int64_t)hb;
+    }
     return order_tiles(b, s, bytes);
 }
 

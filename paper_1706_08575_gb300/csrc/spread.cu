@@ -23,49 +23,67 @@ namespace {
 using tile::kSpreadThreads;
 using tile::es32;
 
-template <int GW, int WT, int T, bool VBF, bool ABF>
+template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO>
 __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
     k_spread(const Entry* __restrict__ ent, const int* __restrict__ colptr,
              const int* __restrict__ tile_order, const void* __restrict__ vals,
-             float2* __restrict__ grid, int G, int ntx, int Wrt, float beta, float inv_hw) {
+             float2* __restrict__ grid, int G, int ntx, int Wrt, float beta, float inv_hw,
+             float2* __restrict__ halo_buf, int halo_cells) {
     extern __shared__ float smem[];
     const int t = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
-    tile::spread_tile<GW, WT, T, VBF, ABF>(ent, colptr, vals, grid, G, ntx, Wrt, beta, inv_hw, t,
-                                           smem);
+    tile::spread_tile<GW, WT, T, VBF, ABF, HALO>(ent, colptr, vals, grid, G, ntx, Wrt, beta,
+                                                 inv_hw, t, smem, halo_buf, halo_cells);
 }
 
-template <int GW, int WT, int T, bool VBF, bool ABF>
+__global__ void __launch_bounds__(256)
+    k_halo_add(const float2* __restrict__ halo_buf, int halo_cells, const int* __restrict__ colptr,
+               int ncb, float2* __restrict__ grid, int G, int T, int W, int ntx) {
+    tile::halo_add_tile(halo_buf, halo_cells, colptr, ncb, grid, G, T, W, ntx, blockIdx.x);
+}
+
+template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO>
 ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
     const Binning& b = p.bin;
-    const size_t smem = (size_t)(2 * T * (T + 1)) * sizeof(float) + (size_t)(b.ncb + 1) * sizeof(int);
-    auto kern = k_spread<GW, WT, T, VBF, ABF>;
+    constexpr int WMAX = WT > 0 ? WT : GW;
+    const size_t smem = tile::tile_smem_bytes<T, WMAX, HALO>();
+    auto kern = k_spread<GW, WT, T, VBF, ABF, HALO>;
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
     const float beta = (float)p.win.beta;
     const float inv_hw = (float)(2.0 / p.win.w);
     kern<<<b.ntiles, kSpreadThreads, smem, s>>>(b.ent, b.colptr, b.tile_order, vals, grid, b.G,
-                                                b.ntx, b.W, beta, inv_hw);
+                                                b.ntx, b.W, beta, inv_hw, b.halo_buf,
+                                                b.halo_cells);
     FTCG_CK(cudaGetLastError());
+    if (HALO) {
+        k_halo_add<<<b.ntiles, 256, 0, s>>>(b.halo_buf, b.halo_cells, b.colptr, b.ncb, grid, b.G,
+                                            b.T, b.W, b.ntx);
+        FTCG_CK(cudaGetLastError());
+    }
     return FTCG_SUCCESS;
 }
 
-template <int T, bool VBF, bool ABF>
+template <int T, bool VBF, bool ABF, bool HALO>
 ftcg_status_t dispatch_w(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
     switch (p.w) {
-        case 6: return run_spread<8, 6, T, VBF, ABF>(p, vals, grid, s);
-        case 8: return run_spread<8, 8, T, VBF, ABF>(p, vals, grid, s);
+        case 6: return run_spread<8, 6, T, VBF, ABF, HALO>(p, vals, grid, s);
+        case 8: return run_spread<8, 8, T, VBF, ABF, HALO>(p, vals, grid, s);
         default:
-            if (p.w <= 4) return run_spread<4, 0, T, VBF, ABF>(p, vals, grid, s);
-            if (p.w <= 8) return run_spread<8, 0, T, VBF, ABF>(p, vals, grid, s);
-            return run_spread<16, 0, T, VBF, ABF>(p, vals, grid, s);
+            if (p.w <= 4) return run_spread<4, 0, T, VBF, ABF, HALO>(p, vals, grid, s);
+            if (p.w <= 8) return run_spread<8, 0, T, VBF, ABF, HALO>(p, vals, grid, s);
+            return run_spread<16, 0, T, VBF, ABF, HALO>(p, vals, grid, s);
     }
 }
 
 template <bool VBF, bool ABF>
 ftcg_status_t dispatch_t(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
-    if (p.bin.T == 32) return dispatch_w<32, VBF, ABF>(p, vals, grid, s);
-    return dispatch_w<64, VBF, ABF>(p, vals, grid, s);
+    if (p.bin.halo) {
+        if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, true>(p, vals, grid, s);
+        return dispatch_w<64, VBF, ABF, true>(p, vals, grid, s);
+    }
+    if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, false>(p, vals, grid, s);
+    return dispatch_w<64, VBF, ABF, false>(p, vals, grid, s);
 }
 
 // ---- deapodisation and crop: I_p = h_{p mod G} / (phi^(p_x/G) phi^(p_y/G)) -------------------

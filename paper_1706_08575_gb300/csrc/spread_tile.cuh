@@ -47,28 +47,43 @@ __device__ __forceinline__ float2 load_value(const void* __restrict__ vals, uint
     }
 }
 
+// Side of the shared accumulator: the tile, plus the overflow strips in the halo layout.
+template <int T, int WMAX, bool HALO>
+__host__ __device__ constexpr int acc_side() { return HALO ? T + WMAX - 1 : T; }
+
+// Dynamic shared memory of one tile body: two accumulator planes and T + w + 1 column offsets.
+template <int T, int WMAX, bool HALO>
+__host__ __device__ constexpr size_t tile_smem_bytes() {
+    return (size_t)(2 * acc_side<T, WMAX, HALO>() * (acc_side<T, WMAX, HALO>() + 1)) * sizeof(float) +
+           (size_t)(T + WMAX + 1) * sizeof(int);
+}
+
 // One tile, by the whole CTA. GW: lanes per group (power of two >= w); WT: compile-time w
-// (0 = runtime w <= GW). smem holds 2 T (T + 1) floats + (T + w) ints.
-template <int GW, int WT, int T, bool VBF, bool ABF>
+// (0 = runtime w <= GW). HALO: the tile's entries are the samples whose first tap lies in it;
+// the accumulator covers the tile plus w - 1 cells to the right and below, the tile's own cells go
+// to the grid and the overflow strips to halo_buf (added to the neighbours by k_halo_add).
+template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO>
 __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
                                             const int* __restrict__ colptr,
                                             const void* __restrict__ vals,
                                             float2* __restrict__ grid, int G, int ntx, int Wrt,
-                                            float beta, float inv_hw, int tile, float* smem) {
-    constexpr int LD = T + 1;
-    constexpr int NG = kSpreadThreads / GW;
+                                            float beta, float inv_hw, int tile, float* smem,
+                                            float2* __restrict__ halo_buf, int halo_cells) {
     constexpr int WMAX = WT > 0 ? WT : GW;
+    constexpr int PT = acc_side<T, WMAX, HALO>();
+    constexpr int LD = PT + 1;
+    constexpr int NG = kSpreadThreads / GW;
     const int W = WT > 0 ? WT : Wrt;
     const int ncb = T + W - 1;
     float* s_re = smem;
-    float* s_im = smem + T * LD;
-    int* s_col = reinterpret_cast<int*>(smem + 2 * T * LD);
+    float* s_im = smem + PT * LD;
+    int* s_col = reinterpret_cast<int*>(smem + 2 * PT * LD);
 
     const int tyi = tile / ntx, txi = tile - tyi * ntx;
     const int X0 = txi * T, Y0 = tyi * T;
     const int Tw = min(T, G - X0), Th = min(T, G - Y0);
 
-    for (int i = threadIdx.x; i < 2 * T * LD; i += kSpreadThreads) smem[i] = 0.0f;
+    for (int i = threadIdx.x; i < 2 * PT * LD; i += kSpreadThreads) smem[i] = 0.0f;
     for (int i = threadIdx.x; i <= ncb; i += kSpreadThreads) s_col[i] = colptr[(int64_t)tile * ncb + i];
     __syncthreads();
 
@@ -90,11 +105,11 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
     // add the whole window to the tile (rows outside the tile belong to other tiles)
     auto flush_all = [&]() {
         const int col = cur_cx + l;
-        const bool okx = lane_tap && col >= 0 && col < Tw;
+        const bool okx = lane_tap && (HALO || (col >= 0 && col < Tw));
 #pragma unroll
         for (int r = 0; r < WMAX; ++r) {
             const int row = yb + r;
-            if (okx && r < W && row >= 0 && row < Th) {
+            if (okx && r < W && (HALO || (row >= 0 && row < Th))) {
                 atomicAdd(s_re + row * LD + col, ar[r]);
                 atomicAdd(s_im + row * LD + col, ai[r]);
             }
@@ -136,7 +151,7 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
             } else {
                 while (yb < cyl) {               // rows below cyl are final for this column bin
                     const int col = cur_cx + l;
-                    if (lane_tap && col >= 0 && col < Tw && yb >= 0 && yb < Th) {
+                    if (lane_tap && (HALO || (col >= 0 && col < Tw && yb >= 0 && yb < Th))) {
                         atomicAdd(s_re + yb * LD + col, ar[0]);
                         atomicAdd(s_im + yb * LD + col, ai[0]);
                     }
@@ -180,14 +195,69 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
             vc = vn;
             en = e2;
         }
+        flush_all();                              // only groups that held a window flush it
     }
-    flush_all();
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int y = warp; y < Th; y += kSpreadThreads / 32) {
         float2* dst = grid + (int64_t)(Y0 + y) * G + X0;
         for (int x = lane; x < Tw; x += 32) dst[x] = make_float2(s_re[y * LD + x], s_im[y * LD + x]);
+    }
+    if (HALO && e1 > e0) {
+        // overflow strips: right (rows 0..Th+w-2, columns Tw..Tw+w-2), bottom (rows Th..Th+w-2,
+        // columns 0..Tw-1); slot layout fixed by T so that k_halo_add can decode it
+        float2* hb = halo_buf + (int64_t)tile * halo_cells;
+        const int right = (T + W - 1) * (W - 1);
+        for (int k = threadIdx.x; k < halo_cells; k += kSpreadThreads) {
+            int y, x;
+            if (k < right) {
+                y = k / (W - 1);
+                x = Tw + (k - y * (W - 1));
+                if (y >= Th + W - 1) continue;
+            } else {
+                const int kk = k - right;
+                y = Th + kk / T;
+                x = kk - (kk / T) * T;
+                if (x >= Tw) continue;
+            }
+            hb[k] = make_float2(s_re[y * LD + x], s_im[y * LD + x]);
+        }
+    }
+}
+
+// Adds the overflow strips of a halo-layout tile to the grid cells they belong to (wrapping mod
+// G). Cells receive at most three such additions (left, upper and upper-left tile), so float
+// atomics are cheap; the tiles' own cells were stored by the spreading kernel before.
+__device__ __forceinline__ void halo_add_tile(const float2* __restrict__ halo_buf, int halo_cells,
+                                              const int* __restrict__ colptr, int ncb,
+                                              float2* __restrict__ grid, int G, int T, int W,
+                                              int ntx, int tile) {
+    if (colptr[(int64_t)(tile + 1) * ncb] == colptr[(int64_t)tile * ncb]) return;   // empty
+    const int tyi = tile / ntx, txi = tile - tyi * ntx;
+    const int X0 = txi * T, Y0 = tyi * T;
+    const int Tw = min(T, G - X0), Th = min(T, G - Y0);
+    const float2* hb = halo_buf + (int64_t)tile * halo_cells;
+    const int right = (T + W - 1) * (W - 1);
+    for (int k = threadIdx.x; k < halo_cells; k += blockDim.x) {
+        int y, x;
+        if (k < right) {
+            y = k / (W - 1);
+            x = Tw + (k - y * (W - 1));
+            if (y >= Th + W - 1) continue;
+        } else {
+            const int kk = k - right;
+            y = Th + kk / T;
+            x = kk - (kk / T) * T;
+            if (x >= Tw) continue;
+        }
+        int gy = Y0 + y, gx = X0 + x;
+        if (gy >= G) gy -= G;
+        if (gx >= G) gx -= G;
+        const float2 v = hb[k];
+        float* dst = reinterpret_cast<float*>(grid + (int64_t)gy * G + gx);
+        atomicAdd(dst, v.x);
+        atomicAdd(dst + 1, v.y);
     }
 }
 

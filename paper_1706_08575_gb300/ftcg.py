@@ -29,16 +29,19 @@ class FtcgError(RuntimeError):
         self.status = status
 
 
+LAYOUT_AUTO, LAYOUT_DUPLICATE, LAYOUT_HALO = 0, 1, 2
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("weight_width", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int32), ("G", ctypes.c_int32),
                 ("w", ctypes.c_int32), ("tile", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
-                ("entries", ctypes.c_int64), ("beta", ctypes.c_double),
+                ("layout", ctypes.c_int32), ("entries", ctypes.c_int64), ("beta", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
 
 
@@ -132,14 +135,14 @@ class Plan:
     """A binned geometry: ftcg_plan on lam (torch float64, M x 2, CUDA)."""
 
     def __init__(self, lam, N, sigma=2.0, w=8, tile=0, precision=PREC_FP32, weight_width=0,
-                 stream=None, allow_numeric=False):
+                 stream=None, allow_numeric=False, layout=LAYOUT_AUTO):
         import torch
         if lam.dtype != torch.float64 or lam.dim() != 2 or lam.shape[1] != 2 or not lam.is_cuda:
             raise TypeError("lam must be a CUDA float64 tensor of shape (M, 2)")
         lam = lam.contiguous()
         self.M, self.N, self.sigma, self.w = int(lam.shape[0]), int(N), float(sigma), int(w)
         self.device = lam.device
-        opts = Opts(0, precision, tile, weight_width)
+        opts = Opts(0, precision, tile, weight_width, layout)
         h = ctypes.c_void_p()
         st = lib().ftcg_plan(ctypes.byref(h), _ptr(lam), self.M, self.N, self.sigma, self.w,
                              ctypes.byref(opts), _stream(stream))
@@ -259,7 +262,8 @@ def _ptr_array(tensors):
 class Batch:
     """Many pings gridded together: ftcg_plan_batch on a list of (M_i, 2) float64 CUDA tensors."""
 
-    def __init__(self, lams, Ns, sigma=2.0, w=8, tile=0, precision=PREC_FP32, stream=None):
+    def __init__(self, lams, Ns, sigma=2.0, w=8, tile=0, precision=PREC_FP32, stream=None,
+                 layout=LAYOUT_AUTO):
         import torch
         self.n = len(lams)
         self.lams = [l.contiguous() for l in lams]
@@ -271,7 +275,7 @@ class Batch:
         self.device = self.lams[0].device
         M_arr = (ctypes.c_int64 * self.n)(*self.Ms)
         N_arr = (ctypes.c_int32 * self.n)(*self.Ns)
-        opts = Opts(0, precision, tile, 0)
+        opts = Opts(0, precision, tile, 0, layout)
         h = ctypes.c_void_p()
         st = lib().ftcg_plan_batch(ctypes.byref(h), self.n, _ptr_array(self.lams), M_arr, N_arr,
                                    float(sigma), int(w), ctypes.byref(opts), _stream(stream))

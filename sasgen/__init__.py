@@ -177,10 +177,14 @@ def batch_ping(b, seed_base=BASE_SEED + 3):
     return Ping(lam, N, 2.0, 8, scene, None, seed, f"batch-ping-{b}", bp, np.hypot(kx, ky))
 
 
-def random_geometry(rng, N_choices=(256, 512), M_range=(2_000, 20_000)):
+def random_geometry(rng, N_choices=(256, 512), M_range=(2_000, 20_000), log_uniform=False):
     """A random jittered polar geometry for weight learning: angle jitter sd ~ U[0, 0.05] deg,
-    sound-speed error ~ U[-3%, 3%], span ~ U[5, 20] deg, N from N_choices."""
-    M = int(rng.integers(M_range[0], M_range[1] + 1))
+    sound-speed error ~ U[-3%, 3%], span ~ U[5, 20] deg, N from N_choices, M uniform (or
+    log-uniform) over M_range; the FOV is sized so that the raster fills 90% of N."""
+    if log_uniform:
+        M = int(round(np.exp(rng.uniform(np.log(M_range[0]), np.log(M_range[1])))))
+    else:
+        M = int(rng.integers(M_range[0], M_range[1] + 1))
     span = float(rng.uniform(5.0, 20.0))
     e = float(rng.uniform(-0.03, 0.03))
     jit = float(rng.uniform(0.0, 0.05))
@@ -193,6 +197,13 @@ def random_geometry(rng, N_choices=(256, 512), M_range=(2_000, 20_000)):
     lam = baseband(kx, ky, L)
     kr = np.hypot(kx, ky)
     return lam, N, kr
+
+
+def training_geometries(rng, n, N_choices=(128, 256, 512), M_range=(5_000, 60_000)):
+    """Geometries for learning the weights. The weights depend on the local sample density in
+    cycles per FOV, not on N, so small images with log-uniform sample counts span the densities
+    of the uneven batch (about 0.02 to 9 samples per square cycle). Returns [(lam, N, kr)]."""
+    return [random_geometry(rng, N_choices, M_range, log_uniform=True) for _ in range(n)]
 
 
 def values_for(ping: Ping, device=None):

@@ -70,6 +70,7 @@ def test_plan_rejects_opts(L):
     assert _plan(L, opts=ftcg.Opts(0, 2, 0, 0)) == 1                 # precision
     assert _plan(L, opts=ftcg.Opts(0, 0, 48, 0)) == 1                # tile
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 3)) == 1                 # weight width
+    assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 3)) == 1              # layout
     o = ftcg.Opts(0, 0, 0, 0)
     o.reserved[2] = 1
     assert _plan(L, opts=o) == 1

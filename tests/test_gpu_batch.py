@@ -35,12 +35,13 @@ def small_batch(seed=0):
     return cases
 
 
-def test_batch_vs_oracle_and_single(F):
+@pytest.mark.parametrize("layout", [0, 1, 2], ids=["auto", "duplicate", "halo"])
+def test_batch_vs_oracle_and_single(F, layout):
     cases = small_batch(1)
     lams = [dev(c[0]) for c in cases]
     vals = [dev(c[1]) for c in cases]
     alphas = [dev(c[2]) for c in cases]
-    with F.Batch(lams, [c[3] for c in cases], 2.0, 8) as b:
+    with F.Batch(lams, [c[3] for c in cases], 2.0, 8, layout=layout) as b:
         tiles, entries, _ = b.info()
         assert set(tiles) <= {32, 64}
         b.set_weights(alphas)

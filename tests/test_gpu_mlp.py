@@ -107,28 +107,28 @@ def test_checkpoint_continuation_is_bitwise(F):
 def test_trained_network_gain(F, tmp_path):
     """Train on exact weights of random jittered polar geometries, then grid a held-out ping with
     the predicted weights: its image is closer to the exact-weight oracle image than the
-    unweighted one. The 16-neighbour features see about 1.5 cycles around a sample, while the
-    Fejer sums behind the exact weights also collect tails along the two axes across the whole
-    raster; on an unseen geometry this leaves a global bias of a few percent on top of a 2-3%
-    per-sample scatter (measured on the FP64 oracle network as well), so the bars are a 15%
-    median weight error and a 25% smaller image error than without weights."""
+    unweighted one. The weights depend on the local density in cycles, so the training
+    geometries span the densities of the held-out one (log-uniform sample counts). The FP64
+    oracle network reaches 0.7-2.5% median weight error on such held-out geometries and the
+    device-trained one 2.5% (image error 0.39 of the unweighted one); the bars are 5% and one
+    half."""
     import torch
     from paper_1706_08575_gb300 import learn
     rng = np.random.default_rng(3)
     geos, Ns = [], []
-    for _ in range(24):
-        lam, N, kr = sasgen.random_geometry(rng, N_choices=(128, 256), M_range=(4000, 9000))
+    for lam, N, kr in sasgen.training_geometries(rng, 24, N_choices=(128, 256),
+                                                 M_range=(3000, 12000)):
         geos.append((lam, kr))
         Ns.append(N)
     feats, targ = learn.build_dataset(geos, Ns)
     mlp = F.Mlp(learn.init_params(0))
-    hist = learn.train(mlp, feats, targ, steps=1500, batch=4096, lr=2e-3, log_every=500)
+    hist = learn.train(mlp, feats, targ, steps=8000, batch=8192, lr=3e-3, log_every=2000)
     assert hist[-1][1] < 0.2 * hist[0][1]
     learn.save_checkpoint(tmp_path / "m.npz", mlp)
     m2 = learn.load_checkpoint(tmp_path / "m.npz")
     # held-out ping
     lam, N, kr = sasgen.random_geometry(np.random.default_rng(99), N_choices=(128,),
-                                        M_range=(6000, 6000))
+                                        M_range=(6000, 6000))   # inside the training range
     a_ref, _ = O.weights_brute(lam, N)
     lt = dev(lam)
     fe = F.features(lt, dev(learn.kr_feature(kr)))
@@ -144,7 +144,7 @@ def test_trained_network_gain(F, tmp_path):
     e_nn, e_1 = O.rel_l2(img_nn, ref), O.rel_l2(img_1, ref)
     print(f"learned: median weight error {w_err:.2e}, image rel-L2 {e_nn:.2e}; "
           f"unweighted image rel-L2 {e_1:.2e}")
-    assert w_err < 0.15
-    assert e_nn < 0.75 * e_1
+    assert w_err < 0.05
+    assert e_nn < 0.5 * e_1
     mlp.close()
     m2.close()

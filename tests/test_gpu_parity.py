@@ -32,9 +32,10 @@ def c64(v):
     return np.asarray(v).astype(np.complex64)
 
 
-def expected_entries(lam, N, sigma, w, T):
-    """(tile, cx, cy, sample, dx, dy) for every (tile, wrap copy) a footprint touches: a new run
-    of taps starts at tap 0, at a tile boundary and where the footprint wraps mod G."""
+def expected_entries(lam, N, sigma, w, T, halo=False):
+    """(tile, cx, cy, sample, dx, dy). Duplicate layout: one entry for every (tile, wrap copy) a
+    footprint touches (a new run of taps starts at tap 0, at a tile boundary and where the
+    footprint wraps mod G). Halo layout: one entry, in the tile of the first tap."""
     G = O.grid_side(N, sigma)
     c, u = O.tap_origins(lam, N, sigma, w)
     d = (u - c).astype(np.float32)
@@ -47,7 +48,7 @@ def expected_entries(lam, N, sigma, w, T):
             r = []
             for t in range(w):
                 col = (cw + t) % G
-                if t == 0 or col % T == 0:
+                if t == 0 or (not halo and col % T == 0):
                     tile = col // T
                     r.append((tile, col - tile * T - t))
             runs.append(r)
@@ -57,14 +58,16 @@ def expected_entries(lam, N, sigma, w, T):
     return rows
 
 
+@pytest.mark.parametrize("layout", [1, 2], ids=["duplicate", "halo"])
 @pytest.mark.parametrize("N,sigma,w,T,spread", [
     (64, 2.0, 6, 32, 64), (50, 2.0, 8, 32, 150), (40, 1.25, 5, 32, 40), (16, 2.0, 8, 64, 40),
 ])
-def test_plan_entries_bit_exact(F, N, sigma, w, T, spread):
+def test_plan_entries_bit_exact(F, N, sigma, w, T, spread, layout):
     lam, _ = sasgen.random_case(3, 900, N, sigma, w, spread)
     lam[:5] = np.array([[3.0, -2.5], [0.25, 7.0], [N / 2, -N / 2], [-N / 2, N / 2 - 1e-12],
                         [0.0, 0.0]])          # ties and wrap edges
-    with F.Plan(dev(lam), N, sigma, w, tile=T) as p:
+    with F.Plan(dev(lam), N, sigma, w, tile=T, layout=layout) as p:
+        assert p.info.layout == layout
         e = p.entries()
         ncb = T + w - 1
         key = (e["tile"].astype(np.int64) * ncb + e["cx"] + w - 1) * ncb + e["cy"] + w - 1
@@ -72,13 +75,13 @@ def test_plan_entries_bit_exact(F, N, sigma, w, T, spread):
         got = sorted(zip(e["tile"].tolist(), e["cx"].tolist(), e["cy"].tolist(),
                          e["sample"].tolist(), e["dx"].tolist(), e["dy"].tolist()))
         exp = sorted((a, b, c, d, float(x), float(y))
-                     for a, b, c, d, x, y in expected_entries(lam, N, sigma, w, T))
+                     for a, b, c, d, x, y in expected_entries(lam, N, sigma, w, T, layout == 2))
         assert len(got) == len(exp)
         assert got == exp
 
 
-def _run_adjoint(F, lam, v, N, sigma, w, alpha=None, T=0):
-    with F.Plan(dev(lam), N, sigma, w, tile=T) as p:
+def _run_adjoint(F, lam, v, N, sigma, w, alpha=None, T=0, layout=0):
+    with F.Plan(dev(lam), N, sigma, w, tile=T, layout=layout) as p:
         if alpha is not None:
             p.set_weights(dev(alpha))
         img = p.adjoint(dev(c64(v)))
@@ -97,16 +100,17 @@ def image_tol(N, sigma, w):
     return max(TOL, 5e-8 * A)
 
 
+@pytest.mark.parametrize("layout", [1, 2], ids=["duplicate", "halo"])
 @pytest.mark.parametrize("M,N,sigma,w,spread,T", [
     (4096, 64, 2.0, 6, 150, 0), (3000, 50, 2.0, 8, 150, 32), (2000, 40, 1.25, 5, 40, 32),
     (5000, 96, 2.0, 7, 96, 64), (3000, 40, 2.0, 10, 120, 32), (1500, 32, 2.0, 13, 32, 32),
     (2500, 48, 1.5, 16, 60, 32), (3000, 64, 2.0, 4, 64, 64), (1, 32, 2.0, 8, 32, 0),
 ])
-def test_adjoint_and_spread_vs_oracle(F, M, N, sigma, w, spread, T):
+def test_adjoint_and_spread_vs_oracle(F, M, N, sigma, w, spread, T, layout):
     lam, v = sasgen.random_case(11 + M, M, N, sigma, w, spread)
     alpha = np.random.default_rng(M).uniform(0.2, 2.0, M)
     vc = c64(v).astype(np.complex128)
-    img, grid = _run_adjoint(F, lam, v, N, sigma, w, alpha, T)
+    img, grid = _run_adjoint(F, lam, v, N, sigma, w, alpha, T, layout)
     ref = O.adjoint(lam, alpha.astype(np.float32) * vc, N, sigma, w)
     assert O.rel_l2(img, ref) < image_tol(N, sigma, w)
     gref = O.spread(lam, alpha.astype(np.float32) * vc, N, sigma, w)
@@ -141,13 +145,14 @@ def test_empty_plan(F):
         p.check()
 
 
-def test_collisions_one_cell(F):
+@pytest.mark.parametrize("layout", [1, 2], ids=["duplicate", "halo"])
+def test_collisions_one_cell(F, layout):
     """Every sample in the same cell: maximal shared-atomic contention."""
     rng = np.random.default_rng(4)
     M, N = 3000, 32
     lam = np.tile([[1.3, -2.7]], (M, 1)) + 1e-3 * rng.random((M, 2))
     v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
-    img, _ = _run_adjoint(F, lam, v, N, 2.0, 8)
+    img, _ = _run_adjoint(F, lam, v, N, 2.0, 8, layout=layout)
     ref = O.adjoint(lam, c64(v).astype(np.complex128), N, 2.0, 8)
     assert O.rel_l2(img, ref) < TOL
 
