@@ -512,7 +512,8 @@ def run_ours(args):
             "stages_ms": {"spread": sp_ms, "fft": fft_ms, "deapod_crop": dp_ms, "calls": ncalls},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(info.tile),
-                         "kernel": "k_spread", "peak_kind": peak_kind,
+                         "kernel": "k_spread (+ k_halo_add in the halo layout: the spreading stage)",
+                         "peak_kind": peak_kind,
                          "alg_bytes_per_launch": alg_bytes},
             "rel_l2_sampled_vs_fp64_oracle": rel,
             "per_ping": {"value": p.M / sum(pp), "unit": UNIT,
@@ -520,7 +521,8 @@ def run_ours(args):
                          "adjoint_ms": 1e3 * pp[2]},
             "e2e": {"value": world * p.M / e2e_max, "unit": UNIT,
                     "h2d_bytes_per_step": int(p.M * 8), "d2h_bytes_per_step": int(p.N * p.N * 8)},
-            "gpu_launches": 2 * args.steps,
+            # per step: k_spread, k_halo_add (halo layout only), k_deapod_crop (cuFFT not counted)
+            "gpu_launches": (3 if info.layout == 2 else 2) * args.steps,
             "wall_s_timed_region": wall,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -535,8 +537,8 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

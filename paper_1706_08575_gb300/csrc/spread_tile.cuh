@@ -15,7 +15,7 @@ namespace tile {
 #define FTCG_SPREAD_THREADS 256
 #endif
 #ifndef FTCG_SPREAD_MINB
-#define FTCG_SPREAD_MINB 1
+#define FTCG_SPREAD_MINB 4
 #endif
 #ifndef FTCG_SPREAD_WINDOW
 #define FTCG_SPREAD_WINDOW 1
@@ -83,6 +83,15 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
     const int X0 = txi * T, Y0 = tyi * T;
     const int Tw = min(T, G - X0), Th = min(T, G - Y0);
 
+    if (colptr[(int64_t)tile * ncb] == colptr[(int64_t)(tile + 1) * ncb]) {
+        // an empty tile (common under a polar footprint): store zeros, no accumulator, no halo
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int y = warp; y < Th; y += kSpreadThreads / 32) {
+            float2* dst = grid + (int64_t)(Y0 + y) * G + X0;
+            for (int x = lane; x < Tw; x += 32) dst[x] = make_float2(0.f, 0.f);
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < 2 * PT * LD; i += kSpreadThreads) smem[i] = 0.0f;
     for (int i = threadIdx.x; i <= ncb; i += kSpreadThreads) s_col[i] = colptr[(int64_t)tile * ncb + i];
     __syncthreads();
