@@ -46,11 +46,13 @@ void release_plan(Plan* p) {
     if (p->lambda) cudaFree(p->lambda);
     if (p->samp) cudaFree(p->samp);
     if (p->deapod) cudaFree(p->deapod);
+    if (p->deapod2) cudaFree(p->deapod2);
     if (p->grid) cudaFree(p->grid);
     if (p->status) cudaFree(p->status);
     if (p->stage_vals) cudaFree(p->stage_vals);
     if (p->stage_img) cudaFree(p->stage_img);
     if (p->fft_ok) cufftDestroy(p->fft);
+    release_pruned_fft(p);
     if (p->prof_ev) {
         for (int i = 0; i < kMaxProfiled * 4; ++i) cudaEventDestroy(p->prof_ev[i]);
         delete[] p->prof_ev;
@@ -73,6 +75,9 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
     FTCG_CK(cudaMalloc(&p->deapod, (size_t)p->N * sizeof(double)));
     bytes += (int64_t)p->N * sizeof(double);
     FTCG_TRY(window_factors(p->deapod, p->N, p->G, p->win, s));
+    FTCG_CK(cudaMalloc(&p->deapod2, (size_t)p->N * sizeof(float2)));
+    bytes += (int64_t)p->N * sizeof(float2);
+    FTCG_TRY(split_factors(p->deapod, p->deapod2, p->N, s));
     FTCG_TRY(build_binning(p->bin, p->lambda, M, p->sigma, p->G, p->opts.tile, p->w,
                            p->opts.layout == FTCG_LAYOUT_HALO, p->status, p->samp, s, &bytes));
     if (own_grid) {
@@ -83,6 +88,7 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
         size_t ws = 0;
         cufftGetSize(p->fft, &ws);
         bytes += (int64_t)ws;
+        FTCG_TRY(build_pruned_fft(p, s, &bytes));
     }
     p->device_bytes = bytes;
     unsigned st = 0;
@@ -151,9 +157,13 @@ ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* im
     if (ev) FTCG_CK(cudaEventRecord(ev[0], s));
     FTCG_TRY(launch_spread(*p, vals, vdtype, p->grid, s));
     if (ev) FTCG_CK(cudaEventRecord(ev[1], s));
-    FTCG_CKFFT(cufftSetStream(p->fft, s));
-    FTCG_CKFFT(cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
-                            reinterpret_cast<cufftComplex*>(p->grid), CUFFT_INVERSE));
+    if (p->pruned_ok) {
+        FTCG_TRY(exec_pruned_inverse(p, s));
+    } else {
+        FTCG_CKFFT(cufftSetStream(p->fft, s));
+        FTCG_CKFFT(cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
+                                reinterpret_cast<cufftComplex*>(p->grid), CUFFT_INVERSE));
+    }
     if (ev) FTCG_CK(cudaEventRecord(ev[2], s));
     FTCG_TRY(launch_deapod_crop(*p, p->grid, reinterpret_cast<float2*>(img), s));
     if (ev) FTCG_CK(cudaEventRecord(ev[3], s));

@@ -30,13 +30,13 @@ struct PingDesc {
     const void* vals;
     float2* grid;
     float2* img;
-    const double* deapod;
+    const float2* deapod2;
     float2* halo_buf;
     int G, ntx, T, N;
     int halo, halo_cells, ncb, W;
 };
 
-template <int GW, int WT, bool VBF, bool ABF>
+template <int GW, int WT, bool VBF, bool ABF, int CPL>
 __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
     k_spread_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items, int nitems,
                    int* __restrict__ counter, int Wrt, float beta, float inv_hw) {
@@ -52,20 +52,20 @@ __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
         const PingDesc d = desc[pt.x];
         if (d.halo) {
             if (d.T == 64)
-                tile::spread_tile<GW, WT, 64, VBF, ABF, true>(d.ent, d.colptr, d.vals, d.grid, d.G,
+                tile::spread_tile<GW, WT, 64, VBF, ABF, true, CPL>(d.ent, d.colptr, d.vals, d.grid, d.G,
                                                               d.ntx, Wrt, beta, inv_hw, pt.y, smem,
                                                               d.halo_buf, d.halo_cells);
             else
-                tile::spread_tile<GW, WT, 32, VBF, ABF, true>(d.ent, d.colptr, d.vals, d.grid, d.G,
+                tile::spread_tile<GW, WT, 32, VBF, ABF, true, CPL>(d.ent, d.colptr, d.vals, d.grid, d.G,
                                                               d.ntx, Wrt, beta, inv_hw, pt.y, smem,
                                                               d.halo_buf, d.halo_cells);
         } else {
             if (d.T == 64)
-                tile::spread_tile<GW, WT, 64, VBF, ABF, false>(d.ent, d.colptr, d.vals, d.grid,
+                tile::spread_tile<GW, WT, 64, VBF, ABF, false, CPL>(d.ent, d.colptr, d.vals, d.grid,
                                                                d.G, d.ntx, Wrt, beta, inv_hw, pt.y,
                                                                smem, nullptr, 0);
             else
-                tile::spread_tile<GW, WT, 32, VBF, ABF, false>(d.ent, d.colptr, d.vals, d.grid,
+                tile::spread_tile<GW, WT, 32, VBF, ABF, false, CPL>(d.ent, d.colptr, d.vals, d.grid,
                                                                d.G, d.ntx, Wrt, beta, inv_hw, pt.y,
                                                                smem, nullptr, 0);
         }
@@ -82,18 +82,12 @@ __global__ void __launch_bounds__(256)
                         pt.y);
 }
 
-__global__ void k_deapod_batch(const PingDesc* __restrict__ desc) {
+__global__ void __launch_bounds__(kDeapodThreads) k_deapod_batch(const PingDesc* __restrict__ desc) {
     const PingDesc d = desc[blockIdx.z];
-    const int N = d.N, G = d.G;
-    const int iy = blockIdx.y;
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    if (iy >= N || ix >= N) return;
-    int qy = iy - N / 2, qx = ix - N / 2;
-    if (qy < 0) qy += G;
-    if (qx < 0) qx += G;
-    const float2 h = d.grid[(int64_t)qy * G + qx];
-    const float f = (float)(d.deapod[iy] * d.deapod[ix]);
-    d.img[(int64_t)iy * N + ix] = make_float2(h.x * f, h.y * f);
+    if (blockIdx.y * kDeapodRows >= d.N) return;
+    const bool vec = d.N % 4 == 0 && (reinterpret_cast<uintptr_t>(d.grid) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(d.img) & 15) == 0;
+    deapod_crop_block(d.grid, d.img, d.deapod2, d.N, d.G, vec);
 }
 
 template <int WMAX>
@@ -251,10 +245,10 @@ void release_batch(Batch* b) {
     delete b;
 }
 
-template <int GW, int WT, bool VBF, bool ABF>
+template <int GW, int WT, bool VBF, bool ABF, int CPL = 1>
 ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
-    auto kern = k_spread_batch<GW, WT, VBF, ABF>;
-    const size_t smem = spread_smem<(WT > 0 ? WT : GW)>();
+    auto kern = k_spread_batch<GW, WT, VBF, ABF, CPL>;
+    const size_t smem = spread_smem<(WT > 0 ? WT : GW * CPL)>();
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
@@ -276,13 +270,15 @@ ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
 
 template <bool VBF, bool ABF>
 ftcg_status_t launch_batch_spread_w(Batch& b, cudaStream_t s) {
+    using tile::kCpl8;
+    using tile::kCpl16;
     switch (b.w) {
-        case 6: return launch_batch_spread_t<8, 6, VBF, ABF>(b, s);
-        case 8: return launch_batch_spread_t<8, 8, VBF, ABF>(b, s);
+        case 6: return launch_batch_spread_t<8 / kCpl8, 6, VBF, ABF, kCpl8>(b, s);
+        case 8: return launch_batch_spread_t<8 / kCpl8, 8, VBF, ABF, kCpl8>(b, s);
         default:
             if (b.w <= 4) return launch_batch_spread_t<4, 0, VBF, ABF>(b, s);
-            if (b.w <= 8) return launch_batch_spread_t<8, 0, VBF, ABF>(b, s);
-            return launch_batch_spread_t<16, 0, VBF, ABF>(b, s);
+            if (b.w <= 8) return launch_batch_spread_t<8 / kCpl8, 0, VBF, ABF, kCpl8>(b, s);
+            return launch_batch_spread_t<16 / kCpl16, 0, VBF, ABF, kCpl16>(b, s);
     }
 }
 
@@ -311,7 +307,9 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
         FTCG_CKFFT(cufftExecC2C(c.fft, reinterpret_cast<cufftComplex*>(c.grids),
                                 reinterpret_cast<cufftComplex*>(c.grids), CUFFT_INVERSE));
     }
-    k_deapod_batch<<<dim3((b.max_N + 255) / 256, b.max_N, b.n), 256, 0, s>>>(b.d_desc);
+    const dim3 blocks((b.max_N + 2 * kDeapodThreads - 1) / (2 * kDeapodThreads),
+                      (b.max_N + kDeapodRows - 1) / kDeapodRows, b.n);
+    k_deapod_batch<<<blocks, kDeapodThreads, 0, s>>>(b.d_desc);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
 }
@@ -385,7 +383,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         d.vals = nullptr;
         d.grid = c.grids + (size_t)b.slot_of[i] * c.G * c.G;
         d.img = nullptr;
-        d.deapod = p->deapod;
+        d.deapod2 = p->deapod2;
         d.G = p->G;
         d.ntx = bn.ntx;
         d.T = bn.T;

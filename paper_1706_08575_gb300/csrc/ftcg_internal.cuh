@@ -54,6 +54,9 @@ enum : unsigned {
 constexpr int kSampleBits = 25;
 constexpr uint32_t kSampleMask = (1u << kSampleBits) - 1u;
 constexpr int64_t kMaxSamples = (int64_t(1) << kSampleBits) - 1;
+// Zeroed entries after the last one (sample 0, which exists whenever there are entries), so that
+// the spreading loop may prefetch up to two entries past its chunk without a bounds test.
+constexpr int kEntryPad = 2;
 
 // One sorted (tile, sample) entry of the spreading plan: 16 bytes, loaded with one LDG.128.
 //   dx, dy : sigma lambda - first tap, in (w/2 - 1, w/2]   (float32)
@@ -79,6 +82,7 @@ struct Binning {
     Entry* ent = nullptr;               // n_entries, sorted by (tile, column bin, row)
     int* colptr = nullptr;              // ntiles * ncb + 1 start offsets
     int* tile_order = nullptr;          // tiles by decreasing entry count (launch order)
+    int n_nonempty = 0;                 // tiles with at least one entry (a prefix of tile_order)
     bool halo = false;                  // FTCG_LAYOUT_HALO: one entry per sample + halo strips
     int halo_cells = 0;                 // halo cells per tile
     float2* halo_buf = nullptr;         // ntiles * halo_cells overflow values (halo layout)
@@ -94,9 +98,17 @@ struct Plan {
     double* lambda = nullptr;           // M x 2 copy (FP64), for the weight construction
     int4* samp = nullptr;               // per sample: (cx mod G, cy mod G, float dx bits, dy bits)
     double* deapod = nullptr;           // N factors 1 / phi^(p / G), p = -N/2 .. N/2-1
+    float2* deapod2 = nullptr;          // the same factors split into FP32 (hi, lo) pairs
     float2* grid = nullptr;             // G x G complex64 work grid
     cufftHandle fft = 0;
     bool fft_ok = false;
+    // Pruned inverse FFT of the adjoint (fft.cu): 1-D column transforms over the occupied columns
+    // (at most two runs, [col_x0[k], col_x0[k] + col_n[k])), then row transforms of the N rows
+    // the crop keeps.
+    cufftHandle fft_col[2] = {0, 0};
+    int col_x0[2] = {0, 0}, col_n[2] = {0, 0};
+    cufftHandle fft_row = 0;
+    bool pruned_ok = false;
     unsigned* status = nullptr;         // device status word
     void* stage_vals = nullptr;         // ftcg_adjoint_host staging (device)
     void* stage_img = nullptr;
@@ -130,6 +142,76 @@ ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStr
 ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2* grid,
                             cudaStream_t s);
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s);
+ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes);
+ftcg_status_t exec_pruned_inverse(Plan* p, cudaStream_t s);
+void release_pruned_fft(Plan* p);
+
+// An FP64 factor r held as an unevaluated FP32 pair r = hi + lo (hi = fl32(r), lo = fl32(r - hi)),
+// so |r - hi - lo| <= 2^-48 |r|.
+ftcg_status_t split_factors(const double* r, float2* r2, int n, cudaStream_t s);
+
+// The product of two factors held as (hi, lo) pairs, rounded once to FP32: the dropped lo*lo term
+// and the rounding of the inner FMA are both below 2^-46 of the product, so the result is the
+// FP32 rounding of the FP64 product, or (within 2^-46 of a rounding boundary) its neighbour.
+__device__ __forceinline__ float df_product(float2 a, float2 b) {
+    return fmaf(a.x, b.x, fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Window division + crop, I_p = h_{p mod G} / (phi^(p_x / G) phi^(p_y / G)) for
+// p in {-N/2..N/2-1}^2 (Eq. newadm). The per-pixel product of the FP64 factors (passed as FP32
+// pairs) is rounded once to FP32. One thread takes two adjacent columns (ix, ix + 1) of
+// kDeapodRows rows, all loads first. vec: 16-byte accesses, valid when N % 4 == 0 (then N/2 is even, so a
+// pair never straddles the wrap of the crop) and grid and img are 16-byte aligned.
+constexpr int kDeapodThreads = 128, kDeapodRows = 4;
+__device__ __forceinline__ void deapod_crop_block(const float2* __restrict__ grid,
+                                                  float2* __restrict__ img,
+                                                  const float2* __restrict__ r2, int N, int G,
+                                                  bool vec) {
+    const int ix = 2 * (blockIdx.x * kDeapodThreads + threadIdx.x);
+    if (ix >= N) return;                        // N is even, so ix + 1 < N as well
+    const int iy0 = blockIdx.y * kDeapodRows;
+    const int h = N / 2;
+    const int qx0 = ix - h < 0 ? ix - h + G : ix - h;
+    const int qx1 = ix + 1 - h < 0 ? ix + 1 - h + G : ix + 1 - h;
+    float2 a[kDeapodRows], b[kDeapodRows];
+#pragma unroll
+    for (int k = 0; k < kDeapodRows; ++k) {
+        const int iy = iy0 + k;
+        if (iy < N) {
+            const float2* row = grid + (int64_t)(iy - h < 0 ? iy - h + G : iy - h) * G;
+            if (vec) {
+                const float4 v = *reinterpret_cast<const float4*>(row + qx0);
+                a[k] = make_float2(v.x, v.y);
+                b[k] = make_float2(v.z, v.w);
+            } else {
+                a[k] = row[qx0];
+                b[k] = row[qx1];
+            }
+        }
+    }
+    const float2 rx0 = r2[ix], rx1 = r2[ix + 1];
+#pragma unroll
+    for (int k = 0; k < kDeapodRows; ++k) {
+        const int iy = iy0 + k;
+        if (iy < N) {
+            const float2 ry = r2[iy];
+            const float f0 = df_product(ry, rx0), f1 = df_product(ry, rx1);
+            float2* out = img + (int64_t)iy * N + ix;
+            if (vec) {
+                *reinterpret_cast<float4*>(out) =
+                    make_float4(a[k].x * f0, a[k].y * f0, b[k].x * f1, b[k].y * f1);
+            } else {
+                out[0] = make_float2(a[k].x * f0, a[k].y * f0);
+                out[1] = make_float2(b[k].x * f1, b[k].y * f1);
+            }
+        }
+    }
+}
+
+inline bool deapod_vec_ok(const void* grid, const void* img, int N) {
+    return N % 4 == 0 && (reinterpret_cast<uintptr_t>(grid) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(img) & 15) == 0;
+}
 ftcg_status_t launch_pad_apod(const Plan& p, const float2* img, float2* grid, cudaStream_t s);
 ftcg_status_t launch_interp(const Plan& p, const float2* grid, float2* vals, cudaStream_t s);
 ftcg_status_t launch_set_alpha(const Plan& p, const void* alpha, int dtype, cudaStream_t s);

@@ -273,6 +273,8 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
     std::iota(order.begin(), order.end(), 0);
     auto cnt = [&](int t) { return cp[(int64_t)(t + 1) * b.ncb] - cp[(int64_t)t * b.ncb]; };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cnt(x) > cnt(y); });
+    b.n_nonempty = 0;
+    while (b.n_nonempty < b.ntiles && cnt(order[b.n_nonempty]) > 0) ++b.n_nonempty;
     FTCG_CK(cudaMalloc(&b.tile_order, b.ntiles * sizeof(int)));
     *bytes += b.ntiles * sizeof(int);
     FTCG_CK(cudaMemcpyAsync(b.tile_order, order.data(), b.ntiles * sizeof(int),
@@ -318,8 +320,9 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
     k_colptr<<<grid_for(nbins + 1), kThreads, 0, s>>>(offs, nbins, b.ncb, total, b.colptr);
     FTCG_CK(cudaGetLastError());
     if (total > 0) {
-        FTCG_CK(cudaMalloc(&b.ent, (size_t)total * sizeof(Entry)));
-        *bytes += (int64_t)total * sizeof(Entry);
+        FTCG_CK(cudaMalloc(&b.ent, (size_t)(total + kEntryPad) * sizeof(Entry)));
+        *bytes += (int64_t)(total + kEntryPad) * sizeof(Entry);
+        FTCG_CK(cudaMemsetAsync(b.ent + total, 0, kEntryPad * sizeof(Entry), s));
         k_bin_scatter<<<grid_for(M), kThreads, 0, s>>>(d_lambda, M, scale, G, T, W, b.ntx, b.ncb,
                                                        halo, offs, b.ent);
         FTCG_CK(cudaGetLastError());

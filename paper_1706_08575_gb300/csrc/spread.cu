@@ -6,13 +6,14 @@
 // memory; tiles are launched heaviest first. The tile's sorted entries (every (tile, sample) pair
 // whose w x w footprint touches the tile, ordered by first-tap column then first-tap row, built
 // by plan.cu) are split into equal contiguous chunks, one per group of GW lanes (GW = 4, 8 or
-// 16 >= w). Lane l of a group owns tap column l of the current column bin and keeps a rolling
-// window of w rows of its column in registers: an entry adds c phi(dx - l) phi(dy - r) to window
-// row r (the w row factors are computed one per lane and broadcast by shuffles); when the next
-// entry starts on a later row, the rows it can no longer reach leave the window with one
-// shared-memory atomic each. A row thus receives one atomic per (column bin, chunk) instead of
-// one per entry. The tile is then stored once, coalesced: every grid cell is written exactly
-// once, with no zero-fill and no global atomics.
+// 16, GW x CPL >= w). Lane l of a group owns tap columns l, l + GW, ... (CPL of them) of the
+// current column bin and keeps a rolling window of w rows of each in registers: an entry adds
+// c phi(dx - l) phi(dy - r) to window row r (the w row factors are computed by the lanes and
+// broadcast by shuffles); when the next entry starts on a later row, the rows it can no longer
+// reach leave the window with one shared-memory atomic each. A row thus receives one atomic per
+// (column bin, chunk) instead of one per entry. The tile is then stored once, coalesced: every
+// grid cell is written exactly once, with no zero-fill. In the halo layout the accumulator also
+// holds the w - 1 overflow rows and columns, which k_halo_add adds to the neighbouring tiles.
 
 #include "spread_tile.cuh"
 
@@ -23,7 +24,7 @@ namespace {
 using tile::kSpreadThreads;
 using tile::es32;
 
-template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO>
+template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL>
 __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
     k_spread(const Entry* __restrict__ ent, const int* __restrict__ colptr,
              const int* __restrict__ tile_order, const void* __restrict__ vals,
@@ -31,22 +32,25 @@ __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
              float2* __restrict__ halo_buf, int halo_cells) {
     extern __shared__ float smem[];
     const int t = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
-    tile::spread_tile<GW, WT, T, VBF, ABF, HALO>(ent, colptr, vals, grid, G, ntx, Wrt, beta,
-                                                 inv_hw, t, smem, halo_buf, halo_cells);
+    tile::spread_tile<GW, WT, T, VBF, ABF, HALO, CPL>(ent, colptr, vals, grid, G, ntx, Wrt, beta,
+                                                      inv_hw, t, smem, halo_buf, halo_cells);
 }
 
+// one CTA per non-empty tile (the first n_nonempty of the heaviest-first order)
 __global__ void __launch_bounds__(256)
     k_halo_add(const float2* __restrict__ halo_buf, int halo_cells, const int* __restrict__ colptr,
-               int ncb, float2* __restrict__ grid, int G, int T, int W, int ntx) {
-    tile::halo_add_tile(halo_buf, halo_cells, colptr, ncb, grid, G, T, W, ntx, blockIdx.x);
+               const int* __restrict__ tile_order, int ncb, float2* __restrict__ grid, int G,
+               int T, int W, int ntx) {
+    tile::halo_add_tile(halo_buf, halo_cells, colptr, ncb, grid, G, T, W, ntx,
+                        tile_order[blockIdx.x]);
 }
 
-template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO>
+template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL = 1>
 ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
     const Binning& b = p.bin;
-    constexpr int WMAX = WT > 0 ? WT : GW;
+    constexpr int WMAX = WT > 0 ? WT : GW * CPL;
     const size_t smem = tile::tile_smem_bytes<T, WMAX, HALO>();
-    auto kern = k_spread<GW, WT, T, VBF, ABF, HALO>;
+    auto kern = k_spread<GW, WT, T, VBF, ABF, HALO, CPL>;
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
@@ -56,9 +60,9 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
                                                 b.ntx, b.W, beta, inv_hw, b.halo_buf,
                                                 b.halo_cells);
     FTCG_CK(cudaGetLastError());
-    if (HALO) {
-        k_halo_add<<<b.ntiles, 256, 0, s>>>(b.halo_buf, b.halo_cells, b.colptr, b.ncb, grid, b.G,
-                                            b.T, b.W, b.ntx);
+    if (HALO && b.n_nonempty > 0) {
+        k_halo_add<<<b.n_nonempty, 256, 0, s>>>(b.halo_buf, b.halo_cells, b.colptr, b.tile_order,
+                                                b.ncb, grid, b.G, b.T, b.W, b.ntx);
         FTCG_CK(cudaGetLastError());
     }
     return FTCG_SUCCESS;
@@ -66,13 +70,15 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
 
 template <int T, bool VBF, bool ABF, bool HALO>
 ftcg_status_t dispatch_w(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
+    using tile::kCpl8;
+    using tile::kCpl16;
     switch (p.w) {
-        case 6: return run_spread<8, 6, T, VBF, ABF, HALO>(p, vals, grid, s);
-        case 8: return run_spread<8, 8, T, VBF, ABF, HALO>(p, vals, grid, s);
+        case 6: return run_spread<8 / kCpl8, 6, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s);
+        case 8: return run_spread<8 / kCpl8, 8, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s);
         default:
             if (p.w <= 4) return run_spread<4, 0, T, VBF, ABF, HALO>(p, vals, grid, s);
-            if (p.w <= 8) return run_spread<8, 0, T, VBF, ABF, HALO>(p, vals, grid, s);
-            return run_spread<16, 0, T, VBF, ABF, HALO>(p, vals, grid, s);
+            if (p.w <= 8) return run_spread<8 / kCpl8, 0, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s);
+            return run_spread<16 / kCpl16, 0, T, VBF, ABF, HALO, kCpl16>(p, vals, grid, s);
     }
 }
 
@@ -86,21 +92,11 @@ ftcg_status_t dispatch_t(const Plan& p, const void* vals, float2* grid, cudaStre
     return dispatch_w<64, VBF, ABF, false>(p, vals, grid, s);
 }
 
-// ---- deapodisation and crop: I_p = h_{p mod G} / (phi^(p_x/G) phi^(p_y/G)) -------------------
-// The factors are FP64; their product for a pixel is formed in FP64 and rounded once to FP32
-// (relative 6e-8), then applied to the FP32 grid value. One thread per pixel, a 2-D launch over
-// (columns, rows); each row reads two contiguous runs of the grid (p_x >= 0 and p_x < 0).
-__global__ void k_deapod_crop(const float2* __restrict__ grid, float2* __restrict__ img,
-                              const double* __restrict__ r, int N, int G) {
-    const int iy = blockIdx.y;
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ix >= N) return;
-    int qy = iy - N / 2, qx = ix - N / 2;
-    if (qy < 0) qy += G;
-    if (qx < 0) qx += G;
-    const float2 h = grid[(int64_t)qy * G + qx];
-    const float f = (float)(r[iy] * r[ix]);
-    img[(int64_t)iy * N + ix] = make_float2(h.x * f, h.y * f);
+// ---- deapodisation and crop (the body is deapod_crop_block) -------------------------------------
+__global__ void __launch_bounds__(kDeapodThreads)
+    k_deapod_crop(const float2* __restrict__ grid, float2* __restrict__ img,
+                  const float2* __restrict__ r2, int N, int G, bool vec) {
+    deapod_crop_block(grid, img, r2, N, G, vec);
 }
 
 // ---- forward: zero grid, place I_p / (phi^ phi^) at p mod G -----------------------------------
@@ -199,7 +195,10 @@ ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2*
 }
 
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s) {
-    k_deapod_crop<<<dim3((p.N + 255) / 256, p.N), 256, 0, s>>>(grid, img, p.deapod, p.N, p.G);
+    const dim3 blocks((p.N + 2 * kDeapodThreads - 1) / (2 * kDeapodThreads),
+                      (p.N + kDeapodRows - 1) / kDeapodRows);
+    k_deapod_crop<<<blocks, kDeapodThreads, 0, s>>>(grid, img, p.deapod2, p.N, p.G,
+                                                    deapod_vec_ok(grid, img, p.N));
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
 }

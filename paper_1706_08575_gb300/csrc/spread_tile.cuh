@@ -8,19 +8,29 @@ namespace ftcg {
 namespace tile {
 
 // Build-time knobs of the spreading kernels (the defaults are the tuned values):
-//   FTCG_SPREAD_THREADS  threads per CTA; FTCG_SPREAD_MINB  minimum resident CTAs per SM requested
-//   from the register allocator; FTCG_SPREAD_WINDOW  1 = rolling row window, 0 = one shared
-//   atomic per tap.
+//   FTCG_SPREAD_THREADS  threads per CTA;
+//   FTCG_SPREAD_MINB     minimum resident CTAs per SM requested from the register allocator;
+//   FTCG_SPREAD_UNROLL   unroll factor of the entry loop;
+//   FTCG_SPREAD_CPL8 / FTCG_SPREAD_CPL16  tap columns per lane for 4 < w <= 8 / 8 < w <= 16
+//                        (a group then has 8 / CPL8 resp. 16 / CPL16 lanes).
 #ifndef FTCG_SPREAD_THREADS
 #define FTCG_SPREAD_THREADS 256
 #endif
 #ifndef FTCG_SPREAD_MINB
 #define FTCG_SPREAD_MINB 4
 #endif
-#ifndef FTCG_SPREAD_WINDOW
-#define FTCG_SPREAD_WINDOW 1
+#ifndef FTCG_SPREAD_UNROLL
+#define FTCG_SPREAD_UNROLL 2
+#endif
+#ifndef FTCG_SPREAD_CPL8
+#define FTCG_SPREAD_CPL8 1
+#endif
+#ifndef FTCG_SPREAD_CPL16
+#define FTCG_SPREAD_CPL16 1
 #endif
 constexpr int kSpreadThreads = FTCG_SPREAD_THREADS;
+constexpr int kCpl8 = FTCG_SPREAD_CPL8, kCpl16 = FTCG_SPREAD_CPL16;
+constexpr int kSpreadUnroll = FTCG_SPREAD_UNROLL;
 
 // ES window in FP32: exp(beta (sqrt(1 - z^2) - 1)) written as exp(-beta z^2 / (1 + sqrt(1 - z^2)))
 // so that no cancellation occurs near the centre (sqrt(1 - z^2) - 1 loses all its digits there).
@@ -58,18 +68,20 @@ __host__ __device__ constexpr size_t tile_smem_bytes() {
            (size_t)(T + WMAX + 1) * sizeof(int);
 }
 
-// One tile, by the whole CTA. GW: lanes per group (power of two >= w); WT: compile-time w
-// (0 = runtime w <= GW). HALO: the tile's entries are the samples whose first tap lies in it;
-// the accumulator covers the tile plus w - 1 cells to the right and below, the tile's own cells go
-// to the grid and the overflow strips to halo_buf (added to the neighbours by k_halo_add).
-template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO>
+// One tile, by the whole CTA. GW: lanes per group (power of two); CPL: tap columns per lane
+// (lane l owns columns l, l + GW, ..., so GW * CPL >= w); WT: compile-time w (0 = runtime
+// w <= GW * CPL). HALO: the tile's entries are the samples whose first tap lies in it; the
+// accumulator covers the tile plus w - 1 cells to the right and below, the tile's own cells go to
+// the grid and the overflow strips to halo_buf (added to the neighbours by k_halo_add).
+template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL>
 __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
                                             const int* __restrict__ colptr,
                                             const void* __restrict__ vals,
                                             float2* __restrict__ grid, int G, int ntx, int Wrt,
                                             float beta, float inv_hw, int tile, float* smem,
                                             float2* __restrict__ halo_buf, int halo_cells) {
-    constexpr int WMAX = WT > 0 ? WT : GW;
+    constexpr int WMAX = WT > 0 ? WT : GW * CPL;
+    static_assert(WMAX <= GW * CPL, "a group must cover the kernel width");
     constexpr int PT = acc_side<T, WMAX, HALO>();
     constexpr int LD = PT + 1;
     constexpr int NG = kSpreadThreads / GW;
@@ -103,48 +115,104 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
     const int per = (n + NG - 1) / NG;
     const int a = e0 + g * per;
     const int b = min(e1, a + per);
-    const bool lane_tap = l < W;
-
-    float ar[WMAX], ai[WMAX];
+    bool tap[CPL];
 #pragma unroll
-    for (int r = 0; r < WMAX; ++r) ar[r] = ai[r] = 0.0f;
+    for (int c = 0; c < CPL; ++c) tap[c] = l + c * GW < W;
+
+    float ar[CPL][WMAX], ai[CPL][WMAX];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+#pragma unroll
+        for (int r = 0; r < WMAX; ++r) ar[c][r] = ai[c][r] = 0.0f;
     int cur_cx = -(1 << 30);   // column bin of the window (local first-tap column), none yet
     int yb = 0;                // local row of window slot 0
 
     // add the whole window to the tile (rows outside the tile belong to other tiles)
     auto flush_all = [&]() {
-        const int col = cur_cx + l;
-        const bool okx = lane_tap && (HALO || (col >= 0 && col < Tw));
 #pragma unroll
-        for (int r = 0; r < WMAX; ++r) {
-            const int row = yb + r;
-            if (okx && r < W && (HALO || (row >= 0 && row < Th))) {
-                atomicAdd(s_re + row * LD + col, ar[r]);
-                atomicAdd(s_im + row * LD + col, ai[r]);
+        for (int c = 0; c < CPL; ++c) {
+            const int col = cur_cx + l + c * GW;
+            const bool okx = tap[c] && (HALO || (col >= 0 && col < Tw));
+#pragma unroll
+            for (int r = 0; r < WMAX; ++r) {
+                const int row = yb + r;
+                if (okx && r < W && (HALO || (row >= 0 && row < Th))) {
+                    atomicAdd(s_re + row * LD + col, ar[c][r]);
+                    atomicAdd(s_im + row * LD + col, ai[c][r]);
+                }
+                ar[c][r] = ai[c][r] = 0.0f;
             }
-            ar[r] = ai[r] = 0.0f;
         }
     };
 
-    if (a < b) {
-        // the column bin of the first entry (last k with s_col[k] <= a), then walk the bins
+    // flush window row 0 (tile row yb) and shift the window by one row
+    auto advance_row = [&]() {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int col = cur_cx + l + c * GW;
+            if (tap[c] && (HALO || (col >= 0 && col < Tw && yb >= 0 && yb < Th))) {
+                atomicAdd(s_re + yb * LD + col, ar[c][0]);
+                atomicAdd(s_im + yb * LD + col, ai[c][0]);
+            }
+#pragma unroll
+            for (int r = 0; r + 1 < WMAX; ++r) {
+                ar[c][r] = ar[c][r + 1];
+                ai[c][r] = ai[c][r + 1];
+            }
+            ar[c][WMAX - 1] = ai[c][WMAX - 1] = 0.0f;
+        }
+        ++yb;
+    };
+
+    // add entry e (value v) to window rows 0..w-1
+    auto add_entry = [&](const Entry& e, float2 v) {
+        const float al = ABF ? bf16_bits_to_float(e.alpha) : __uint_as_float(e.alpha);
+        float xr[CPL], xi[CPL], fy[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const float fx = tap[c] ? es32(e.dx - (float)(l + c * GW), inv_hw, beta) : 0.0f;
+            fy[c] = tap[c] ? es32(e.dy - (float)(l + c * GW), inv_hw, beta) : 0.0f;
+            const float ax = al * fx;
+            xr[c] = v.x * ax;
+            xi[c] = v.y * ax;
+        }
+#pragma unroll
+        for (int r = 0; r < WMAX; ++r) {
+            // row factor r lives in lane r % GW, slot r / GW (zero for r >= W)
+            const float py = __shfl_sync(gmask, fy[r / GW], r % GW, GW);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                ar[c][r] = fmaf(xr[c], py, ar[c][r]);
+                ai[c][r] = fmaf(xi[c], py, ai[c][r]);
+            }
+        }
+    };
+
+    // the column bin of entry i (last k with s_col[k] <= i)
+    auto find_bin = [&](int i) {
         int lo = 0, hi = ncb - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (s_col[mid] <= a) lo = mid; else hi = mid - 1;
+            if (s_col[mid] <= i) lo = mid; else hi = mid - 1;
         }
-        int bin = lo;
+        return lo;
+    };
+
+    if (a < b) {
+        int bin = find_bin(a);
         int bin_end = s_col[bin + 1];
         cur_cx = bin - (W - 1);
         // every lane of the group reads the same entry (one broadcast load per group); entries
-        // are prefetched two ahead and values one ahead
+        // are prefetched two ahead and values one ahead (the entry array is padded, so the
+        // prefetch needs no bounds test)
         Entry ec = ent[a];
         float2 vc = load_value<VBF>(vals, ec.packed & kSampleMask);
-        Entry en = a + 1 < b ? ent[a + 1] : ec;
+        Entry en = ent[a + 1];
         yb = (int)(ec.packed >> kSampleBits) - (W - 1);
+#pragma unroll kSpreadUnroll
         for (int idx = a; idx < b; ++idx) {
-            const Entry e2 = idx + 2 < b ? ent[idx + 2] : en;
-            const float2 vn = idx + 1 < b ? load_value<VBF>(vals, en.packed & kSampleMask) : vc;
+            const Entry e2 = ent[idx + 2];
+            const float2 vn = load_value<VBF>(vals, en.packed & kSampleMask);
             const int cyl = (int)(ec.packed >> kSampleBits) - (W - 1);
             if (idx >= bin_end) {                // the next column bin (empty bins skipped)
                 flush_all();
@@ -158,48 +226,9 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
                 flush_all();
                 yb = cyl;
             } else {
-                while (yb < cyl) {               // rows below cyl are final for this column bin
-                    const int col = cur_cx + l;
-                    if (lane_tap && (HALO || (col >= 0 && col < Tw && yb >= 0 && yb < Th))) {
-                        atomicAdd(s_re + yb * LD + col, ar[0]);
-                        atomicAdd(s_im + yb * LD + col, ai[0]);
-                    }
-#pragma unroll
-                    for (int r = 0; r + 1 < WMAX; ++r) {
-                        ar[r] = ar[r + 1];
-                        ai[r] = ai[r + 1];
-                    }
-                    ar[WMAX - 1] = ai[WMAX - 1] = 0.0f;
-                    ++yb;
-                }
+                while (yb < cyl) advance_row();   // rows below cyl are final for this bin
             }
-            const float al = ABF ? bf16_bits_to_float(ec.alpha) : __uint_as_float(ec.alpha);
-            const float fx = lane_tap ? es32(ec.dx - (float)l, inv_hw, beta) : 0.0f;
-            const float fy = lane_tap ? es32(ec.dy - (float)l, inv_hw, beta) : 0.0f;
-            const float ax = al * fx;
-            const float xr = vc.x * ax, xi = vc.y * ax;
-#if FTCG_SPREAD_WINDOW
-#pragma unroll
-            for (int r = 0; r < WMAX; ++r) {
-                const float py = __shfl_sync(gmask, fy, r, GW);   // zero for r >= W
-                ar[r] = fmaf(xr, py, ar[r]);
-                ai[r] = fmaf(xi, py, ai[r]);
-            }
-#else
-            {
-                const int col = cur_cx + l;
-                const bool okx = lane_tap && col >= 0 && col < Tw;
-#pragma unroll
-                for (int r = 0; r < WMAX; ++r) {
-                    const float py = __shfl_sync(gmask, fy, r, GW);
-                    const int row = cyl + r;
-                    if (okx && r < W && row >= 0 && row < Th) {
-                        atomicAdd(s_re + row * LD + col, xr * py);
-                        atomicAdd(s_im + row * LD + col, xi * py);
-                    }
-                }
-            }
-#endif
+            add_entry(ec, vc);
             ec = en;
             vc = vn;
             en = e2;
@@ -263,10 +292,7 @@ __device__ __forceinline__ void halo_add_tile(const float2* __restrict__ halo_bu
         int gy = Y0 + y, gx = X0 + x;
         if (gy >= G) gy -= G;
         if (gx >= G) gx -= G;
-        const float2 v = hb[k];
-        float* dst = reinterpret_cast<float*>(grid + (int64_t)gy * G + gx);
-        atomicAdd(dst, v.x);
-        atomicAdd(dst + 1, v.y);
+        atomicAdd(grid + (int64_t)gy * G + gx, hb[k]);     // one 8-byte vector atomic
     }
 }
 

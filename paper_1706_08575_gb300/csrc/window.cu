@@ -98,4 +98,18 @@ ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cud
     return FTCG_SUCCESS;
 }
 
+__global__ void k_split_factors(const double* __restrict__ r, float2* __restrict__ r2, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float hi = __double2float_rn(r[i]);
+    r2[i] = make_float2(hi, __double2float_rn(r[i] - (double)hi));
+}
+
+ftcg_status_t split_factors(const double* r, float2* r2, int n, cudaStream_t s) {
+    if (n == 0) return FTCG_SUCCESS;
+    k_split_factors<<<(n + 127) / 128, 128, 0, s>>>(r, r2, n);
+    FTCG_CK(cudaGetLastError());
+    return FTCG_SUCCESS;
+}
+
 }  // namespace ftcg

@@ -117,6 +117,39 @@ def test_adjoint_and_spread_vs_oracle(F, M, N, sigma, w, spread, T, layout):
     assert O.rel_l2(grid, gref) < TOL
 
 
+@pytest.mark.parametrize("xlo,xhi", [(-3.0, 3.0), (6.0, 14.0), (-32.0, 32.0), (-31.0, -29.5)],
+                         ids=["wraps", "one-run", "all-columns", "edge"])
+def test_pruned_fft_column_runs(F, xlo, xhi):
+    """The inverse FFT transforms only the grid columns that taps reach (one or two periodic runs)
+    and only the rows of the crop: samples confined to a band of lambda_x around 0 (the occupied
+    columns wrap around G), off centre (one run), everywhere, and at the band edge."""
+    rng = np.random.default_rng(int(100 * (xlo + 40)))
+    M, N = 2500, 64
+    lam = np.stack([rng.uniform(xlo, xhi, M), rng.uniform(-32, 32, M)], axis=1)
+    v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    img, _ = _run_adjoint(F, lam, v, N, 2.0, 8)
+    ref = O.adjoint(lam, c64(v).astype(np.complex128), N, 2.0, 8)
+    assert O.rel_l2(img, ref) < TOL
+
+
+def test_image_at_8_byte_offset(F):
+    """An output image that is only 8-byte aligned takes the element-wise path of the window
+    division; N = 64 (the vector path otherwise) so both paths are compared on one raster."""
+    import torch
+    lam, v = sasgen.random_case(5, 3000, 64, 2.0, 8, 100)
+    vc = c64(v)
+    with F.Plan(dev(lam), 64, 2.0, 8) as p:
+        aligned = p.adjoint(dev(vc)).cpu().numpy()
+        buf = torch.zeros(64 * 64 + 1, dtype=torch.complex64, device="cuda")
+        view = buf[1:].view(64, 64)
+        assert view.data_ptr() % 16 == 8
+        p.adjoint(dev(vc), out=view)
+        shifted = view.cpu().numpy()
+    assert O.rel_l2(shifted, aligned) < 1e-6      # shared-memory atomics: order varies per call
+    ref = O.adjoint(lam, vc.astype(np.complex128), 64, 2.0, 8)
+    assert O.rel_l2(shifted, ref) < TOL
+
+
 def test_tiny_config(F):
     """The 4096-sample polar raster: weights, weighted image vs O2 and vs the direct sum."""
     p = sasgen.tiny()
