@@ -98,22 +98,48 @@ __global__ void k_cell_scatter(int64_t M, const int* __restrict__ cell, int* __r
         sorted[atomicAdd(cursor + cell[i], 1)] = (int)i;
 }
 
-// one thread per query; the best list is kept sorted by (distance^2, index) with static indices
+// Sorted copies of the coordinates: pts[s] = lambda_{sorted[s]} (FP64) and pts32[s] = the same
+// relative to the bounding-box corner, rounded to FP32 (for the candidate filter).
+__global__ void k_gather_pts(const double* __restrict__ lam, int64_t M, const int* __restrict__ sorted,
+                             double x0, double y0, double2* __restrict__ pts,
+                             float2* __restrict__ pts32) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < M;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int j = sorted[s];
+        const double x = lam[2 * j], y = lam[2 * j + 1];
+        pts[s] = make_double2(x, y);
+        pts32[s] = make_float2((float)(x - x0), (float)(y - y0));
+    }
+}
+
+// Exact 16 nearest neighbours, one thread per query, queries in cell order (a warp's queries are
+// neighbours). The ring search visits cells at Chebyshev distance r = 0, 1, ... and stops once the
+// 16th best squared distance is below (r h)^2. A candidate is first tested in FP32 against the
+// current 16th distance d16 with the slack T(d16) = 2^-16 d16 + 4 e sqrt(d16) + 4 e^2, where
+// e bounds the FP32 offset error (2^-24 of twice the bounding-box extent): a candidate whose FP32
+// distance exceeds d16 + T cannot beat d16 exactly. The others get the FP64 distance
+// (dx dx + dy dy, rounded like the brute force) and enter the list, ordered by (distance, index);
+// distances are compared as the integer images of their non-negative FP64 bit patterns.
 __global__ void __launch_bounds__(128)
     k_knn(const double* __restrict__ lam, const double* __restrict__ aux, int64_t M, Hash hs,
           const int* __restrict__ start, const int* __restrict__ sorted,
+          const double2* __restrict__ pts, const float2* __restrict__ pts32, float err,
           __nv_bfloat16* __restrict__ feat, int* __restrict__ nbr) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double xi = lam[2 * i], yi = lam[2 * i + 1];
-        const int cx = cell_of(xi, hs.x0, hs.inv_h, hs.nx), cy = cell_of(yi, hs.y0, hs.inv_h, hs.ny);
-        double bd[kNb];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = sorted[t];
+        const double2 pi = pts[t];
+        const float2 qi = pts32[t];
+        const int cx = cell_of(pi.x, hs.x0, hs.inv_h, hs.nx);
+        const int cy = cell_of(pi.y, hs.y0, hs.inv_h, hs.ny);
+        unsigned long long bk[kNb];
         int bj[kNb];
 #pragma unroll
         for (int k = 0; k < kNb; ++k) {
-            bd[k] = 1e300;
+            bk[k] = ~0ull;
             bj[k] = 0x7fffffff;
         }
+        float thr = INFINITY;
         const int rmax = max(hs.nx, hs.ny);
         for (int r = 0; r <= rmax; ++r) {
             for (int dy = -r; dy <= r; ++dy) {
@@ -124,37 +150,50 @@ __global__ void __launch_bounds__(128)
                     const int xx = cx + dx;
                     if (xx < 0 || xx >= hs.nx) continue;
                     const int c = yy * hs.nx + xx;
-                    for (int s = start[c]; s < start[c + 1]; ++s) {
-                        const int j = sorted[s];
-                        if (j == (int)i) continue;
-                        const double ddx = __dsub_rn(lam[2 * j], xi);
-                        const double ddy = __dsub_rn(lam[2 * j + 1], yi);
+                    const int s1 = start[c + 1];
+                    for (int s = start[c]; s < s1; ++s) {
+                        if (s == (int)t) continue;
+                        const float2 q = pts32[s];
+                        const float fx = q.x - qi.x, fy = q.y - qi.y;
+                        if (fmaf(fx, fx, fy * fy) > thr) continue;
+                        const double2 pj = pts[s];
+                        const double ddx = __dsub_rn(pj.x, pi.x);
+                        const double ddy = __dsub_rn(pj.y, pi.y);
                         const double d2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
-                        if (d2 > bd[kNb - 1] || (d2 == bd[kNb - 1] && j > bj[kNb - 1])) continue;
-                        bd[kNb - 1] = d2;
+                        const unsigned long long key = (unsigned long long)__double_as_longlong(d2);
+                        const int j = sorted[s];
+                        if (key > bk[kNb - 1] || (key == bk[kNb - 1] && j > bj[kNb - 1])) continue;
+                        bk[kNb - 1] = key;
                         bj[kNb - 1] = j;
 #pragma unroll
                         for (int k = kNb - 1; k > 0; --k) {
-                            const bool sw = bd[k] < bd[k - 1] || (bd[k] == bd[k - 1] && bj[k] < bj[k - 1]);
+                            const bool sw = bk[k] < bk[k - 1] || (bk[k] == bk[k - 1] && bj[k] < bj[k - 1]);
                             if (sw) {
-                                const double td = bd[k]; bd[k] = bd[k - 1]; bd[k - 1] = td;
+                                const unsigned long long tk = bk[k]; bk[k] = bk[k - 1]; bk[k - 1] = tk;
                                 const int tj = bj[k]; bj[k] = bj[k - 1]; bj[k - 1] = tj;
                             }
+                        }
+                        if (bj[kNb - 1] != 0x7fffffff) {
+                            const float d16 = (float)__longlong_as_double((long long)bk[kNb - 1]);
+                            thr = d16 + (d16 * 1.52587890625e-5f + 4.0f * err * sqrtf(d16) +
+                                         4.0f * err * err);
                         }
                     }
                 }
             }
             // unvisited samples lie at least r h away (less a rounding margin of the cell index)
             const double reach = r * hs.h * (1.0 - 1e-9);
-            if (bj[kNb - 1] != 0x7fffffff && bd[kNb - 1] < reach * reach) break;
+            if (bj[kNb - 1] != 0x7fffffff &&
+                __longlong_as_double((long long)bk[kNb - 1]) < reach * reach)
+                break;
         }
-        __nv_bfloat16* f = feat + i * kInPad;
+        __nv_bfloat16* f = feat + (int64_t)i * kInPad;
 #pragma unroll
         for (int k = 0; k < kNb; ++k) {
-            const int j = bj[k] == 0x7fffffff ? (int)i : bj[k];   // fewer than 16 samples in all
-            f[2 * k] = __double2bfloat16(__dsub_rn(lam[2 * j], xi));
-            f[2 * k + 1] = __double2bfloat16(__dsub_rn(lam[2 * j + 1], yi));
-            if (nbr) nbr[i * kNb + k] = bj[k] == 0x7fffffff ? -1 : bj[k];
+            const int j = bj[k] == 0x7fffffff ? i : bj[k];   // fewer than 16 samples in all
+            f[2 * k] = __double2bfloat16(__dsub_rn(lam[2 * j], pi.x));
+            f[2 * k + 1] = __double2bfloat16(__dsub_rn(lam[2 * j + 1], pi.y));
+            if (nbr) nbr[(int64_t)i * kNb + k] = bj[k] == 0x7fffffff ? -1 : bj[k];
         }
         f[2 * kNb] = __double2bfloat16(aux ? aux[i] : 0.0);
         for (int k = kIn; k < kInPad; ++k) f[k] = __float2bfloat16(0.f);
@@ -703,7 +742,7 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
         return FTCG_ERR_NUMERIC;
     }
     const double area = std::max((x1 - x0) * (y1 - y0), 1e-300);
-    double h = std::sqrt(2.0 * area / (double)M);
+    double h = std::sqrt(area / (double)M);           // one sample per bounding-box cell
     if (!(h > 0)) h = 1.0;
     Hash hs;
     hs.x0 = x0;
@@ -726,8 +765,15 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     FTCG_TRY(exclusive_scan_i32(cnt, start, ncell + 1, s));
     FTCG_CK(cudaMemcpyAsync(cnt, start, (ncell + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
     k_cell_scatter<<<nb(M, 256), 256, 0, s>>>(M, cell, cnt, sorted);
-    k_knn<<<nb(M, 128, 152 * 32), 128, 0, s>>>(d_lambda, d_aux, M, hs, start, sorted,
-                                                  reinterpret_cast<__nv_bfloat16*>(d_features),
+    double2* pts = nullptr;
+    float2* pts32 = nullptr;
+    FTCG_CK(cudaMalloc(&pts, M * sizeof(double2)));
+    FTCG_CK(cudaMalloc(&pts32, M * sizeof(float2)));
+    k_gather_pts<<<nb(M, 256), 256, 0, s>>>(d_lambda, M, sorted, x0, y0, pts, pts32);
+    // bound on the FP32 offset error: 2^-24 of twice the extent, with a 1% margin
+    const float err = (float)(2.0 * std::max(x1 - x0, y1 - y0) * 5.9604644775390625e-8 * 1.01);
+    k_knn<<<nb(M, 128, 152 * 32), 128, 0, s>>>(d_lambda, d_aux, M, hs, start, sorted, pts, pts32,
+                                                  err, reinterpret_cast<__nv_bfloat16*>(d_features),
                                                   d_neighbors);
     cudaError_t e = cudaGetLastError();
     cudaStreamSynchronize(s);
@@ -735,6 +781,8 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     cudaFree(start);
     cudaFree(cell);
     cudaFree(sorted);
+    cudaFree(pts);
+    cudaFree(pts32);
     FTCG_CK(e);
     return FTCG_SUCCESS;
 }

@@ -11,8 +11,21 @@
 // fine grid together with both window divisions, and S is a gridded forward transform at 2 lambda
 // (W3). alpha = 1 / Re S (W4); S >= 1 in exact arithmetic (the j = k term), so S <= 0 or a
 // non-finite S flags FTCG_ERR_NUMERIC.
+//
+// The W1 grid is real (unit strengths, real window), so H is Hermitian, and so is H c (c and the
+// window factors are real and even); the result of W3's transform is then real. The transforms
+// are therefore a real-to-complex FFT (D2Z, exponent sign -, which gives conj(H) for a real grid)
+// and a complex-to-real FFT (Z2D, sign +): conj(sum_m H(m) c(m) e^{-...}) = the real S grid. Both
+// are in place on a real grid padded to G + 2 doubles per row. W1 stores each sample's 2 w window
+// values so that W3 reads them instead of evaluating the window again.
 
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "ftcg_internal.cuh"
 
@@ -20,10 +33,25 @@ namespace ftcg {
 
 namespace {
 
-__device__ __forceinline__ double es64(double t, double inv_hw, double beta) {
-    double z = t * inv_hw;
-    double q = 1.0 - z * z;
-    return q >= 0.0 ? exp(beta * (sqrt(q) - 1.0)) : 0.0;
+// The window on the weight path, in FP64, as one polynomial per tap: the first-tap offset d lies in
+// (w/2 - 1, w/2], so tap l's argument d - l covers one unit interval, and with s = d - (w/2 - 1)
+// in (0, 1] phi(d - l) = p_l(2 s - 1). p_l has degree kPolyDeg and interpolates phi at the
+// Chebyshev points of its interval (coefficients from window_poly on the host). The end
+// intervals hold the window's square-root branch point, where phi = exp(-beta); the interpolation
+// error there is about exp(-beta) / 2 of phi(0) (6e-13 at w = 12, sigma = 2; 1e-10 at w = 12,
+// sigma = 1.25) and far smaller inside, i.e. at the level of the window's own truncation.
+constexpr int kPolyDeg = 14;
+constexpr int kPolyMaxW = 16;
+
+struct PolyCoef {
+    double c[kPolyMaxW][kPolyDeg + 1];   // c[l][k]: coefficient of x^k in p_l
+};
+
+__device__ __forceinline__ double poly_eval(const double* c, double x) {
+    double v = c[kPolyDeg];
+#pragma unroll
+    for (int k = kPolyDeg - 1; k >= 0; --k) v = fma(v, x, c[k]);
+    return v;
 }
 
 struct Origin64 {
@@ -53,61 +81,75 @@ __device__ __forceinline__ int wrapi(long long c, int G) {
 }
 
 // W1: g_l += phi(u_x - l_x) phi(u_y - l_y) (real, unit strengths), one 16-lane group per sample:
-// lane l evaluates tap l of both axes once, the row factors are broadcast by shuffles, and lane l
-// adds its column with FP64 global atomics on the real part of a complex128 grid.
+// lane l evaluates tap l of both axes once with its polynomial (and stores both values in the
+// sample's row of phi), the row factors are broadcast by shuffles, and lane l adds its column with
+// FP64 global atomics to the real grid (row stride ld).
 __global__ void __launch_bounds__(256)
-    k_w1_spread(const double* __restrict__ lam, int64_t M, double scale, int G, int W,
-                double beta, double inv_hw, double* __restrict__ grid) {
+    k_w1_spread(const double* __restrict__ lam, int64_t M, double scale, int G, int64_t ld, int W,
+                const PolyCoef* __restrict__ pc, double* __restrict__ grid,
+                double* __restrict__ phi) {
     const int l = threadIdx.x & 15;
     const unsigned gmask = 0xffffu << ((threadIdx.x & 31) & 16);
+    double c[kPolyDeg + 1];                  // this lane's tap polynomial
+#pragma unroll
+    for (int k = 0; k <= kPolyDeg; ++k) c[k] = l < W ? pc->c[l][k] : 0.0;
+    const double s0 = 0.5 * W - 1.0;
     const int64_t ngr = (int64_t)gridDim.x * (blockDim.x / 16);
     const int64_t j0 = blockIdx.x * (int64_t)(blockDim.x / 16) + threadIdx.x / 16;
     for (int64_t j = j0; j < M; j += ngr) {
         Origin64 ox = origin64(lam[2 * j], scale, W);
         Origin64 oy = origin64(lam[2 * j + 1], scale, W);
         if (!ox.ok || !oy.ok) continue;                       // uniform within the group
-        const double fx = l < W ? es64(ox.d - l, inv_hw, beta) : 0.0;
-        const double fyl = l < W ? es64(oy.d - l, inv_hw, beta) : 0.0;
+        const double fx = l < W ? poly_eval(c, 2.0 * (ox.d - s0) - 1.0) : 0.0;
+        const double fyl = l < W ? poly_eval(c, 2.0 * (oy.d - s0) - 1.0) : 0.0;
+        if (l < W) {
+            phi[j * 2 * W + l] = fx;
+            phi[j * 2 * W + W + l] = fyl;
+        }
         const int col = wrapi(ox.c + l, G);
         int row = wrapi(oy.c, G);
         for (int r = 0; r < W; ++r) {
             const double fy = __shfl_sync(gmask, fyl, r, 16);
-            if (l < W) atomicAdd(grid + 2 * ((int64_t)row * G + col), fx * fy);
+            if (l < W) atomicAdd(grid + (int64_t)row * ld + col, fx * fy);
             if (++row == G) row = 0;
         }
     }
 }
 
-// W2: on the fine grid after the inverse FFT, keep q = m mod G for m in {-N..N-1}^2 and multiply
-// by r(m_x) r(m_y) (adjoint window division) * c(m) * r(m_x) r(m_y) (forward window division);
-// zero every other cell. r has 2N entries for m = -N..N-1.
-__global__ void k_w2_lag(double2* __restrict__ grid, int G, int N, const double* __restrict__ r) {
-    const int64_t total = (int64_t)G * G;
+// W2: on the half spectrum of the real-to-complex transform (G rows x (G/2 + 1) columns) keep
+// q = m mod G for m in {-N..N-1}^2 and multiply by r(m_x) r(m_y) (adjoint window division) * c(m) *
+// r(m_x) r(m_y) (forward window division); zero every other cell. The columns q_x < N hold
+// m_x = q_x; m_x < 0 lies in the implicit conjugate half (q_x >= G - N > G / 2), and m_x = N
+// (q_x = N) has c = 0. r has 2N entries for m = -N..N-1.
+__global__ void k_w2_lag(double2* __restrict__ spec, int G, int N, const double* __restrict__ r) {
+    const int H = G / 2 + 1;
+    const int64_t total = (int64_t)G * H;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int qy = (int)(i / G), qx = (int)(i - (int64_t)qy * G);
-        int my = qy < N ? qy : (qy >= G - N ? qy - G : INT32_MIN);
-        int mx = qx < N ? qx : (qx >= G - N ? qx - G : INT32_MIN);
-        double2 v = grid[i];
-        if (my == INT32_MIN || mx == INT32_MIN) {
+        const int qy = (int)(i / H), qx = (int)(i - (int64_t)qy * H);
+        const int my = qy < N ? qy : (qy >= G - N ? qy - G : INT32_MIN);
+        double2 v = spec[i];
+        if (my == INT32_MIN || qx >= N) {
             v.x = 0.0;
             v.y = 0.0;
         } else {
+            const int mx = qx;
             const double ry = r[my + N], rx = r[mx + N];
-            const double cx = (double)(N - (mx < 0 ? -mx : mx)) / ((double)N * N);
+            const double cx = (double)(N - mx) / ((double)N * N);
             const double cy = (double)(N - (my < 0 ? -my : my)) / ((double)N * N);
             const double f = rx * rx * ry * ry * cx * cy;
             v.x *= f;
             v.y *= f;
         }
-        grid[i] = v;
+        spec[i] = v;
     }
 }
 
-// W3 + W4: S_k = sum_taps phi phi h_l at 2 lambda_k; alpha_k = 1 / Re S_k.
+// W3 + W4: S_k = sum_taps phi phi h_l at 2 lambda_k, with the window values W1 stored; alpha_k =
+// 1 / S_k.
 __global__ void __launch_bounds__(256)
-    k_w3_interp(const double* __restrict__ lam, int64_t M, double scale, int G, int W,
-                double beta, double inv_hw, const double2* __restrict__ grid,
+    k_w3_interp(const double* __restrict__ lam, int64_t M, double scale, int G, int64_t ld, int W,
+                const double* __restrict__ grid, const double* __restrict__ phi,
                 double* __restrict__ alpha, unsigned* __restrict__ status) {
     const int l = threadIdx.x & 15;
     const unsigned gmask = 0xffffu << ((threadIdx.x & 31) & 16);
@@ -118,13 +160,13 @@ __global__ void __launch_bounds__(256)
         const bool ok = ox.ok && oy.ok;                       // uniform within the group
         double sr = 0.0;
         if (ok) {
-            const double fx = l < W ? es64(ox.d - l, inv_hw, beta) : 0.0;
-            const double fyl = l < W ? es64(oy.d - l, inv_hw, beta) : 0.0;
+            const double fx = l < W ? phi[j * 2 * W + l] : 0.0;
+            const double fyl = l < W ? phi[j * 2 * W + W + l] : 0.0;
             const int col = wrapi(ox.c + l, G);
             int row = wrapi(oy.c, G);
             for (int r = 0; r < W; ++r) {
                 const double fy = __shfl_sync(gmask, fyl, r, 16);
-                if (l < W) sr += fy * grid[(int64_t)row * G + col].x;
+                if (l < W) sr += fy * grid[(int64_t)row * ld + col];
                 if (++row == G) row = 0;
             }
             sr *= fx;
@@ -152,91 +194,165 @@ int nblocks(int64_t n, int t) {
 
 }  // namespace
 
+namespace {
+
+// cuFFT plans of the lag grid, one pair per (device, G), created once and shared; they own no
+// workspace (each call passes its own), and their use is serialised by the mutex.
+struct LagFft {
+    cufftHandle d2z = 0, z2d = 0;
+    size_t ws = 0;
+};
+std::mutex g_lag_mu;
+std::map<std::pair<int, int>, LagFft> g_lag;
+
+ftcg_status_t lag_fft_locked(int G, LagFft* out) {
+    int dev = 0;
+    FTCG_CK(cudaGetDevice(&dev));
+    auto it = g_lag.find({dev, G});
+    if (it == g_lag.end()) {
+        LagFft f;
+        size_t w1 = 0, w2 = 0;
+        FTCG_CKFFT(cufftCreate(&f.d2z));
+        FTCG_CKFFT(cufftSetAutoAllocation(f.d2z, 0));
+        FTCG_CKFFT(cufftMakePlan2d(f.d2z, G, G, CUFFT_D2Z, &w1));
+        FTCG_CKFFT(cufftCreate(&f.z2d));
+        FTCG_CKFFT(cufftSetAutoAllocation(f.z2d, 0));
+        FTCG_CKFFT(cufftMakePlan2d(f.z2d, G, G, CUFFT_Z2D, &w2));
+        f.ws = std::max(w1, w2);
+        it = g_lag.emplace(std::make_pair(dev, G), f).first;
+    }
+    *out = it->second;
+    return FTCG_SUCCESS;
+}
+
+// Device buffers of one weight computation, released on every path.
+struct WeightBuffers {
+    double* r2 = nullptr;
+    double* grid = nullptr;
+    double* phi = nullptr;
+    void* work = nullptr;
+    PolyCoef* coef = nullptr;
+    double* alpha = nullptr;
+    bool own_alpha = false;
+    ~WeightBuffers() {
+        cudaFree(r2);
+        cudaFree(grid);
+        cudaFree(phi);
+        cudaFree(work);
+        cudaFree(coef);
+        if (own_alpha) cudaFree(alpha);
+    }
+};
+
+// p_l interpolates phi(s + w/2 - 1 - l), s = (x + 1) / 2, at the kPolyDeg + 1 Chebyshev points
+// x_i = cos(pi (i + 1/2) / n); the Chebyshev coefficients a_k = (2 - [k = 0]) / n sum_i f_i T_k(x_i)
+// are converted to powers of x with T_{k+1} = 2 x T_k - T_{k-1}.
+void window_poly(int W, double beta, PolyCoef* out) {
+    const double pi = 3.14159265358979323846;
+    const int n = kPolyDeg + 1;
+    auto phi_host = [&](double t) {
+        const double z = 2.0 * t / W;
+        const double q = 1.0 - z * z;
+        return q >= 0.0 ? std::exp(beta * (std::sqrt(q) - 1.0)) : 0.0;
+    };
+    for (int l = 0; l < kPolyMaxW; ++l)
+        for (int k = 0; k <= kPolyDeg; ++k) out->c[l][k] = 0.0;
+    for (int l = 0; l < W; ++l) {
+        double f[kPolyDeg + 1], a[kPolyDeg + 1];
+        for (int i = 0; i < n; ++i) {
+            const double x = std::cos(pi * (i + 0.5) / n);
+            f[i] = phi_host(0.5 * (x + 1.0) + 0.5 * W - 1.0 - l);
+        }
+        for (int k = 0; k < n; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += f[i] * std::cos(pi * k * (i + 0.5) / n);
+            a[k] = (k == 0 ? 1.0 : 2.0) * acc / n;
+        }
+        double tm[kPolyDeg + 1] = {0}, tc[kPolyDeg + 1] = {0}, tn[kPolyDeg + 1];
+        tm[0] = 1.0;                                 // T_0
+        tc[1] = 1.0;                                 // T_1
+        out->c[l][0] += a[0];
+        for (int k = 1; k < n; ++k) {
+            for (int j = 0; j <= kPolyDeg; ++j) out->c[l][j] += a[k] * tc[j];
+            if (k + 1 < n) {
+                for (int j = 0; j <= kPolyDeg; ++j)
+                    tn[j] = (j > 0 ? 2.0 * tc[j - 1] : 0.0) - tm[j];
+                for (int j = 0; j <= kPolyDeg; ++j) {
+                    tm[j] = tc[j];
+                    tc[j] = tn[j];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
 ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s) {
     if (p.M == 0) return FTCG_SUCCESS;
     const int Wa = p.opts.weight_width > 0 ? p.opts.weight_width : 12;
     const int N2 = 2 * p.N;
     const int G2 = 2 * p.G;                      // sigma * (2N)
+    const int64_t ld = G2 + 2;                   // real row stride of the in-place transforms
     const double scale = 2.0 * p.sigma;          // u = sigma * (2 lambda)
     Window wa{Wa, es_beta(Wa, p.sigma)};
-    const double inv_hw = 2.0 / Wa;
 
-    double* r2 = nullptr;
-    double2* g = nullptr;
-    double* alpha = d_alpha_out;
-    bool own_alpha = false;
-    unsigned before = 0;
-    const size_t gbytes = (size_t)G2 * G2 * sizeof(double2);
-    FTCG_CK(cudaMalloc(&r2, N2 * sizeof(double)));
-    cudaError_t e = cudaMalloc(&g, gbytes);
-    if (e != cudaSuccess) {
-        cudaFree(r2);
-        set_error("ftcg_weights: cannot allocate the %zu-byte FP64 lag grid", gbytes);
+    std::lock_guard<std::mutex> lk(g_lag_mu);
+    LagFft fft;
+    FTCG_TRY(lag_fft_locked(G2, &fft));
+    WeightBuffers b;
+    const size_t gbytes = (size_t)G2 * ld * sizeof(double);
+    const size_t pbytes = (size_t)p.M * 2 * Wa * sizeof(double);
+    if (cudaMalloc(&b.r2, N2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b.grid, gbytes) != cudaSuccess || cudaMalloc(&b.phi, pbytes) != cudaSuccess ||
+        cudaMalloc(&b.coef, sizeof(PolyCoef)) != cudaSuccess ||
+        (fft.ws > 0 && cudaMalloc(&b.work, fft.ws) != cudaSuccess)) {
+        cudaGetLastError();
+        set_error("ftcg_weights: cannot allocate the FP64 lag grid (%zu bytes), the window table "
+                  "(%zu bytes) or the FFT workspace (%zu bytes)", gbytes, pbytes, fft.ws);
         return FTCG_ERR_OUT_OF_MEMORY;
     }
-    if (!alpha) {
-        e = cudaMalloc(&alpha, p.M * sizeof(double));
-        if (e != cudaSuccess) {
-            cudaFree(r2);
-            cudaFree(g);
+    b.alpha = d_alpha_out;
+    if (!b.alpha) {
+        if (cudaMalloc(&b.alpha, p.M * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
             set_error("ftcg_weights: cannot allocate the weight array");
             return FTCG_ERR_OUT_OF_MEMORY;
         }
-        own_alpha = true;
+        b.own_alpha = true;
     }
-    cufftHandle plan2 = 0;
-    ftcg_status_t st = FTCG_SUCCESS;
-    do {
-        if ((st = window_factors(r2, N2, G2, wa, s)) != FTCG_SUCCESS) break;
-        if (cudaMemsetAsync(g, 0, gbytes, s) != cudaSuccess) { st = FTCG_ERR_CUDA; break; }
-        k_w1_spread<<<nblocks(p.M * 16, 256), 256, 0, s>>>(p.lambda, p.M, scale, G2, Wa, wa.beta,
-                                                            inv_hw, reinterpret_cast<double*>(g));
-        if (cufftPlan2d(&plan2, G2, G2, CUFFT_Z2Z) != CUFFT_SUCCESS) {
-            set_error("ftcg_weights: cufftPlan2d(Z2Z %d) failed", G2);
-            st = FTCG_ERR_CUDA;
-            break;
-        }
-        cufftSetStream(plan2, s);
-        if (cufftExecZ2Z(plan2, reinterpret_cast<cufftDoubleComplex*>(g),
-                         reinterpret_cast<cufftDoubleComplex*>(g), CUFFT_INVERSE) != CUFFT_SUCCESS) {
-            set_error("ftcg_weights: inverse Z2Z failed");
-            st = FTCG_ERR_CUDA;
-            break;
-        }
-        k_w2_lag<<<nblocks((int64_t)G2 * G2, 256), 256, 0, s>>>(g, G2, p.N, r2);
-        if (cufftExecZ2Z(plan2, reinterpret_cast<cufftDoubleComplex*>(g),
-                         reinterpret_cast<cufftDoubleComplex*>(g), CUFFT_FORWARD) != CUFFT_SUCCESS) {
-            set_error("ftcg_weights: forward Z2Z failed");
-            st = FTCG_ERR_CUDA;
-            break;
-        }
-        if (cudaMemcpyAsync(&before, p.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess) { st = FTCG_ERR_CUDA; break; }
-        k_w3_interp<<<nblocks(p.M * 16, 256), 256, 0, s>>>(p.lambda, p.M, scale, G2, Wa, wa.beta,
-                                                            inv_hw, g, alpha, p.status);
-        if (cudaGetLastError() != cudaSuccess) { st = FTCG_ERR_CUDA; break; }
-        if ((st = launch_set_alpha(p, alpha, FTCG_WEIGHTS_F64, s)) != FTCG_SUCCESS) break;
-        unsigned after = 0;
-        if (cudaMemcpyAsync(&after, p.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            set_error("ftcg_weights: %s", cudaGetErrorString(cudaGetLastError()));
-            st = FTCG_ERR_CUDA;
-            break;
-        }
-        if ((after & STATUS_BAD_WEIGHT_SUM) && !(before & STATUS_BAD_WEIGHT_SUM)) {
-            set_error("ftcg_weights: a weight sum S_k was <= 0 or not finite (weight set to 0)");
-            st = FTCG_ERR_NUMERIC;
-        }
-    } while (0);
-    if (st == FTCG_ERR_CUDA && ftcg_last_error()[0] == 0)
-        set_error("ftcg_weights: %s", cudaGetErrorString(cudaGetLastError()));
-    cudaStreamSynchronize(s);
-    if (plan2) cufftDestroy(plan2);
-    cudaFree(r2);
-    cudaFree(g);
-    if (own_alpha) cudaFree(alpha);
-    return st;
+    PolyCoef hc;
+    window_poly(Wa, wa.beta, &hc);
+    FTCG_CK(cudaMemcpyAsync(b.coef, &hc, sizeof(PolyCoef), cudaMemcpyHostToDevice, s));
+    FTCG_TRY(window_factors(b.r2, N2, G2, wa, s));
+    FTCG_CK(cudaMemsetAsync(b.grid, 0, gbytes, s));
+    k_w1_spread<<<nblocks(p.M * 16, 256), 256, 0, s>>>(p.lambda, p.M, scale, G2, ld, Wa, b.coef,
+                                                        b.grid, b.phi);
+    FTCG_CK(cudaGetLastError());
+    cufftDoubleComplex* spec = reinterpret_cast<cufftDoubleComplex*>(b.grid);
+    FTCG_CKFFT(cufftSetStream(fft.d2z, s));
+    FTCG_CKFFT(cufftSetWorkArea(fft.d2z, b.work));
+    FTCG_CKFFT(cufftExecD2Z(fft.d2z, b.grid, spec));
+    k_w2_lag<<<nblocks((int64_t)G2 * (G2 / 2 + 1), 256), 256, 0, s>>>(
+        reinterpret_cast<double2*>(b.grid), G2, p.N, b.r2);
+    FTCG_CK(cudaGetLastError());
+    FTCG_CKFFT(cufftSetStream(fft.z2d, s));
+    FTCG_CKFFT(cufftSetWorkArea(fft.z2d, b.work));
+    FTCG_CKFFT(cufftExecZ2D(fft.z2d, spec, b.grid));
+    unsigned before = 0;
+    FTCG_CK(cudaMemcpyAsync(&before, p.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    k_w3_interp<<<nblocks(p.M * 16, 256), 256, 0, s>>>(p.lambda, p.M, scale, G2, ld, Wa, b.grid,
+                                                        b.phi, b.alpha, p.status);
+    FTCG_CK(cudaGetLastError());
+    FTCG_TRY(launch_set_alpha(p, b.alpha, FTCG_WEIGHTS_F64, s));
+    unsigned after = 0;
+    FTCG_CK(cudaMemcpyAsync(&after, p.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    FTCG_CK(cudaStreamSynchronize(s));            // the buffers are freed on return
+    if ((after & STATUS_BAD_WEIGHT_SUM) && !(before & STATUS_BAD_WEIGHT_SUM)) {
+        set_error("ftcg_weights: a weight sum S_k was <= 0 or not finite (weight set to 0)");
+        return FTCG_ERR_NUMERIC;
+    }
+    return FTCG_SUCCESS;
 }
 
 }  // namespace ftcg

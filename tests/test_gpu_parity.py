@@ -212,6 +212,19 @@ def test_weights_random(F):
     assert np.max(np.abs(a - ab) / ab) < 1e-9
 
 
+@pytest.mark.parametrize("sigma,wa", [(2.0, 12), (1.5, 14), (1.25, 16), (2.0, 16), (2.0, 0)])
+def test_weights_widths(F, sigma, wa):
+    """The FP64 weight path at several oversampling factors and weight-window widths (0 = the
+    default 12), each wide enough that the gridding error of the lag sums is below the 1e-9 bar
+    (exp(-beta) <= 1e-12; at sigma = 2, w = 10 the gridding error alone is 2e-9), against the
+    brute-force Fejer sum."""
+    lam, _ = sasgen.random_case(37, 2500, 40, spread=36)
+    with F.Plan(dev(lam), 40, sigma, 8, weight_width=wa) as p:
+        a = p.weights().cpu().numpy()
+    ab, _ = O.weights_brute(lam, 40)
+    assert np.max(np.abs(a - ab) / ab) < 1e-9
+
+
 def test_weights_uniform_grid(F):
     N = 32
     g = np.arange(-N // 2, N // 2)
