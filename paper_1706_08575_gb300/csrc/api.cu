@@ -157,6 +157,11 @@ ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* im
     if (ev) FTCG_CK(cudaEventRecord(ev[0], s));
     FTCG_TRY(launch_spread(*p, vals, vdtype, p->grid, s));
     if (ev) FTCG_CK(cudaEventRecord(ev[1], s));
+    if (p->smem_fft) {                         // both passes, the second writes the image
+        FTCG_TRY(exec_smem_fft(p, reinterpret_cast<float2*>(img), s, ev ? ev[2] : nullptr));
+        if (ev) FTCG_CK(cudaEventRecord(ev[3], s));
+        return FTCG_SUCCESS;
+    }
     if (p->pruned_ok) {
         FTCG_TRY(exec_pruned_inverse(p, s));
     } else {

@@ -8,7 +8,9 @@
 //     at most two contiguous runs of the periodic column index);
 //   * of the row transforms only the N rows of the crop are needed.
 // The other cells of the grid are left as they are (never read). The arithmetic of every kept
-// output is that of a full 2-D inverse FFT, with cuFFT as the 1-D engine.
+// output is that of a full 2-D inverse FFT. For power-of-two G from 256 to 4096 the 1-D transforms
+// are this library's shared-memory kernels (fft_smem.cu, with the window division and crop fused
+// into the row pass); otherwise cuFFT is the 1-D engine.
 
 #include "ftcg_internal.cuh"
 
@@ -84,6 +86,9 @@ ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes) {
         FTCG_CK(cudaFreeAsync(d_occ, s));
         FTCG_CK(cudaStreamSynchronize(s));
         covering_interval(occ, &x0, &n);
+        if (smem_fft_supported(G)) return build_smem_fft(p, occ, s, bytes);
+    } else if (smem_fft_supported(G)) {
+        return build_smem_fft(p, std::vector<unsigned char>(G, 0), s, bytes);
     }
     // at most two runs of columns: [x0, min(G, x0 + n)) and [0, x0 + n - G)
     p->col_x0[0] = x0;
@@ -120,6 +125,7 @@ ftcg_status_t exec_pruned_inverse(Plan* p, cudaStream_t s) {
 }
 
 void release_pruned_fft(Plan* p) {
+    release_smem_fft(p);
     for (int k = 0; k < 2; ++k)
         if (p->fft_col[k]) cufftDestroy(p->fft_col[k]);
     if (p->fft_row) cufftDestroy(p->fft_row);

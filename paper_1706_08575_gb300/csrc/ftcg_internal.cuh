@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ftcg.h"
 
@@ -109,6 +110,13 @@ struct Plan {
     int col_x0[2] = {0, 0}, col_n[2] = {0, 0};
     cufftHandle fft_row = 0;
     bool pruned_ok = false;
+    // Shared-memory transforms for power-of-two G (fft_smem.cu): the column blocks that taps
+    // reach, and the FP32 twiddle tables of the transform stages.
+    bool smem_fft = false;
+    int* col_blocks = nullptr;
+    int n_col_blocks = 0;
+    unsigned* col_mask = nullptr;       // the same blocks as a bit mask
+    float2* tw = nullptr;
     unsigned* status = nullptr;         // device status word
     void* stage_vals = nullptr;         // ftcg_adjoint_host staging (device)
     void* stage_img = nullptr;
@@ -143,6 +151,13 @@ ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2*
                             cudaStream_t s);
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s);
 ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes);
+bool smem_fft_supported(int G);
+ftcg_status_t build_smem_fft(Plan* p, const std::vector<unsigned char>& occ, cudaStream_t s,
+                             int64_t* bytes);
+// the inverse transform and the window division + crop into img; mid (may be null) is recorded
+// between the column and the row pass
+ftcg_status_t exec_smem_fft(Plan* p, float2* img, cudaStream_t s, cudaEvent_t mid);
+void release_smem_fft(Plan* p);
 ftcg_status_t exec_pruned_inverse(Plan* p, cudaStream_t s);
 void release_pruned_fft(Plan* p);
 

@@ -132,6 +132,34 @@ def test_pruned_fft_column_runs(F, xlo, xhi):
     assert O.rel_l2(img, ref) < TOL
 
 
+@pytest.mark.parametrize("N,sigma,xlo,xhi", [
+    (128, 2.0, -3.0, 3.0), (128, 2.0, 6.0, 14.0), (256, 2.0, -128.0, 128.0),
+    (512, 2.0, -40.0, 90.0), (160, 1.6, -80.0, 80.0)])
+def test_smem_fft_sizes(F, N, sigma, xlo, xhi):
+    """Grid sides 256, 512 and 1024 take the shared-memory transforms (column blocks that taps
+    reach, then the crop's rows fused with the window division): whole images against the oracle,
+    with occupied columns that wrap, form one run, cover everything, or sit off centre."""
+    rng = np.random.default_rng(N + int(xlo))
+    M = 4000
+    lam = np.stack([rng.uniform(xlo, xhi, M), rng.uniform(-N / 2, N / 2, M)], axis=1)
+    v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    img, _ = _run_adjoint(F, lam, v, N, sigma, 8)
+    ref = O.adjoint(lam, c64(v).astype(np.complex128), N, sigma, 8)
+    assert O.rel_l2(img, ref) < image_tol(N, sigma, 8)
+
+
+def test_smem_fft_4096_sampled(F):
+    """G = 4096 (N = 2048): sampled pixels against the oracle one by one."""
+    rng = np.random.default_rng(7)
+    M, N = 3000, 2048
+    lam = np.stack([rng.uniform(-700, 300, M), rng.uniform(-1024, 1024, M)], axis=1)
+    v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    img, _ = _run_adjoint(F, lam, v, N, 2.0, 8)
+    pix = rng.integers(-N // 2, N // 2, size=(40, 2))
+    ref = O.adjoint_pixels(lam, c64(v).astype(np.complex128), N, 2.0, 8, pix)
+    assert O.rel_l2(img[pix[:, 1] + N // 2, pix[:, 0] + N // 2], ref) < TOL
+
+
 def test_image_at_8_byte_offset(F):
     """An output image that is only 8-byte aligned takes the element-wise path of the window
     division; N = 64 (the vector path otherwise) so both paths are compared on one raster."""
