@@ -155,7 +155,7 @@ ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* im
     cudaEvent_t* ev = nullptr;
     if (p->profiling && p->prof_calls < kMaxProfiled) ev = p->prof_ev + 4 * p->prof_calls++;
     if (ev) FTCG_CK(cudaEventRecord(ev[0], s));
-    FTCG_TRY(launch_spread(*p, vals, vdtype, p->grid, s));
+    FTCG_TRY(launch_spread(*p, vals, vdtype, p->grid, s, p->smem_fft));
     if (ev) FTCG_CK(cudaEventRecord(ev[1], s));
     if (p->smem_fft) {                         // both passes, the second writes the image
         FTCG_TRY(exec_smem_fft(p, reinterpret_cast<float2*>(img), s, ev ? ev[2] : nullptr));

@@ -84,6 +84,8 @@ struct Binning {
     int* colptr = nullptr;              // ntiles * ncb + 1 start offsets
     int* tile_order = nullptr;          // tiles by decreasing entry count (launch order)
     int n_nonempty = 0;                 // tiles with at least one entry (a prefix of tile_order)
+    int n_read = 0;                     // tiles the pruned inverse transform reads (a prefix of
+                                        // tile_order holding the non-empty ones; 0 = all)
     bool halo = false;                  // FTCG_LAYOUT_HALO: one entry per sample + halo strips
     int halo_cells = 0;                 // halo cells per tile
     float2* halo_buf = nullptr;         // ntiles * halo_cells overflow values (halo layout)
@@ -147,8 +149,10 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
 void free_binning(Binning& b);
 ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStream_t s);
 // spread.cu
+// pruned: only the tiles the pruned inverse transform reads (adjoint with shared-memory FFT);
+// otherwise every tile of the grid is stored
 ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2* grid,
-                            cudaStream_t s);
+                            cudaStream_t s, bool pruned = false);
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s);
 ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes);
 bool smem_fft_supported(int G);

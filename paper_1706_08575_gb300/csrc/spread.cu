@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256)
 }
 
 template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL = 1>
-ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
+ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
     const Binning& b = p.bin;
     constexpr int WMAX = WT > 0 ? WT : GW * CPL;
     const size_t smem = tile::tile_smem_bytes<T, WMAX, HALO>();
@@ -56,7 +56,7 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
                                  cudaSharedmemCarveoutMaxShared));
     const float beta = (float)p.win.beta;
     const float inv_hw = (float)(2.0 / p.win.w);
-    kern<<<b.ntiles, kSpreadThreads, smem, s>>>(b.ent, b.colptr, b.tile_order, vals, grid, b.G,
+    kern<<<nt, kSpreadThreads, smem, s>>>(b.ent, b.colptr, b.tile_order, vals, grid, b.G,
                                                 b.ntx, b.W, beta, inv_hw, b.halo_buf,
                                                 b.halo_cells);
     FTCG_CK(cudaGetLastError());
@@ -69,27 +69,27 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
 }
 
 template <int T, bool VBF, bool ABF, bool HALO>
-ftcg_status_t dispatch_w(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
+ftcg_status_t dispatch_w(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
     using tile::kCpl8;
     using tile::kCpl16;
     switch (p.w) {
-        case 6: return run_spread<8 / kCpl8, 6, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s);
-        case 8: return run_spread<8 / kCpl8, 8, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s);
+        case 6: return run_spread<8 / kCpl8, 6, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s, nt);
+        case 8: return run_spread<8 / kCpl8, 8, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s, nt);
         default:
-            if (p.w <= 4) return run_spread<4, 0, T, VBF, ABF, HALO>(p, vals, grid, s);
-            if (p.w <= 8) return run_spread<8 / kCpl8, 0, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s);
-            return run_spread<16 / kCpl16, 0, T, VBF, ABF, HALO, kCpl16>(p, vals, grid, s);
+            if (p.w <= 4) return run_spread<4, 0, T, VBF, ABF, HALO>(p, vals, grid, s, nt);
+            if (p.w <= 8) return run_spread<8 / kCpl8, 0, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s, nt);
+            return run_spread<16 / kCpl16, 0, T, VBF, ABF, HALO, kCpl16>(p, vals, grid, s, nt);
     }
 }
 
 template <bool VBF, bool ABF>
-ftcg_status_t dispatch_t(const Plan& p, const void* vals, float2* grid, cudaStream_t s) {
+ftcg_status_t dispatch_t(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
     if (p.bin.halo) {
-        if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, true>(p, vals, grid, s);
-        return dispatch_w<64, VBF, ABF, true>(p, vals, grid, s);
+        if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, true>(p, vals, grid, s, nt);
+        return dispatch_w<64, VBF, ABF, true>(p, vals, grid, s, nt);
     }
-    if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, false>(p, vals, grid, s);
-    return dispatch_w<64, VBF, ABF, false>(p, vals, grid, s);
+    if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, false>(p, vals, grid, s, nt);
+    return dispatch_w<64, VBF, ABF, false>(p, vals, grid, s, nt);
 }
 
 // ---- deapodisation and crop (the body is deapod_crop_block) -------------------------------------
@@ -181,17 +181,19 @@ int blocks_for(int64_t n, int threads) {
 }  // namespace
 
 ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2* grid,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool pruned) {
     if (p.bin.n_entries == 0) {
         FTCG_CK(cudaMemsetAsync(grid, 0, (size_t)p.G * p.G * sizeof(float2), s));
         return FTCG_SUCCESS;
     }
+    // the pruned transform reads only the tiles in the first n_read of the launch order
+    const int nt = pruned && p.bin.n_read > 0 ? p.bin.n_read : p.bin.ntiles;
     const bool vbf = vdtype == FTCG_VALUES_BF16X2;
     const bool abf = p.opts.precision == FTCG_PREC_BF16;
-    if (vbf && abf) return dispatch_t<true, true>(p, vals, grid, s);
-    if (vbf) return dispatch_t<true, false>(p, vals, grid, s);
-    if (abf) return dispatch_t<false, true>(p, vals, grid, s);
-    return dispatch_t<false, false>(p, vals, grid, s);
+    if (vbf && abf) return dispatch_t<true, true>(p, vals, grid, s, nt);
+    if (vbf) return dispatch_t<true, false>(p, vals, grid, s, nt);
+    if (abf) return dispatch_t<false, true>(p, vals, grid, s, nt);
+    return dispatch_t<false, false>(p, vals, grid, s, nt);
 }
 
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s) {
