@@ -483,6 +483,7 @@ def run_ours(args):
 
     info = plan.info
     G = info.G
+    smem_fft = 256 <= G <= 4096 and (G & (G - 1)) == 0
     alg_bytes = 20 * p.M + 8 * G * G              # spreading: 20 B per sample + the grid write
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (sp_ms * 1e-3) / 1e9
@@ -509,7 +510,9 @@ def run_ours(args):
                        "G": G, "tile": info.tile, "entries": info.entries,
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
-            "stages_ms": {"spread": sp_ms, "fft": fft_ms, "deapod_crop": dp_ms, "calls": ncalls},
+            "stages_ms": {"spread": sp_ms, "fft": fft_ms, "deapod_crop": dp_ms, "calls": ncalls,
+                          "note": ("fft = column pass; deapod_crop = row pass fused with the "
+                                   "window division and crop") if smem_fft else "cuFFT + k_deapod_crop"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(info.tile),
                          "kernel": "k_spread (+ k_halo_add in the halo layout: the spreading stage)",
@@ -521,8 +524,10 @@ def run_ours(args):
                          "adjoint_ms": 1e3 * pp[2]},
             "e2e": {"value": world * p.M / e2e_max, "unit": UNIT,
                     "h2d_bytes_per_step": int(p.M * 8), "d2h_bytes_per_step": int(p.N * p.N * 8)},
-            # per step: k_spread, k_halo_add (halo layout only), k_deapod_crop (cuFFT not counted)
-            "gpu_launches": (3 if info.layout == 2 else 2) * args.steps,
+            # per step: k_spread, k_halo_add (halo layout only), then for power-of-two G in
+            # 256..4096 the two shared-memory FFT passes (the second fused with the window
+            # division), otherwise k_deapod_crop after cuFFT (whose kernels are not counted)
+            "gpu_launches": ((2 if info.layout == 2 else 1) + (2 if smem_fft else 1)) * args.steps,
             "wall_s_timed_region": wall,
             "clocks": clk,
             "cpu_baseline": cpu,
