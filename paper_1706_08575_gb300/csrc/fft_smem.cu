@@ -200,6 +200,8 @@ __global__ void __launch_bounds__(kColThreads)
     static_assert(kColBlock == 4, "two float4 per row segment");
     constexpr int NV = (2 * L + kColThreads - 1) / kColThreads;   // float4 per thread
     extern __shared__ float2 sm[];
+    pdl_wait();                                // the grid is complete
+    pdl_allow_next();
     const int x0 = blocks[blockIdx.x] * kColBlock;
     float4 v[NV];
 #pragma unroll
@@ -243,6 +245,7 @@ __global__ void __launch_bounds__(row_threads(L))
     constexpr int NT = row_threads(L);
     constexpr int NV = (L / 2 + NT - 1) / NT;          // float4 (two columns) per thread
     extern __shared__ float2 sm[];
+    pdl_wait();                                // the column pass is complete
     const int iy = blockIdx.x;
     const int qy = iy - N / 2 < 0 ? iy - N / 2 + L : iy - N / 2;
     const float2* row = grid + (int64_t)qy * L;
@@ -300,13 +303,13 @@ ftcg_status_t run_smem_fft(const Plan& p, float2* img, cudaStream_t s, cudaEvent
     FTCG_CK(cudaFuncSetAttribute(k_fft_rows_crop<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smB));
     if (p.n_col_blocks > 0) {
-        k_fft_cols<L><<<p.n_col_blocks, kColThreads, smA, s>>>(p.grid, p.col_blocks, p.tw);
-        FTCG_CK(cudaGetLastError());
+        FTCG_CK(launch_pdl(k_fft_cols<L>, dim3(p.n_col_blocks), dim3(kColThreads), smA, s,
+                           p.grid, (const int*)p.col_blocks, (const float2*)p.tw));
     }
     if (mid) FTCG_CK(cudaEventRecord(mid, s));
-    k_fft_rows_crop<L><<<p.N, row_threads(L), smB, s>>>(p.grid, p.col_mask, p.tw, p.deapod2,
-                                                         p.N, img);
-    FTCG_CK(cudaGetLastError());
+    FTCG_CK(launch_pdl(k_fft_rows_crop<L>, dim3(p.N), dim3(row_threads(L)), smB, s,
+                       (const float2*)p.grid, (const unsigned*)p.col_mask, (const float2*)p.tw,
+                       (const float2*)p.deapod2, p.N, img));
     return FTCG_SUCCESS;
 }
 

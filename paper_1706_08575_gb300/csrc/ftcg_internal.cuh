@@ -75,6 +75,32 @@ struct Window {
     double beta;
 };
 
+// Launch with programmatic dependent launch: the kernel may be scheduled while the previous
+// kernel in the stream is finishing (its CTAs start once every CTA of that kernel has started or
+// signalled), and it must call pdl_wait() before reading what the previous kernel wrote.
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<K>(args)...);
+}
+
+// Wait until the previous kernel in the stream has completed and its writes are visible (a no-op
+// when the kernel was launched normally); let the next kernel's CTAs be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow_next() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // A binning of samples into square tiles of a G x G periodic grid.
 struct Binning {
     int G = 0, T = 0, W = 0;

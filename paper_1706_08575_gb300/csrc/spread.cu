@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
              float2* __restrict__ grid, int G, int ntx, int Wrt, float beta, float inv_hw,
              float2* __restrict__ halo_buf, int halo_cells) {
     extern __shared__ float smem[];
+    pdl_allow_next();                          // the fix-up may be scheduled during the tail
     const int t = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     tile::spread_tile<GW, WT, T, VBF, ABF, HALO, CPL>(ent, colptr, vals, grid, G, ntx, Wrt, beta,
                                                       inv_hw, t, smem, halo_buf, halo_cells);
@@ -41,6 +42,8 @@ __global__ void __launch_bounds__(256)
     k_halo_add(const float2* __restrict__ halo_buf, int halo_cells, const int* __restrict__ colptr,
                const int* __restrict__ tile_order, int ncb, float2* __restrict__ grid, int G,
                int T, int W, int ntx) {
+    pdl_wait();                                // the spreading kernel's tiles and strips
+    pdl_allow_next();
     tile::halo_add_tile(halo_buf, halo_cells, colptr, ncb, grid, G, T, W, ntx,
                         tile_order[blockIdx.x]);
 }
@@ -61,9 +64,9 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
                                                 b.halo_cells);
     FTCG_CK(cudaGetLastError());
     if (HALO && b.n_nonempty > 0) {
-        k_halo_add<<<b.n_nonempty, 256, 0, s>>>(b.halo_buf, b.halo_cells, b.colptr, b.tile_order,
-                                                b.ncb, grid, b.G, b.T, b.W, b.ntx);
-        FTCG_CK(cudaGetLastError());
+        FTCG_CK(launch_pdl(k_halo_add, dim3(b.n_nonempty), dim3(256), 0, s,
+                           (const float2*)b.halo_buf, b.halo_cells, (const int*)b.colptr,
+                           (const int*)b.tile_order, b.ncb, grid, b.G, b.T, b.W, b.ntx));
     }
     return FTCG_SUCCESS;
 }
