@@ -18,6 +18,7 @@
 #include <new>
 #include <vector>
 
+#include "fft_smem.cuh"
 #include "spread_tile.cuh"
 
 namespace ftcg {
@@ -32,8 +33,10 @@ struct PingDesc {
     float2* img;
     const float2* deapod2;
     float2* halo_buf;
+    const unsigned* col_mask;    // shared-memory FFT: column blocks that taps reach
     int G, ntx, T, N;
     int halo, halo_cells, ncb, W;
+    int fused;                   // 1: the row pass writes the image (no k_deapod_batch)
 };
 
 template <int GW, int WT, bool VBF, bool ABF, int CPL>
@@ -84,10 +87,30 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(kDeapodThreads) k_deapod_batch(const PingDesc* __restrict__ desc) {
     const PingDesc d = desc[blockIdx.z];
-    if (blockIdx.y * kDeapodRows >= d.N) return;
+    if (d.fused || blockIdx.y * kDeapodRows >= d.N) return;
     const bool vec = d.N % 4 == 0 && (reinterpret_cast<uintptr_t>(d.grid) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(d.img) & 15) == 0;
     deapod_crop_block(d.grid, d.img, d.deapod2, d.N, d.G, vec);
+}
+
+// Shared-memory FFT passes of a size class with power-of-two side L: the column pass over the
+// class's (ping, column block) items, then one CTA per (image row, ping of the class).
+template <int L>
+__global__ void __launch_bounds__(sfft::kColThreads)
+    k_fft_cols_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items,
+                     const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    const int2 it = items[blockIdx.x];
+    sfft::cols_body<L>(desc[it.x].grid, it.y * sfft::kColBlock, tw, sm);
+}
+
+template <int L>
+__global__ void __launch_bounds__(sfft::row_threads(L))
+    k_fft_rows_batch(const PingDesc* __restrict__ desc, const int* __restrict__ pings,
+                     const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    const PingDesc d = desc[pings[blockIdx.y]];
+    sfft::rows_body<L>(d.grid, d.col_mask, tw, d.deapod2, d.N, d.img, blockIdx.x, sm);
 }
 
 template <int WMAX>
@@ -209,10 +232,17 @@ struct Batch {
     ftcg_opts_t opts{};
     std::vector<Plan*> pings;
     struct Class {
-        int G = 0, count = 0;
+        int G = 0, count = 0, N = 0;
         float2* grids = nullptr;
         cufftHandle fft = 0;
         bool fft_ok = false;
+        // shared-memory FFT (power-of-two G in 256..4096): twiddle tables, (ping, column block)
+        // items of the column pass, and the class's pings for the row pass
+        bool smem = false;
+        float2* tw = nullptr;
+        int2* col_items = nullptr;
+        int n_col_items = 0;
+        int* pings = nullptr;
     };
     std::vector<Class> classes;
     std::vector<int> cls_of, slot_of;
@@ -236,6 +266,9 @@ void release_batch(Batch* b) {
     for (auto& c : b->classes) {
         if (c.grids) cudaFree(c.grids);
         if (c.fft_ok) cufftDestroy(c.fft);
+        if (c.tw) cudaFree(c.tw);
+        if (c.col_items) cudaFree(c.col_items);
+        if (c.pings) cudaFree(c.pings);
     }
     if (b->h_desc) cudaFreeHost(b->h_desc);
     if (b->d_desc) cudaFree(b->d_desc);
@@ -282,6 +315,48 @@ ftcg_status_t launch_batch_spread_w(Batch& b, cudaStream_t s) {
     }
 }
 
+template <int L>
+ftcg_status_t launch_class_fft_t(Batch& b, const Batch::Class& c, cudaStream_t s) {
+    const size_t smA = (size_t)sfft::kColBlock * sfft::col_stride(L) * sizeof(float2);
+    const size_t smB = (size_t)sfft::padded_len(L) * sizeof(float2);
+    FTCG_CK(cudaFuncSetAttribute(k_fft_cols_batch<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smA));
+    FTCG_CK(cudaFuncSetAttribute(k_fft_rows_batch<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smB));
+    if (c.n_col_items > 0) {
+        k_fft_cols_batch<L><<<c.n_col_items, sfft::kColThreads, smA, s>>>(b.d_desc, c.col_items,
+                                                                          c.tw);
+        FTCG_CK(cudaGetLastError());
+    }
+    k_fft_rows_batch<L><<<dim3(c.N, c.count), sfft::row_threads(L), smB, s>>>(b.d_desc, c.pings,
+                                                                             c.tw);
+    FTCG_CK(cudaGetLastError());
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t launch_class_fft(Batch& b, const Batch::Class& c, cudaStream_t s) {
+    switch (c.G) {
+        case 256: return launch_class_fft_t<256>(b, c, s);
+        case 512: return launch_class_fft_t<512>(b, c, s);
+        case 1024: return launch_class_fft_t<1024>(b, c, s);
+        case 2048: return launch_class_fft_t<2048>(b, c, s);
+        case 4096: return launch_class_fft_t<4096>(b, c, s);
+        default:
+            set_error("internal: no shared-memory FFT for G = %d", c.G);
+            return FTCG_ERR_NOT_SUPPORTED;
+    }
+}
+
+std::vector<float2> class_twiddles(int G) {
+    switch (G) {
+        case 256: return sfft::stage_twiddles<256>();
+        case 512: return sfft::stage_twiddles<512>();
+        case 1024: return sfft::stage_twiddles<1024>();
+        case 2048: return sfft::stage_twiddles<2048>();
+        default: return sfft::stage_twiddles<4096>();
+    }
+}
+
 ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, void* const* imgs,
                             cudaStream_t s) {
     for (int i = 0; i < b.n; ++i) {
@@ -302,11 +377,18 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
         k_halo_add_batch<<<b.nitems, 256, 0, s>>>(b.d_desc, b.d_items);
         FTCG_CK(cudaGetLastError());
     }
+    bool any_cufft = false;
     for (auto& c : b.classes) {
+        if (c.smem) {
+            FTCG_TRY(launch_class_fft(b, c, s));
+            continue;
+        }
+        any_cufft = true;
         FTCG_CKFFT(cufftSetStream(c.fft, s));
         FTCG_CKFFT(cufftExecC2C(c.fft, reinterpret_cast<cufftComplex*>(c.grids),
                                 reinterpret_cast<cufftComplex*>(c.grids), CUFFT_INVERSE));
     }
+    if (!any_cufft) return FTCG_SUCCESS;
     const dim3 blocks((b.max_N + 2 * kDeapodThreads - 1) / (2 * kDeapodThreads),
                       (b.max_N + kDeapodRows - 1) / kDeapodRows, b.n);
     k_deapod_batch<<<blocks, kDeapodThreads, 0, s>>>(b.d_desc);
@@ -358,6 +440,11 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         const size_t per = (size_t)c.G * c.G;
         FTCG_CK(cudaMalloc(&c.grids, per * c.count * sizeof(float2)));
         b.device_bytes += (int64_t)(per * c.count * sizeof(float2));
+        c.N = (int)std::llround(c.G / b.sigma);
+        if (smem_fft_supported(c.G)) {
+            c.smem = true;
+            continue;                       // set up with the descriptors below
+        }
         int dims[2] = {c.G, c.G};
         FTCG_CKFFT(cufftPlanMany(&c.fft, 2, dims, nullptr, 1, (int)per, nullptr, 1, (int)per,
                                  CUFFT_C2C, c.count));
@@ -393,11 +480,58 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         d.halo_cells = bn.halo_cells;
         d.ncb = bn.ncb;
         d.W = bn.W;
+        d.col_mask = nullptr;
+        d.fused = c.smem ? 1 : 0;
         b.any_halo = b.any_halo || bn.halo;
         std::vector<int> cp((size_t)bn.ntiles * bn.ncb + 1);
         FTCG_CK(cudaMemcpy(cp.data(), bn.colptr, cp.size() * sizeof(int), cudaMemcpyDeviceToHost));
         for (int t = 0; t < bn.ntiles; ++t)
             items.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t});
+    }
+    // shared-memory FFT classes: per ping the column blocks that taps reach (items of the column
+    // pass and a bit mask for the row pass), per class the twiddles and the ping list
+    std::vector<std::vector<int2>> col_items(b.classes.size());
+    std::vector<std::vector<int>> cls_pings(b.classes.size());
+    for (int i = 0; i < b.n; ++i) {
+        const int ci = b.cls_of[i];
+        if (!b.classes[ci].smem) continue;
+        Plan* p = b.pings[i];
+        std::vector<unsigned char> occ;
+        FTCG_TRY(column_occupancy(p, s, &occ));
+        const int nblk = p->G / sfft::kColBlock;
+        std::vector<unsigned> mask((nblk + 31) / 32, 0u);
+        for (int k = 0; k < nblk; ++k) {
+            bool any = false;
+            for (int c = 0; c < sfft::kColBlock; ++c) any = any || occ[k * sfft::kColBlock + c];
+            if (!any) continue;
+            col_items[ci].push_back(make_int2(i, k));
+            mask[k >> 5] |= 1u << (k & 31);
+        }
+        FTCG_CK(cudaMalloc(&p->col_mask, mask.size() * sizeof(unsigned)));
+        FTCG_CK(cudaMemcpy(p->col_mask, mask.data(), mask.size() * sizeof(unsigned),
+                           cudaMemcpyHostToDevice));
+        b.device_bytes += (int64_t)(mask.size() * sizeof(unsigned));
+        b.h_desc[i].col_mask = p->col_mask;
+        cls_pings[ci].push_back(i);
+    }
+    for (size_t ci = 0; ci < b.classes.size(); ++ci) {
+        auto& c = b.classes[ci];
+        if (!c.smem) continue;
+        const std::vector<float2> tw = class_twiddles(c.G);
+        FTCG_CK(cudaMalloc(&c.tw, tw.size() * sizeof(float2)));
+        FTCG_CK(cudaMemcpy(c.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        c.n_col_items = (int)col_items[ci].size();
+        if (c.n_col_items > 0) {
+            FTCG_CK(cudaMalloc(&c.col_items, col_items[ci].size() * sizeof(int2)));
+            FTCG_CK(cudaMemcpy(c.col_items, col_items[ci].data(), col_items[ci].size() * sizeof(int2),
+                               cudaMemcpyHostToDevice));
+        }
+        FTCG_CK(cudaMalloc(&c.pings, cls_pings[ci].size() * sizeof(int)));
+        FTCG_CK(cudaMemcpy(c.pings, cls_pings[ci].data(), cls_pings[ci].size() * sizeof(int),
+                           cudaMemcpyHostToDevice));
+        b.device_bytes += (int64_t)(tw.size() * sizeof(float2) +
+                                    col_items[ci].size() * sizeof(int2) +
+                                    cls_pings[ci].size() * sizeof(int));
     }
     std::stable_sort(items.begin(), items.end(),
                      [](const Item& x, const Item& y) { return x.cnt > y.cnt; });

@@ -71,20 +71,27 @@ cufftResult plan_columns(cufftHandle* h, int G, int batch) {
 
 }  // namespace
 
+ftcg_status_t column_occupancy(const Plan* p, cudaStream_t s, std::vector<unsigned char>* occ) {
+    occ->assign(p->G, 0);
+    if (p->M == 0) return FTCG_SUCCESS;
+    unsigned char* d_occ = nullptr;
+    FTCG_CK(cudaMallocAsync(&d_occ, p->G, s));
+    FTCG_CK(cudaMemsetAsync(d_occ, 0, p->G, s));
+    const int blocks = (int)std::min<int64_t>((p->M + 255) / 256, 4096);
+    k_col_occupancy<<<blocks, 256, 0, s>>>(p->samp, p->M, p->G, p->w, d_occ);
+    FTCG_CK(cudaGetLastError());
+    FTCG_CK(cudaMemcpyAsync(occ->data(), d_occ, p->G, cudaMemcpyDeviceToHost, s));
+    FTCG_CK(cudaFreeAsync(d_occ, s));
+    FTCG_CK(cudaStreamSynchronize(s));
+    return FTCG_SUCCESS;
+}
+
 ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes) {
     const int G = p->G, N = p->N;
     int x0 = 0, n = 0;
     if (p->M > 0) {
-        unsigned char* d_occ = nullptr;
-        FTCG_CK(cudaMallocAsync(&d_occ, G, s));
-        FTCG_CK(cudaMemsetAsync(d_occ, 0, G, s));
-        const int blocks = (int)std::min<int64_t>((p->M + 255) / 256, 4096);
-        k_col_occupancy<<<blocks, 256, 0, s>>>(p->samp, p->M, G, p->w, d_occ);
-        FTCG_CK(cudaGetLastError());
-        std::vector<unsigned char> occ(G);
-        FTCG_CK(cudaMemcpyAsync(occ.data(), d_occ, G, cudaMemcpyDeviceToHost, s));
-        FTCG_CK(cudaFreeAsync(d_occ, s));
-        FTCG_CK(cudaStreamSynchronize(s));
+        std::vector<unsigned char> occ;
+        FTCG_TRY(column_occupancy(p, s, &occ));
         covering_interval(occ, &x0, &n);
         if (smem_fft_supported(G)) return build_smem_fft(p, occ, s, bytes);
     } else if (smem_fft_supported(G)) {

@@ -1,0 +1,283 @@
+// Shared-memory 1-D FFTs of power-of-two length (256..4096) along the columns and rows of a
+// G x G grid: the Stockham stages, twiddle tables and the two pass bodies used by the single-ping
+// kernels (fft_smem.cu) and the batched ones (batch.cu). See fft_smem.cu for the method.
+#pragma once
+
+#include "ftcg_internal.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace ftcg {
+namespace sfft {
+namespace {
+
+constexpr int kColBlock = 4;                  // grid columns per pass-A CTA
+constexpr int kColThreads = 512;
+
+__host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
+// distance between the transforms of a block in shared memory: 4 extra elements shift each
+// column by 8 banks, so that the row-wise loads and stores of a block do not collide
+__host__ __device__ constexpr int col_stride(int L) { return padded_len(L) + 4; }
+
+// radix of stage s for a transform of length L: 16 while at least 16 remains, then the rest
+__host__ __device__ constexpr int stage_radix(int L, int s) {
+    int rem = L;
+    for (int i = 0; i < s; ++i) rem /= (rem >= 16 ? 16 : rem);
+    return rem >= 16 ? 16 : rem;
+}
+__host__ __device__ constexpr int num_stages(int L) {
+    int n = 0;
+    for (int rem = L; rem > 1; rem /= (rem >= 16 ? 16 : rem)) ++n;
+    return n;
+}
+__host__ __device__ constexpr int log2i(int x) {
+    int n = 0;
+    while ((1 << n) < x) ++n;
+    return n;
+}
+// transforms already done before stage S
+__host__ __device__ constexpr int stage_ns(int L, int S) {
+    int ns = 1;
+    for (int i = 0; i < S; ++i) ns *= stage_radix(L, i);
+    return ns;
+}
+// Twiddle table: for stage S (radix R, NS, step L / (NS R)) the entries w^(2^i k L / (NS R)),
+// i < log2 R, k < NS, at tw_offset(L, S) + i NS + k, so that lanes with consecutive k read
+// consecutive entries.
+__host__ __device__ constexpr int tw_offset(int L, int S) {
+    int off = 0;
+    for (int i = 0; i < S; ++i) off += log2i(stage_radix(L, i)) * stage_ns(L, i);
+    return off;
+}
+__host__ __device__ constexpr int tw_total(int L) { return tw_offset(L, num_stages(L)); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// cos(2 pi m / 16), m = 0..15
+__constant__ float kCos16[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f,
+                                 0.38268343236508977f, 0.0f, -0.38268343236508977f,
+                                 -0.70710678118654752f, -0.92387953251128674f, -1.0f,
+                                 -0.92387953251128674f, -0.70710678118654752f,
+                                 -0.38268343236508977f, 0.0f, 0.38268343236508977f,
+                                 0.70710678118654752f, 0.92387953251128674f};
+
+// exp(+2 pi i m / 16) for a compile-time m; sin(t) = cos(t - pi/2)
+template <int m>
+__device__ __forceinline__ float2 unit16() {
+    return make_float2(kCos16[m & 15], kCos16[(m + 12) & 15]);
+}
+
+__host__ __device__ constexpr int bitrev(int i, int R) {
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
+    return r;
+}
+
+// Butterflies of length LEN over v (radix-2 decimation in time), for every block i, offset k.
+template <int R, int LEN, int K = 0>
+__device__ __forceinline__ void butterflies(float2 (&v)[R]) {
+    if constexpr (K < LEN / 2) {
+#pragma unroll
+        for (int i = 0; i < R; i += LEN) {
+            const float2 a = v[i + K];
+            const float2 b = K == 0 ? v[i + K + LEN / 2]
+                                    : cmul(v[i + K + LEN / 2], unit16<K * (16 / LEN)>());
+            v[i + K] = make_float2(a.x + b.x, a.y + b.y);
+            v[i + K + LEN / 2] = make_float2(a.x - b.x, a.y - b.y);
+        }
+        butterflies<R, LEN, K + 1>(v);
+    }
+}
+
+template <int R, int LEN = 2>
+__device__ __forceinline__ void levels(float2 (&v)[R]) {
+    if constexpr (LEN <= R) {
+        butterflies<R, LEN>(v);
+        levels<R, LEN * 2>(v);
+    }
+}
+
+// V_q = sum_r v_r exp(+2 pi i r q / R) in place (R <= 16): bit-reversed reordering, then log2 R
+// levels of butterflies
+template <int R>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+    float2 t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) t[i] = v[bitrev(i, R)];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = t[i];
+    levels<R>(v);
+}
+
+// One Stockham stage (radix R, NS transforms of size NS already done) over CB transforms of length
+// L stored at s + c * col_stride(L), by NT threads. Every size is a compile-time constant; the
+// first radix is 16 (or L), so NS is 1 or a multiple of 16 and the padded addresses of a
+// butterfly's values are its first address plus constant offsets.
+template <int L, int R, int NS, int CB, int NT, int S>
+__device__ __forceinline__ void stage(float2* s, const float2* __restrict__ tw) {
+    constexpr int NJ = L / R;
+    constexpr int NB = CB * NJ;
+    constexpr int BPT = (NB + NT - 1) / NT;
+    constexpr int IN_STEP = padded(NJ);               // NJ is a multiple of 16 (or the stride is 1)
+    constexpr int OUT_STEP = NS == 1 ? 1 : padded(NS);
+    static_assert(NJ % 16 == 0, "input stride must keep the padding linear");
+    static_assert(NS == 1 || NS % 16 == 0, "output stride must keep the padding linear");
+    float2 v[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int id = threadIdx.x + b * NT;
+        if (NB % NT == 0 || id < NB) {
+            const int c = id / NJ, j = id - (id / NJ) * NJ;
+            const float2* src = s + c * col_stride(L) + padded(j);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = src[r * IN_STEP];
+            if constexpr (NS > 1) {                   // the first stage has k = 0
+                // w^(r k TSTEP) for the powers of two r from the table, the rest as products
+                // of at most three table values
+                const int k = j & (NS - 1);
+                const float2* t = tw + tw_offset(L, S) + k;
+                float2 w[R];
+#pragma unroll
+                for (int p2 = 1, i = 0; p2 < R; p2 *= 2, ++i) {
+                    w[p2] = __ldg(t + i * NS);
+#pragma unroll
+                    for (int q = 1; q < p2; ++q) w[p2 + q] = cmul(w[p2], w[q]);
+                }
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int id = threadIdx.x + b * NT;
+        if (NB % NT == 0 || id < NB) {
+            const int c = id / NJ, j = id - (id / NJ) * NJ;
+            const int k = j & (NS - 1);
+            dft<R>(v[b]);
+            float2* dst = s + c * col_stride(L) + padded((j - k) * R + k);
+#pragma unroll
+            for (int q = 0; q < R; ++q) dst[q * OUT_STEP] = v[b][q];
+        }
+    }
+    __syncthreads();
+}
+
+template <int L, int CB, int NT, int S = 0, int NS = 1>
+__device__ __forceinline__ void transform(float2* s, const float2* __restrict__ tw) {
+    if constexpr (S < num_stages(L)) {
+        constexpr int R = stage_radix(L, S);
+        stage<L, R, NS, CB, NT, S>(s, tw);
+        transform<L, CB, NT, S + 1, NS * R>(s, tw);
+    }
+}
+
+// pass A: transform along y the kColBlock columns starting at blocks[blockIdx.x] * kColBlock.
+// Each grid row segment of the block is two 16-byte vectors; all of a thread's loads are issued
+// before the first shared-memory store.
+__host__ __device__ constexpr int row_threads(int L) { return L / 16 >= 32 ? L / 16 : 32; }
+
+// pass A body: transform along y the kColBlock columns x0 .. x0 + kColBlock - 1 of the L x L grid.
+// Each grid row segment of the block is two 16-byte vectors; all of a thread's loads are issued
+// before the first shared-memory store. sm: kColBlock * col_stride(L) elements.
+template <int L>
+__device__ __forceinline__ void cols_body(float2* __restrict__ grid, int x0,
+                                          const float2* __restrict__ tw, float2* sm) {
+    static_assert(kColBlock == 4, "two float4 per row segment");
+    constexpr int NV = (2 * L + kColThreads - 1) / kColThreads;   // float4 per thread
+    float4 v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int e = threadIdx.x + k * kColThreads;  // (row, half) = (e / 2, e % 2)
+        if (e < 2 * L)
+            v[k] = *reinterpret_cast<const float4*>(grid + (int64_t)(e >> 1) * L + x0 + 2 * (e & 1));
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int e = threadIdx.x + k * kColThreads;
+        const int y = e >> 1, c = 2 * (e & 1);
+        if (e < 2 * L) {
+            sm[c * col_stride(L) + padded(y)] = make_float2(v[k].x, v[k].y);
+            sm[(c + 1) * col_stride(L) + padded(y)] = make_float2(v[k].z, v[k].w);
+        }
+    }
+    __syncthreads();
+    transform<L, kColBlock, kColThreads>(sm, tw);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int e = threadIdx.x + k * kColThreads;
+        const int y = e >> 1, c = 2 * (e & 1);
+        if (e >= 2 * L) continue;
+        const float2 a = sm[c * col_stride(L) + padded(y)];
+        const float2 b = sm[(c + 1) * col_stride(L) + padded(y)];
+        *reinterpret_cast<float4*>(grid + (int64_t)y * L + x0 + c) = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// pass B body: image row iy from grid row (iy - N/2) mod L, transformed along x; the N kept
+// frequencies are divided by the window transforms (FP32 pairs, see df_product). Only the column
+// blocks marked in mask (the ones taps reach) are read; the others are zero.
+// sm: padded_len(L) elements; row_threads(L) threads.
+template <int L>
+__device__ __forceinline__ void rows_body(const float2* __restrict__ grid,
+                                          const unsigned* __restrict__ mask,
+                                          const float2* __restrict__ tw,
+                                          const float2* __restrict__ r2, int N,
+                                          float2* __restrict__ img, int iy, float2* sm) {
+    constexpr int NT = row_threads(L);
+    constexpr int NV = (L / 2 + NT - 1) / NT;          // float4 (two columns) per thread
+    const int qy = iy - N / 2 < 0 ? iy - N / 2 + L : iy - N / 2;
+    const float2* row = grid + (int64_t)qy * L;
+    float4 v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int i = threadIdx.x + k * NT;            // columns 2i, 2i + 1 (block i / 2)
+        const int blk = i >> 1;
+        const bool on = i < L / 2 && ((__ldg(mask + (blk >> 5)) >> (blk & 31)) & 1u);
+        v[k] = on ? *reinterpret_cast<const float4*>(row + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int i = threadIdx.x + k * NT;
+        if (i < L / 2) {
+            sm[padded(2 * i)] = make_float2(v[k].x, v[k].y);
+            sm[padded(2 * i + 1)] = make_float2(v[k].z, v[k].w);
+        }
+    }
+    __syncthreads();
+    transform<L, 1, NT>(sm, tw);
+    const float2 ry = r2[iy];
+    float2* out = img + (int64_t)iy * N;
+    for (int ix = threadIdx.x; ix < N; ix += NT) {
+        const int kx = ix - N / 2 < 0 ? ix - N / 2 + L : ix - N / 2;
+        const float2 h = sm[padded(kx)];
+        const float f = df_product(ry, r2[ix]);
+        out[ix] = make_float2(h.x * f, h.y * f);
+    }
+}
+
+// the stage tables of a transform of length L (see tw_offset), in FP64 rounded to FP32
+template <int L>
+std::vector<float2> stage_twiddles() {
+    std::vector<float2> t(tw_total(L));
+    const double pi = 3.14159265358979323846;
+    for (int S = 0; S < num_stages(L); ++S) {
+        const int R = stage_radix(L, S), NS = stage_ns(L, S);
+        for (int i = 0; (1 << i) < R; ++i)
+            for (int k = 0; k < NS; ++k) {
+                const long long m = ((long long)(1 << i) * k * (L / (NS * R))) % L;
+                t[tw_offset(L, S) + i * NS + k] =
+                    make_float2((float)std::cos(2.0 * pi * m / L), (float)std::sin(2.0 * pi * m / L));
+            }
+    }
+    return t;
+}
+
+}  // namespace
+}  // namespace sfft
+}  // namespace ftcg

@@ -180,6 +180,8 @@ ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStr
 ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2* grid,
                             cudaStream_t s, bool pruned = false);
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s);
+// occ[x] = 1 for every grid column x that some sample's taps reach
+ftcg_status_t column_occupancy(const Plan* p, cudaStream_t s, std::vector<unsigned char>* occ);
 ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes);
 bool smem_fft_supported(int G);
 ftcg_status_t build_smem_fft(Plan* p, const std::vector<unsigned char>& occ, cudaStream_t s,

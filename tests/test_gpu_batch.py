@@ -109,3 +109,39 @@ def test_batch_of_sas_pings_sampled(F):
         ref = O.adjoint_pixels(p.lam, v.astype(np.complex128), p.N, 2.0, 8, pix)
         got = img[pix[:, 1] + p.N // 2, pix[:, 0] + p.N // 2]
         assert O.rel_l2(got, ref) < TOL
+
+
+def test_batch_mixed_fft_classes_and_graph(F):
+    """Pings whose grid side is a power of two from 256 take the shared-memory FFT passes (column
+    blocks that taps reach, then the rows fused with the window division); the others cuFFT and a
+    separate window division. A batch mixing both, with an empty ping, against the oracle, directly
+    and replayed from a CUDA graph."""
+    import torch
+    rng = np.random.default_rng(9)
+    cases = []
+    for i, N in enumerate([128, 96, 256, 128, 128]):
+        M = 0 if i == 3 else int(rng.integers(1500, 5000))
+        lo = -N / 2 if i != 4 else -3.0
+        hi = N / 2 if i != 4 else 3.0
+        lam = np.stack([rng.uniform(lo, hi, M), rng.uniform(-N / 2, N / 2, M)], axis=1)
+        v = (rng.standard_normal(M) + 1j * rng.standard_normal(M)).astype(np.complex64)
+        cases.append((lam, v, N))
+    lams = [dev(c[0]) for c in cases]
+    vals = [dev(c[1]) for c in cases]
+    refs = [O.adjoint(lam, v.astype(np.complex128), N, 2.0, 8) if lam.shape[0] else None
+            for lam, v, N in cases]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s), F.Batch(lams, [c[2] for c in cases], 2.0, 8) as b:
+        direct = [x.cpu().numpy() for x in b.adjoint(vals)]
+        imgs = b.capture(vals)
+        for x in imgs:
+            x.fill_(1.0)
+        b.launch()
+        s.synchronize()
+        replay = [x.cpu().numpy() for x in imgs]
+    for ref, d, r in zip(refs, direct, replay):
+        if ref is None:
+            assert np.count_nonzero(d) == 0 and np.count_nonzero(r) == 0
+            continue
+        assert O.rel_l2(d, ref) < TOL
+        assert O.rel_l2(r, ref) < TOL
