@@ -316,9 +316,10 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
         with F.Plan(lam, p.N, p.sigma, p.w) as pl:
             a_ex = pl.weights()
             img_ex = pl.adjoint(v).clone()
+            aux = torch.from_numpy(learn.kr_feature(p.kr)).to(device)   # an input, like lambda
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            a_nn = mlp.predict(F.features(lam, torch.from_numpy(learn.kr_feature(p.kr)).to(device)))
+            a_nn = mlp.predict(F.features(lam, aux))
             pl.set_weights(a_nn)
             img_nn = pl.adjoint(v)
             torch.cuda.synchronize()
