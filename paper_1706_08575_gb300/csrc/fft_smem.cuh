@@ -12,8 +12,15 @@ namespace ftcg {
 namespace sfft {
 namespace {
 
-constexpr int kColBlock = 4;                  // grid columns per pass-A CTA
-constexpr int kColThreads = 512;
+// grid columns per pass-A CTA (2, 4 or 8) and its threads
+#ifndef FTCG_FFT_COL_BLOCK
+#define FTCG_FFT_COL_BLOCK 4
+#endif
+#ifndef FTCG_FFT_COL_THREADS
+#define FTCG_FFT_COL_THREADS 512
+#endif
+constexpr int kColBlock = FTCG_FFT_COL_BLOCK;
+constexpr int kColThreads = FTCG_FFT_COL_THREADS;
 
 __host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
@@ -180,7 +187,13 @@ __device__ __forceinline__ void transform(float2* s, const float2* __restrict__ 
 // pass A: transform along y the kColBlock columns starting at blocks[blockIdx.x] * kColBlock.
 // Each grid row segment of the block is two 16-byte vectors; all of a thread's loads are issued
 // before the first shared-memory store.
-__host__ __device__ constexpr int row_threads(int L) { return L / 16 >= 32 ? L / 16 : 32; }
+#ifndef FTCG_FFT_ROW_DIV
+#define FTCG_FFT_ROW_DIV 16
+#endif
+// threads of a pass-B CTA: L / FTCG_FFT_ROW_DIV (at least one warp)
+__host__ __device__ constexpr int row_threads(int L) {
+    return L / FTCG_FFT_ROW_DIV >= 32 ? L / FTCG_FFT_ROW_DIV : 32;
+}
 
 // pass A body: transform along y the kColBlock columns x0 .. x0 + kColBlock - 1 of the L x L grid.
 // Each grid row segment of the block is two 16-byte vectors; all of a thread's loads are issued
@@ -188,20 +201,21 @@ __host__ __device__ constexpr int row_threads(int L) { return L / 16 >= 32 ? L /
 template <int L>
 __device__ __forceinline__ void cols_body(float2* __restrict__ grid, int x0,
                                           const float2* __restrict__ tw, float2* sm) {
-    static_assert(kColBlock == 4, "two float4 per row segment");
-    constexpr int NV = (2 * L + kColThreads - 1) / kColThreads;   // float4 per thread
+    static_assert(kColBlock == 2 || kColBlock == 4 || kColBlock == 8, "float4 row segments");
+    constexpr int HV = kColBlock / 2;                                // float4 per row segment
+    constexpr int NV = (HV * L + kColThreads - 1) / kColThreads;     // float4 per thread
     float4 v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        const int e = threadIdx.x + k * kColThreads;  // (row, half) = (e / 2, e % 2)
-        if (e < 2 * L)
-            v[k] = *reinterpret_cast<const float4*>(grid + (int64_t)(e >> 1) * L + x0 + 2 * (e & 1));
+        const int e = threadIdx.x + k * kColThreads;  // (row, vector) = (e / HV, e % HV)
+        if (e < HV * L)
+            v[k] = *reinterpret_cast<const float4*>(grid + (int64_t)(e / HV) * L + x0 + 2 * (e % HV));
     }
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         const int e = threadIdx.x + k * kColThreads;
-        const int y = e >> 1, c = 2 * (e & 1);
-        if (e < 2 * L) {
+        const int y = e / HV, c = 2 * (e % HV);
+        if (e < HV * L) {
             sm[c * col_stride(L) + padded(y)] = make_float2(v[k].x, v[k].y);
             sm[(c + 1) * col_stride(L) + padded(y)] = make_float2(v[k].z, v[k].w);
         }
@@ -211,8 +225,8 @@ __device__ __forceinline__ void cols_body(float2* __restrict__ grid, int x0,
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         const int e = threadIdx.x + k * kColThreads;
-        const int y = e >> 1, c = 2 * (e & 1);
-        if (e >= 2 * L) continue;
+        const int y = e / HV, c = 2 * (e % HV);
+        if (e >= HV * L) continue;
         const float2 a = sm[c * col_stride(L) + padded(y)];
         const float2 b = sm[(c + 1) * col_stride(L) + padded(y)];
         *reinterpret_cast<float4*>(grid + (int64_t)y * L + x0 + c) = make_float4(a.x, a.y, b.x, b.y);
@@ -236,8 +250,8 @@ __device__ __forceinline__ void rows_body(const float2* __restrict__ grid,
     float4 v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        const int i = threadIdx.x + k * NT;            // columns 2i, 2i + 1 (block i / 2)
-        const int blk = i >> 1;
+        const int i = threadIdx.x + k * NT;            // columns 2i, 2i + 1 (one column block)
+        const int blk = (2 * i) / kColBlock;
         const bool on = i < L / 2 && ((__ldg(mask + (blk >> 5)) >> (blk & 31)) & 1u);
         v[k] = on ? *reinterpret_cast<const float4*>(row + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
