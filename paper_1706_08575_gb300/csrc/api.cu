@@ -83,11 +83,7 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
     if (own_grid) {
         FTCG_CK(cudaMalloc(&p->grid, (size_t)p->G * p->G * sizeof(float2)));
         bytes += (int64_t)p->G * p->G * sizeof(float2);
-        FTCG_CKFFT(cufftPlan2d(&p->fft, p->G, p->G, CUFFT_C2C));
-        p->fft_ok = true;
-        size_t ws = 0;
-        cufftGetSize(p->fft, &ws);
-        bytes += (int64_t)ws;
+        // the full 2-D plan serves only the forward operator: created on its first call
         FTCG_TRY(build_pruned_fft(p, s, &bytes));
     }
     p->device_bytes = bytes;
@@ -150,6 +146,16 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
 
 namespace {
 
+// the full G x G C2C plan (forward operator; adjoint fallback), created on first use
+ftcg_status_t ensure_full_fft(Plan* p) {
+    if (p->fft_ok) return FTCG_SUCCESS;
+    FTCG_CKFFT(cufftPlan2d(&p->fft, p->G, p->G, CUFFT_C2C));
+    p->fft_ok = true;
+    size_t ws = 0;
+    if (cufftGetSize(p->fft, &ws) == CUFFT_SUCCESS) p->device_bytes += (int64_t)ws;
+    return FTCG_SUCCESS;
+}
+
 ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* img, cudaStream_t s) {
     p->last_stream = s;
     cudaEvent_t* ev = nullptr;
@@ -165,6 +171,7 @@ ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* im
     if (p->pruned_ok) {
         FTCG_TRY(exec_pruned_inverse(p, s));
     } else {
+        FTCG_TRY(ensure_full_fft(p));
         FTCG_CKFFT(cufftSetStream(p->fft, s));
         FTCG_CKFFT(cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
                                 reinterpret_cast<cufftComplex*>(p->grid), CUFFT_INVERSE));
@@ -320,6 +327,7 @@ ftcg_status_t ftcg_forward(ftcg_plan_t plan, const void* d_image, void* d_values
     if (p->M > 0 && !d_values) return invalid("ftcg_forward: values pointer is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
+    FTCG_TRY(ensure_full_fft(p));
     FTCG_TRY(launch_pad_apod(*p, reinterpret_cast<const float2*>(d_image), p->grid, s));
     FTCG_CKFFT(cufftSetStream(p->fft, s));
     FTCG_CKFFT(cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
