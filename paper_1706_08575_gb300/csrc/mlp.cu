@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(128)
     k_knn(const double* __restrict__ lam, const double* __restrict__ aux, int64_t M, Hash hs,
           const int* __restrict__ start, const int* __restrict__ sorted,
           const double2* __restrict__ pts, const float2* __restrict__ pts32, float err,
-          __nv_bfloat16* __restrict__ feat, int* __restrict__ nbr) {
+          __nv_bfloat16* __restrict__ feat, int* __restrict__ nbr, bool vec) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = sorted[t];
@@ -187,16 +187,46 @@ __global__ void __launch_bounds__(128)
                 __longlong_as_double((long long)bk[kNb - 1]) < reach * reach)
                 break;
         }
-        __nv_bfloat16* f = feat + (int64_t)i * kInPad;
+        // the feature row (offsets of the 16 neighbours, aux, zero padding) as 24 bf16 pairs,
+        // stored as six 16-byte vectors (vec) or pair by pair
+        uint32_t row[kInPad / 2];
 #pragma unroll
         for (int k = 0; k < kNb; ++k) {
             const int j = bj[k] == 0x7fffffff ? i : bj[k];   // fewer than 16 samples in all
-            f[2 * k] = __double2bfloat16(__dsub_rn(lam[2 * j], pi.x));
-            f[2 * k + 1] = __double2bfloat16(__dsub_rn(lam[2 * j + 1], pi.y));
-            if (nbr) nbr[(int64_t)i * kNb + k] = bj[k] == 0x7fffffff ? -1 : bj[k];
+            const uint32_t lo = __bfloat16_as_ushort(__double2bfloat16(__dsub_rn(lam[2 * j], pi.x)));
+            const uint32_t hi =
+                __bfloat16_as_ushort(__double2bfloat16(__dsub_rn(lam[2 * j + 1], pi.y)));
+            row[k] = lo | (hi << 16);
         }
-        f[2 * kNb] = __double2bfloat16(aux ? aux[i] : 0.0);
-        for (int k = kIn; k < kInPad; ++k) f[k] = __float2bfloat16(0.f);
+        row[kNb] = __bfloat16_as_ushort(__double2bfloat16(aux ? aux[i] : 0.0));
+#pragma unroll
+        for (int k = kNb + 1; k < kInPad / 2; ++k) row[k] = 0u;
+        if (vec) {
+            uint4* f4 = reinterpret_cast<uint4*>(feat + (int64_t)i * kInPad);
+#pragma unroll
+            for (int q = 0; q < kInPad / 8; ++q)
+                f4[q] = make_uint4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
+            if (nbr) {
+                int4* n4 = reinterpret_cast<int4*>(nbr + (int64_t)i * kNb);
+#pragma unroll
+                for (int q = 0; q < kNb / 4; ++q) {
+                    int v[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        v[r] = bj[4 * q + r] == 0x7fffffff ? -1 : bj[4 * q + r];
+                    n4[q] = make_int4(v[0], v[1], v[2], v[3]);
+                }
+            }
+        } else {
+            uint32_t* f2 = reinterpret_cast<uint32_t*>(feat + (int64_t)i * kInPad);
+#pragma unroll
+            for (int k = 0; k < kInPad / 2; ++k) f2[k] = row[k];
+            if (nbr) {
+#pragma unroll
+                for (int k = 0; k < kNb; ++k)
+                    nbr[(int64_t)i * kNb + k] = bj[k] == 0x7fffffff ? -1 : bj[k];
+            }
+        }
     }
 }
 
@@ -772,9 +802,12 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     k_gather_pts<<<nb(M, 256), 256, 0, s>>>(d_lambda, M, sorted, x0, y0, pts, pts32);
     // bound on the FP32 offset error: 2^-24 of twice the extent, with a 1% margin
     const float err = (float)(2.0 * std::max(x1 - x0, y1 - y0) * 5.9604644775390625e-8 * 1.01);
+    // 16-byte row stores need 16-byte aligned outputs (rows are 96 and 64 bytes)
+    const bool vec = (reinterpret_cast<uintptr_t>(d_features) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(d_neighbors) & 15) == 0;
     k_knn<<<nb(M, 128, 152 * 32), 128, 0, s>>>(d_lambda, d_aux, M, hs, start, sorted, pts, pts32,
                                                   err, reinterpret_cast<__nv_bfloat16*>(d_features),
-                                                  d_neighbors);
+                                                  d_neighbors, vec);
     cudaError_t e = cudaGetLastError();
     cudaStreamSynchronize(s);
     cudaFree(cnt);
