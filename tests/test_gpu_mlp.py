@@ -55,6 +55,30 @@ def test_features_exact_neighbours(F):
     assert np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-30)
 
 
+def test_features_unaligned_outputs(F):
+    """Outputs that are only 4-byte aligned take the element-wise store path: same features and
+    neighbours as the 16-byte vector path."""
+    import ctypes
+    import torch
+    from paper_1706_08575_gb300 import ftcg as A
+    rng = np.random.default_rng(1)
+    lam = dev(rng.random((2000, 2)) * 30 - 15)
+    aux = dev(rng.uniform(-0.1, 0.1, 2000))
+    feats, nb = F.features(lam, aux, neighbors=True)
+    M = 2000
+    fbuf = torch.zeros(M * 48 + 2, dtype=torch.bfloat16, device="cuda")
+    nbuf = torch.zeros(M * 16 + 1, dtype=torch.int32, device="cuda")
+    fptr, nptr = fbuf.data_ptr() + 4, nbuf.data_ptr() + 4          # 4-byte offsets
+    assert fptr % 16 != 0 and nptr % 16 != 0
+    st = A.lib().ftcg_features(ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(aux.data_ptr()),
+                               ctypes.c_int64(M), ctypes.c_void_p(fptr), ctypes.c_void_p(nptr),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert torch.equal(fbuf[2:].view(M, 48), feats)
+    assert torch.equal(nbuf[1:].view(M, 16), nb)
+
+
 def test_forward_and_grads_vs_oracle(F):
     import torch
     rng = np.random.default_rng(1)
