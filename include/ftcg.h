@@ -150,8 +150,10 @@ ftcg_status_t ftcg_adjoint(ftcg_plan_t plan, const void* d_values, int32_t vdtyp
 
 /*
  * ftcg_adjoint_host -- ftcg_adjoint on HOST buffers: copies h_values to the device, runs the
- * adjoint and copies the image back into h_image, all on `stream`, then synchronises it.
- * Pinned host memory gives the fastest copies; pageable memory also works.
+ * adjoint and returns the image in h_image, all on `stream`, then synchronises it. A page-locked
+ * h_image (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory) is written in place by the
+ * device; any other h_image receives one copy of a device staging image. Pinned h_values give
+ * the fastest copy; pageable memory also works.
  */
 ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t vdtype,
                                 void* h_image, ftcg_stream_t stream);

@@ -310,10 +310,25 @@ ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t 
     const size_t vbytes = (size_t)p->M * (vdtype == FTCG_VALUES_C64 ? 8 : 4);
     const size_t ibytes = (size_t)p->N * p->N * sizeof(float2);
     if (!p->stage_vals && p->M > 0) FTCG_CK(cudaMalloc(&p->stage_vals, (size_t)p->M * 8));
-    if (!p->stage_img) FTCG_CK(cudaMalloc(&p->stage_img, ibytes));
+    // A page-locked (pinned or registered) image the device can address is written in place by
+    // the last kernel (no staging copy, the transfer overlaps that kernel); any other host
+    // memory goes through a device staging image and one copy.
+    void* img_dev = nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h_image) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer) {
+        img_dev = at.devicePointer;
+    } else {
+        cudaGetLastError();
+        if (!p->stage_img) FTCG_CK(cudaMalloc(&p->stage_img, ibytes));
+    }
     if (vbytes) FTCG_CK(cudaMemcpyAsync(p->stage_vals, h_values, vbytes, cudaMemcpyHostToDevice, s));
-    FTCG_TRY(adjoint_device(p, p->stage_vals, vdtype, p->stage_img, s));
-    FTCG_CK(cudaMemcpyAsync(h_image, p->stage_img, ibytes, cudaMemcpyDeviceToHost, s));
+    if (img_dev) {
+        FTCG_TRY(adjoint_device(p, p->stage_vals, vdtype, img_dev, s));
+    } else {
+        FTCG_TRY(adjoint_device(p, p->stage_vals, vdtype, p->stage_img, s));
+        FTCG_CK(cudaMemcpyAsync(h_image, p->stage_img, ibytes, cudaMemcpyDeviceToHost, s));
+    }
     FTCG_CK(cudaStreamSynchronize(s));
     return FTCG_SUCCESS;
 }

@@ -279,12 +279,19 @@ def test_nonfinite_coordinate_reported(F):
     p.close()
 
 
-def test_adjoint_host_matches_device(F):
+@pytest.mark.parametrize("N", [64, 128], ids=["cufft-path", "smem-fft-path"])
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_adjoint_host_matches_device(F, N, pinned):
+    """Host buffers: a pinned image is written in place by the device, a pageable one through a
+    staging copy; both equal the device-buffer adjoint."""
     import torch
-    lam, v = sasgen.random_case(51, 2000, 64, spread=64)
-    with F.Plan(dev(lam), 64, 2.0, 8) as p:
+    lam, v = sasgen.random_case(51, 2000, N, spread=N)
+    with F.Plan(dev(lam), N, 2.0, 8) as p:
         a = p.adjoint(dev(c64(v))).cpu()
-        hv = torch.from_numpy(c64(v)).pin_memory()
-        himg = torch.empty((64, 64), dtype=torch.complex64).pin_memory()
+        hv = torch.from_numpy(c64(v))
+        himg = torch.full((N, N), 7.0 + 0j, dtype=torch.complex64)
+        if pinned:
+            hv, himg = hv.pin_memory(), himg.pin_memory()
         p.adjoint_host(hv, himg)
+        p.adjoint_host(hv, himg)                       # twice: the result does not accumulate
     assert O.rel_l2(himg.numpy(), a.numpy()) < 1e-6   # same kernels; atomics order may differ
