@@ -359,6 +359,23 @@ def spread_source_hash():
     return h.hexdigest()[:16]
 
 
+def recorded_issue(tile):
+    """Instruction issue of the recorded k_spread capture (warp instructions per SM per cycle,
+    at most 4 on this GPU), or None if the spreading sources changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_spread_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("source_sha") != spread_source_hash() or int(d.get("tile", -1)) != int(tile):
+            return None
+        ipc = float(d["warp_inst_per_sm_cycle"])
+        return {"bound": "issue", "achieved": ipc, "peak": 4.0,
+                "unit": "warp instructions / SM / cycle", "frac": ipc / 4.0,
+                "warp_instructions_per_launch": d.get("warp_inst_per_launch"),
+                "source": "profiles/k_spread_large_ping.md"}
+    except Exception:
+        return None
+
+
 def recorded_traffic(tile):
     """DRAM bytes (read + write) of one k_spread launch on this workload from the committed ncu
     summary, or None if the spreading sources changed since that capture."""
@@ -633,6 +650,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": recorded_traffic(info.tile),
                          "kernel": "k_spread (+ k_halo_add in the halo layout: the spreading stage)",
                          "peak_kind": peak_kind,
+                         "issue": recorded_issue(info.tile),
                          "alg_bytes_per_launch": alg_bytes},
             "rel_l2_sampled_vs_fp64_oracle": rel,
             "per_ping": {"value": p.M / sum(pp), "unit": UNIT,
