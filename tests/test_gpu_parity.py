@@ -280,6 +280,30 @@ def test_nonfinite_coordinate_reported(F):
 
 
 @pytest.mark.parametrize("N", [64, 128], ids=["cufft-path", "smem-fft-path"])
+def test_adjoint_captured_in_cuda_graph(F, N):
+    """ftcg_adjoint enqueues only kernels and cuFFT executions on its stream, so it can be captured
+    in a CUDA graph and replayed (with new values in the same buffer)."""
+    import torch
+    lam, v = sasgen.random_case(61, 3000, N, spread=N)
+    v2 = np.random.default_rng(62).standard_normal(3000) + 1j
+    with F.Plan(dev(lam), N, 2.0, 8) as p:
+        vals = dev(c64(v))
+        img = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+        p.adjoint(vals, out=img)                       # warm-up outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            p.adjoint(vals, out=img)
+        vals.copy_(dev(c64(v2)))
+        img.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = img.cpu().numpy()
+    ref = O.adjoint(lam, c64(v2).astype(np.complex128), N, 2.0, 8)
+    assert O.rel_l2(got, ref) < TOL
+
+
+@pytest.mark.parametrize("N", [64, 128], ids=["cufft-path", "smem-fft-path"])
 @pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
 def test_adjoint_host_matches_device(F, N, pinned):
     """Host buffers: a pinned image is written in place by the device, a pageable one through a
