@@ -444,7 +444,9 @@ def precision_sweep_extra(device, reps=20):
             torch.cuda.synchronize()
             ms = statistics.median(a.elapsed_time(b) for a, b in ev)
             got = img.cpu().numpy()
-        out[name] = {"value": p.M / (ms * 1e-3), "unit": UNIT, "ms_median": ms}
+            inf = pl.info
+        out[name] = {"value": p.M / (ms * 1e-3), "unit": UNIT, "ms_median": ms, "tile": inf.tile,
+                     "layout": inf.layout}
     ref = O.adjoint_pixels(p.lam, alpha * v.cpu().numpy().astype(np.complex128), p.N, p.sigma,
                            p.w, pix)
     # both images against the same FP64 reference (inputs in FP64): the rounding of the stored
@@ -456,6 +458,36 @@ def precision_sweep_extra(device, reps=20):
         out[name]["rel_l2_sampled_vs_fp64_oracle"] = O.rel_l2(
             got[pix[:, 1] + p.N // 2, pix[:, 0] + p.N // 2], ref)
     return out
+
+
+def tiny_extra(device, reps=50):
+    """The 4,096-sample raster (N = 64, w = 6): launch-latency bound, reported in microseconds
+    (median of CUDA-event times, warm L2), with its sampled error against the direct sum."""
+    import numpy as np
+    import torch
+    import sasgen
+    import paper_1706_08575_gb300 as F
+    from oracle import ftcg_oracle as O
+    p = sasgen.tiny()
+    v = sasgen.values_for(p).astype(np.complex64)
+    with F.Plan(torch.from_numpy(p.lam).to(device), p.N, p.sigma, p.w) as pl:
+        alpha = pl.weights().cpu().numpy()
+        vals = torch.from_numpy(v).to(device)
+        img = pl.adjoint(vals)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for e0, e1 in ev:
+            e0.record()
+            pl.adjoint(vals, out=img)
+            e1.record()
+        torch.cuda.synchronize()
+        us = 1e3 * statistics.median(a.elapsed_time(b) for a, b in ev)
+        got = img.cpu().numpy()
+        info = pl.info
+    ref = O.direct_adjoint(p.lam, alpha * v.astype(np.complex128), p.N)
+    return {"workload": "tiny: 64 kr x 64 theta (M=4096), N=64, sigma=2, w=6", "us_median": us,
+            "value": p.M / (us * 1e-6), "unit": UNIT, "tile": info.tile,
+            "rel_l2_vs_direct_sum": O.rel_l2(got, ref)}
 
 
 def batch_full_extra(device, n_pings=512, reps=5):
@@ -624,7 +656,7 @@ def run_ours(args):
             except Exception as e:       # the headline line must still print
                 extras = {"error": f"{type(e).__name__}: {e}"}
             for key, fn in [("precision_sweep", precision_sweep_extra),
-                            ("batch_512_pings", batch_full_extra)]:
+                            ("batch_512_pings", batch_full_extra), ("tiny", tiny_extra)]:
                 try:
                     more[key] = fn(device)
                 except Exception as e:
