@@ -145,3 +145,27 @@ def test_batch_mixed_fft_classes_and_graph(F):
             continue
         assert O.rel_l2(d, ref) < TOL
         assert O.rel_l2(r, ref) < TOL
+
+
+def test_batch_bf16_smem_classes(F):
+    """BF16 values and weights through the shared-memory FFT classes (G = 256 and 512) and a
+    cuFFT class, against the oracle on the same bf16-rounded inputs."""
+    import torch
+    rng = np.random.default_rng(21)
+    cases = []
+    for N in [128, 256, 96]:
+        M = int(rng.integers(2000, 5000))
+        lam = np.stack([rng.uniform(-N / 2, N / 2, M), rng.uniform(-N / 2, N / 2, M)], axis=1)
+        v = (rng.standard_normal(M) + 1j * rng.standard_normal(M)).astype(np.complex64)
+        cases.append((lam, v, N))
+    vb = [torch.view_as_real(torch.from_numpy(c[1])).to(torch.bfloat16).cuda() for c in cases]
+    with F.Batch([dev(c[0]) for c in cases], [c[2] for c in cases], 2.0, 8,
+                 precision=F.PREC_BF16) as b:
+        alphas = [a.cpu().numpy() for a in b.weights()]
+        imgs = [x.cpu().numpy() for x in b.adjoint(vb)]
+    for (lam, _, N), img, a, vbt in zip(cases, imgs, alphas, vb):
+        vr = vbt.cpu().to(torch.float64).numpy()
+        vr = vr[:, 0] + 1j * vr[:, 1]
+        a_r = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+        ref = O.adjoint(lam, a_r * vr, N, 2.0, 8)
+        assert O.rel_l2(img, ref) < TOL
