@@ -25,7 +25,7 @@ constexpr int kColThreads = FTCG_FFT_COL_THREADS;
 __host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
 // distance between the transforms of a block in shared memory: 4 extra elements shift each
-// column by 8 banks, so that the row-wise loads and stores of a block do not collide
+// column by 8 banks, so that the four columns a half-warp touches (4 rows each) do not collide
 __host__ __device__ constexpr int col_stride(int L) { return padded_len(L) + 4; }
 
 // radix of stage s for a transform of length L: 16 while at least 16 remains, then the rest
@@ -123,9 +123,14 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
 // One Stockham stage (radix R, NS transforms of size NS already done) over CB transforms of length
 // L stored at s + c * col_stride(L), by NT threads. Every size is a compile-time constant; the
 // first radix is 16 (or L), so NS is 1 or a multiple of 16 and the padded addresses of a
-// butterfly's values are its first address plus constant offsets.
-template <int L, int R, int NS, int CB, int NT, int S>
-__device__ __forceinline__ void stage(float2* s, const float2* __restrict__ tw) {
+// butterfly's values are its first address plus constant offsets. Butterfly id maps to
+// transform c = id % CB and index j = id / CB, so that the lanes of a warp cover CB adjacent
+// columns of consecutive rows. The first stage may read its values from global memory through
+// ld(c, index) instead of shared memory, and the last may hand its results to st(c, index, value).
+template <int L, int R, int NS, int CB, int NT, int S, bool FIRST, bool LAST, typename LD,
+          typename ST>
+__device__ __forceinline__ void stage(float2* s, const float2* __restrict__ tw, const LD& ld,
+                                      const ST& st) {
     constexpr int NJ = L / R;
     constexpr int NB = CB * NJ;
     constexpr int BPT = (NB + NT - 1) / NT;
@@ -138,10 +143,15 @@ __device__ __forceinline__ void stage(float2* s, const float2* __restrict__ tw) 
     for (int b = 0; b < BPT; ++b) {
         const int id = threadIdx.x + b * NT;
         if (NB % NT == 0 || id < NB) {
-            const int c = id / NJ, j = id - (id / NJ) * NJ;
-            const float2* src = s + c * col_stride(L) + padded(j);
+            const int c = id % CB, j = id / CB;
+            if constexpr (FIRST) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b][r] = src[r * IN_STEP];
+                for (int r = 0; r < R; ++r) v[b][r] = ld(c, j + r * NJ);
+            } else {
+                const float2* src = s + c * col_stride(L) + padded(j);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[b][r] = src[r * IN_STEP];
+            }
             if constexpr (NS > 1) {                   // the first stage has k = 0
                 // w^(r k TSTEP) for the powers of two r from the table, the rest as products
                 // of at most three table values
@@ -159,34 +169,37 @@ __device__ __forceinline__ void stage(float2* s, const float2* __restrict__ tw) 
             }
         }
     }
-    __syncthreads();
+    if constexpr (!FIRST) __syncthreads();            // in place: every read before any write
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const int id = threadIdx.x + b * NT;
         if (NB % NT == 0 || id < NB) {
-            const int c = id / NJ, j = id - (id / NJ) * NJ;
+            const int c = id % CB, j = id / CB;
             const int k = j & (NS - 1);
             dft<R>(v[b]);
-            float2* dst = s + c * col_stride(L) + padded((j - k) * R + k);
+            if constexpr (LAST) {
 #pragma unroll
-            for (int q = 0; q < R; ++q) dst[q * OUT_STEP] = v[b][q];
+                for (int q = 0; q < R; ++q) st(c, (j - k) * R + k + q * NS, v[b][q]);
+            } else {
+                float2* dst = s + c * col_stride(L) + padded((j - k) * R + k);
+#pragma unroll
+                for (int q = 0; q < R; ++q) dst[q * OUT_STEP] = v[b][q];
+            }
         }
     }
-    __syncthreads();
+    if constexpr (!LAST) __syncthreads();
 }
 
-template <int L, int CB, int NT, int S = 0, int NS = 1>
-__device__ __forceinline__ void transform(float2* s, const float2* __restrict__ tw) {
+template <int L, int CB, int NT, typename LD, typename ST, int S = 0, int NS = 1>
+__device__ __forceinline__ void transform(float2* s, const float2* __restrict__ tw, const LD& ld,
+                                          const ST& st) {
     if constexpr (S < num_stages(L)) {
         constexpr int R = stage_radix(L, S);
-        stage<L, R, NS, CB, NT, S>(s, tw);
-        transform<L, CB, NT, S + 1, NS * R>(s, tw);
+        stage<L, R, NS, CB, NT, S, S == 0, S + 1 == num_stages(L)>(s, tw, ld, st);
+        transform<L, CB, NT, LD, ST, S + 1, NS * R>(s, tw, ld, st);
     }
 }
 
-// pass A: transform along y the kColBlock columns starting at blocks[blockIdx.x] * kColBlock.
-// Each grid row segment of the block is two 16-byte vectors; all of a thread's loads are issued
-// before the first shared-memory store.
 #ifndef FTCG_FFT_ROW_DIV
 #define FTCG_FFT_ROW_DIV 16
 #endif
@@ -195,48 +208,23 @@ __host__ __device__ constexpr int row_threads(int L) {
     return L / FTCG_FFT_ROW_DIV >= 32 ? L / FTCG_FFT_ROW_DIV : 32;
 }
 
-// pass A body: transform along y the kColBlock columns x0 .. x0 + kColBlock - 1 of the L x L grid.
-// Each grid row segment of the block is two 16-byte vectors; all of a thread's loads are issued
-// before the first shared-memory store. sm: kColBlock * col_stride(L) elements.
+// pass A body: transform along y the kColBlock columns x0 .. x0 + kColBlock - 1 of the L x L grid,
+// in place: the first stage reads the columns from the grid, the last writes them back (each
+// warp access covers kColBlock adjacent cells of consecutive rows); the stages between exchange
+// through shared memory (sm: kColBlock * col_stride(L) elements).
 template <int L>
 __device__ __forceinline__ void cols_body(float2* __restrict__ grid, int x0,
                                           const float2* __restrict__ tw, float2* sm) {
-    static_assert(kColBlock == 2 || kColBlock == 4 || kColBlock == 8, "float4 row segments");
-    constexpr int HV = kColBlock / 2;                                // float4 per row segment
-    constexpr int NV = (HV * L + kColThreads - 1) / kColThreads;     // float4 per thread
-    float4 v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int e = threadIdx.x + k * kColThreads;  // (row, vector) = (e / HV, e % HV)
-        if (e < HV * L)
-            v[k] = *reinterpret_cast<const float4*>(grid + (int64_t)(e / HV) * L + x0 + 2 * (e % HV));
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int e = threadIdx.x + k * kColThreads;
-        const int y = e / HV, c = 2 * (e % HV);
-        if (e < HV * L) {
-            sm[c * col_stride(L) + padded(y)] = make_float2(v[k].x, v[k].y);
-            sm[(c + 1) * col_stride(L) + padded(y)] = make_float2(v[k].z, v[k].w);
-        }
-    }
-    __syncthreads();
-    transform<L, kColBlock, kColThreads>(sm, tw);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int e = threadIdx.x + k * kColThreads;
-        const int y = e / HV, c = 2 * (e % HV);
-        if (e >= HV * L) continue;
-        const float2 a = sm[c * col_stride(L) + padded(y)];
-        const float2 b = sm[(c + 1) * col_stride(L) + padded(y)];
-        *reinterpret_cast<float4*>(grid + (int64_t)y * L + x0 + c) = make_float4(a.x, a.y, b.x, b.y);
-    }
+    auto ld = [&](int c, int y) { return grid[(int64_t)y * L + x0 + c]; };
+    auto st = [&](int c, int y, float2 v) { grid[(int64_t)y * L + x0 + c] = v; };
+    transform<L, kColBlock, kColThreads>(sm, tw, ld, st);
 }
 
-// pass B body: image row iy from grid row (iy - N/2) mod L, transformed along x; the N kept
-// frequencies are divided by the window transforms (FP32 pairs, see df_product). Only the column
-// blocks marked in mask (the ones taps reach) are read; the others are zero.
-// sm: padded_len(L) elements; row_threads(L) threads.
+// pass B body: image row iy from grid row (iy - N/2) mod L, transformed along x; the first stage
+// reads the row from the grid (only the column blocks marked in mask, the ones taps reach; the
+// others are zero) and the last writes the N kept frequencies straight into the image, divided
+// by the window transforms (FP32 pairs, see df_product). sm: padded_len(L) elements;
+// row_threads(L) threads.
 template <int L>
 __device__ __forceinline__ void rows_body(const float2* __restrict__ grid,
                                           const unsigned* __restrict__ mask,
@@ -244,35 +232,27 @@ __device__ __forceinline__ void rows_body(const float2* __restrict__ grid,
                                           const float2* __restrict__ r2, int N,
                                           float2* __restrict__ img, int iy, float2* sm) {
     constexpr int NT = row_threads(L);
-    constexpr int NV = (L / 2 + NT - 1) / NT;          // float4 (two columns) per thread
     const int qy = iy - N / 2 < 0 ? iy - N / 2 + L : iy - N / 2;
     const float2* row = grid + (int64_t)qy * L;
-    float4 v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int i = threadIdx.x + k * NT;            // columns 2i, 2i + 1 (one column block)
-        const int blk = (2 * i) / kColBlock;
-        const bool on = i < L / 2 && ((__ldg(mask + (blk >> 5)) >> (blk & 31)) & 1u);
-        v[k] = on ? *reinterpret_cast<const float4*>(row + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int i = threadIdx.x + k * NT;
-        if (i < L / 2) {
-            sm[padded(2 * i)] = make_float2(v[k].x, v[k].y);
-            sm[padded(2 * i + 1)] = make_float2(v[k].z, v[k].w);
-        }
-    }
-    __syncthreads();
-    transform<L, 1, NT>(sm, tw);
+    auto ld = [&](int, int x) {
+        const int blk = x / kColBlock;
+        return ((__ldg(mask + (blk >> 5)) >> (blk & 31)) & 1u) ? row[x] : make_float2(0.f, 0.f);
+    };
     const float2 ry = r2[iy];
     float2* out = img + (int64_t)iy * N;
-    for (int ix = threadIdx.x; ix < N; ix += NT) {
-        const int kx = ix - N / 2 < 0 ? ix - N / 2 + L : ix - N / 2;
-        const float2 h = sm[padded(kx)];
+    auto st = [&](int, int kx, float2 h) {
+        int ix;
+        if (kx < N / 2) {
+            ix = kx + N / 2;
+        } else if (kx >= L - N / 2) {
+            ix = kx - (L - N / 2);
+        } else {
+            return;                                   // outside the crop
+        }
         const float f = df_product(ry, r2[ix]);
         out[ix] = make_float2(h.x * f, h.y * f);
-    }
+    };
+    transform<L, 1, NT>(sm, tw, ld, st);
 }
 
 // the stage tables of a transform of length L (see tw_offset), in FP64 rounded to FP32
