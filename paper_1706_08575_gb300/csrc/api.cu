@@ -63,25 +63,25 @@ void release_plan(Plan* p) {
 ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool own_grid) {
     int64_t bytes = 0;
     const int64_t M = p->M;
-    FTCG_CK(cudaMalloc(&p->status, sizeof(unsigned)));
+    FTCG_CK(pool_malloc(&p->status, sizeof(unsigned), s));
     FTCG_CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), s));
     if (M > 0) {
-        FTCG_CK(cudaMalloc(&p->lambda, (size_t)M * 2 * sizeof(double)));
+        FTCG_CK(pool_malloc(&p->lambda, (size_t)M * 2 * sizeof(double), s));
         FTCG_CK(cudaMemcpyAsync(p->lambda, d_lambda, (size_t)M * 2 * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
-        FTCG_CK(cudaMalloc(&p->samp, (size_t)M * sizeof(int4)));
+        FTCG_CK(pool_malloc(&p->samp, (size_t)M * sizeof(int4), s));
         bytes += (int64_t)M * (2 * sizeof(double) + sizeof(int4));
     }
-    FTCG_CK(cudaMalloc(&p->deapod, (size_t)p->N * sizeof(double)));
+    FTCG_CK(pool_malloc(&p->deapod, (size_t)p->N * sizeof(double), s));
     bytes += (int64_t)p->N * sizeof(double);
     FTCG_TRY(window_factors(p->deapod, p->N, p->G, p->win, s));
-    FTCG_CK(cudaMalloc(&p->deapod2, (size_t)p->N * sizeof(float2)));
+    FTCG_CK(pool_malloc(&p->deapod2, (size_t)p->N * sizeof(float2), s));
     bytes += (int64_t)p->N * sizeof(float2);
     FTCG_TRY(split_factors(p->deapod, p->deapod2, p->N, s));
     FTCG_TRY(build_binning(p->bin, p->lambda, M, p->sigma, p->G, p->opts.tile, p->w,
                            p->opts.layout == FTCG_LAYOUT_HALO, p->status, p->samp, s, &bytes));
     if (own_grid) {
-        FTCG_CK(cudaMalloc(&p->grid, (size_t)p->G * p->G * sizeof(float2)));
+        FTCG_CK(pool_malloc(&p->grid, (size_t)p->G * p->G * sizeof(float2), s));
         bytes += (int64_t)p->G * p->G * sizeof(float2);
         // the full 2-D plan serves only the forward operator: created on its first call
         FTCG_TRY(build_pruned_fft(p, s, &bytes));
@@ -309,7 +309,7 @@ ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t vbytes = (size_t)p->M * (vdtype == FTCG_VALUES_C64 ? 8 : 4);
     const size_t ibytes = (size_t)p->N * p->N * sizeof(float2);
-    if (!p->stage_vals && p->M > 0) FTCG_CK(cudaMalloc(&p->stage_vals, (size_t)p->M * 8));
+    if (!p->stage_vals && p->M > 0) FTCG_CK(pool_malloc(&p->stage_vals, (size_t)p->M * 8, s));
     // A page-locked (pinned or registered) image the device can address is written in place by
     // the last kernel (no staging copy, the transfer overlaps that kernel); any other host
     // memory goes through a device staging image and one copy.
@@ -320,7 +320,7 @@ ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t 
         img_dev = at.devicePointer;
     } else {
         cudaGetLastError();
-        if (!p->stage_img) FTCG_CK(cudaMalloc(&p->stage_img, ibytes));
+        if (!p->stage_img) FTCG_CK(pool_malloc(&p->stage_img, ibytes, s));
     }
     if (vbytes) FTCG_CK(cudaMemcpyAsync(p->stage_vals, h_values, vbytes, cudaMemcpyHostToDevice, s));
     if (img_dev) {

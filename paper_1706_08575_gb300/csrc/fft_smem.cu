@@ -106,7 +106,7 @@ ftcg_status_t build_smem_fft(Plan* p, const std::vector<unsigned char>& occ, cud
     }
     std::vector<unsigned> mask((G / kColBlock + 31) / 32, 0u);
     for (int b : blocks) mask[b >> 5] |= 1u << (b & 31);
-    FTCG_CK(cudaMalloc(&p->col_mask, mask.size() * sizeof(unsigned)));
+    FTCG_CK(pool_malloc(&p->col_mask, mask.size() * sizeof(unsigned), s));
     *bytes += mask.size() * sizeof(unsigned);
     FTCG_CK(cudaMemcpyAsync(p->col_mask, mask.data(), mask.size() * sizeof(unsigned),
                             cudaMemcpyHostToDevice, s));
@@ -118,11 +118,11 @@ ftcg_status_t build_smem_fft(Plan* p, const std::vector<unsigned char>& occ, cud
         case 2048: tw = stage_twiddles<2048>(); break;
         default: tw = stage_twiddles<4096>(); break;
     }
-    FTCG_CK(cudaMalloc(&p->tw, tw.size() * sizeof(float2)));
+    FTCG_CK(pool_malloc(&p->tw, tw.size() * sizeof(float2), s));
     *bytes += tw.size() * sizeof(float2);
     FTCG_CK(cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     if (!blocks.empty()) {
-        FTCG_CK(cudaMalloc(&p->col_blocks, blocks.size() * sizeof(int)));
+        FTCG_CK(pool_malloc(&p->col_blocks, blocks.size() * sizeof(int), s));
         *bytes += blocks.size() * sizeof(int);
         FTCG_CK(cudaMemcpyAsync(p->col_blocks, blocks.data(), blocks.size() * sizeof(int),
                                 cudaMemcpyHostToDevice, s));

@@ -101,6 +101,14 @@ __device__ __forceinline__ void pdl_allow_next() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Stream-ordered allocation from the library's per-device pool (pool.cu); bytes == 0 gives
+// nullptr. Free with cudaFreeAsync on a stream, or with cudaFree.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+template <typename T>
+cudaError_t pool_malloc(T** p, size_t bytes, cudaStream_t s) {
+    return pool_malloc(reinterpret_cast<void**>(p), bytes, s);
+}
+
 // A binning of samples into square tiles of a G x G periodic grid.
 struct Binning {
     int G = 0, T = 0, W = 0;

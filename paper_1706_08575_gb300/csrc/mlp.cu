@@ -754,12 +754,12 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int nbk = nb(M, 256, 1024);
     double* bb = nullptr;
-    FTCG_CK(cudaMalloc(&bb, nbk * 4 * sizeof(double)));
+    FTCG_CK(pool_malloc(&bb, nbk * 4 * sizeof(double), s));
     k_bbox<<<nbk, 256, 0, s>>>(d_lambda, M, bb);
     std::vector<double> hb(nbk * 4);
     FTCG_CK(cudaMemcpyAsync(hb.data(), bb, nbk * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FTCG_CK(cudaStreamSynchronize(s));
-    cudaFree(bb);
+    cudaFreeAsync(bb, s);
     double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
     for (int i = 0; i < nbk; ++i) {
         x0 = std::min(x0, hb[4 * i]);
@@ -786,10 +786,10 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     hs.ny = std::max(1, (int)std::ceil((y1 - y0) / h + 1e-9));
     const int64_t ncell = (int64_t)hs.nx * hs.ny;
     int *cnt = nullptr, *start = nullptr, *cell = nullptr, *sorted = nullptr;
-    FTCG_CK(cudaMalloc(&cnt, (ncell + 1) * sizeof(int)));
-    FTCG_CK(cudaMalloc(&start, (ncell + 1) * sizeof(int)));
-    FTCG_CK(cudaMalloc(&cell, M * sizeof(int)));
-    FTCG_CK(cudaMalloc(&sorted, M * sizeof(int)));
+    FTCG_CK(pool_malloc(&cnt, (ncell + 1) * sizeof(int), s));
+    FTCG_CK(pool_malloc(&start, (ncell + 1) * sizeof(int), s));
+    FTCG_CK(pool_malloc(&cell, M * sizeof(int), s));
+    FTCG_CK(pool_malloc(&sorted, M * sizeof(int), s));
     FTCG_CK(cudaMemsetAsync(cnt, 0, (ncell + 1) * sizeof(int), s));
     k_cell_count<<<nb(M, 256), 256, 0, s>>>(d_lambda, M, hs, cnt, cell);
     FTCG_TRY(exclusive_scan_i32(cnt, start, ncell + 1, s));
@@ -797,8 +797,8 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     k_cell_scatter<<<nb(M, 256), 256, 0, s>>>(M, cell, cnt, sorted);
     double2* pts = nullptr;
     float2* pts32 = nullptr;
-    FTCG_CK(cudaMalloc(&pts, M * sizeof(double2)));
-    FTCG_CK(cudaMalloc(&pts32, M * sizeof(float2)));
+    FTCG_CK(pool_malloc(&pts, M * sizeof(double2), s));
+    FTCG_CK(pool_malloc(&pts32, M * sizeof(float2), s));
     k_gather_pts<<<nb(M, 256), 256, 0, s>>>(d_lambda, M, sorted, x0, y0, pts, pts32);
     // bound on the FP32 offset error: 2^-24 of twice the extent, with a 1% margin
     const float err = (float)(2.0 * std::max(x1 - x0, y1 - y0) * 5.9604644775390625e-8 * 1.01);
@@ -810,12 +810,12 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
                                                   d_neighbors, vec);
     cudaError_t e = cudaGetLastError();
     cudaStreamSynchronize(s);
-    cudaFree(cnt);
-    cudaFree(start);
-    cudaFree(cell);
-    cudaFree(sorted);
-    cudaFree(pts);
-    cudaFree(pts32);
+    cudaFreeAsync(cnt, s);
+    cudaFreeAsync(start, s);
+    cudaFreeAsync(cell, s);
+    cudaFreeAsync(sorted, s);
+    cudaFreeAsync(pts, s);
+    cudaFreeAsync(pts32, s);
     FTCG_CK(e);
     return FTCG_SUCCESS;
 }

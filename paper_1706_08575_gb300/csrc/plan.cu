@@ -275,7 +275,7 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cnt(x) > cnt(y); });
     b.n_nonempty = 0;
     while (b.n_nonempty < b.ntiles && cnt(order[b.n_nonempty]) > 0) ++b.n_nonempty;
-    FTCG_CK(cudaMalloc(&b.tile_order, b.ntiles * sizeof(int)));
+    FTCG_CK(pool_malloc(&b.tile_order, b.ntiles * sizeof(int), s));
     *bytes += b.ntiles * sizeof(int);
     FTCG_CK(cudaMemcpyAsync(b.tile_order, order.data(), b.ntiles * sizeof(int),
                             cudaMemcpyHostToDevice, s));
@@ -295,7 +295,7 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
     b.ncb = T + W - 1;
     const int64_t nbins = (int64_t)b.ntiles * b.ncb;      // (tile, column bin)
     const int64_t nkeys = nbins * b.ncb;                  // (tile, column bin, row)
-    FTCG_CK(cudaMalloc(&b.colptr, (nbins + 1) * sizeof(int)));
+    FTCG_CK(pool_malloc(&b.colptr, (nbins + 1) * sizeof(int), s));
     *bytes += (nbins + 1) * sizeof(int);
     if (M == 0) {
         FTCG_CK(cudaMemsetAsync(b.colptr, 0, (nbins + 1) * sizeof(int), s));
@@ -320,7 +320,7 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
     k_colptr<<<grid_for(nbins + 1), kThreads, 0, s>>>(offs, nbins, b.ncb, total, b.colptr);
     FTCG_CK(cudaGetLastError());
     if (total > 0) {
-        FTCG_CK(cudaMalloc(&b.ent, (size_t)(total + kEntryPad) * sizeof(Entry)));
+        FTCG_CK(pool_malloc(&b.ent, (size_t)(total + kEntryPad) * sizeof(Entry), s));
         *bytes += (int64_t)(total + kEntryPad) * sizeof(Entry);
         FTCG_CK(cudaMemsetAsync(b.ent + total, 0, kEntryPad * sizeof(Entry), s));
         k_bin_scatter<<<grid_for(M), kThreads, 0, s>>>(d_lambda, M, scale, G, T, W, b.ntx, b.ncb,
@@ -333,7 +333,7 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
         // per tile: the right strip (T + w - 1) x (w - 1) and the bottom strip (w - 1) x T
         b.halo_cells = (T + W - 1) * (W - 1) + (W - 1) * T;
         const size_t hb = (size_t)b.ntiles * b.halo_cells * sizeof(float2);
-        FTCG_CK(cudaMalloc(&b.halo_buf, hb));
+        FTCG_CK(pool_malloc(&b.halo_buf, hb, s));
         *bytes += (int64_t)hb;
     }
     return order_tiles(b, s, bytes);

@@ -234,13 +234,11 @@ struct WeightBuffers {
     PolyCoef* coef = nullptr;
     double* alpha = nullptr;
     bool own_alpha = false;
+    cudaStream_t s = nullptr;            // allocated from the pool on s, freed on s
     ~WeightBuffers() {
-        cudaFree(r2);
-        cudaFree(grid);
-        cudaFree(phi);
-        cudaFree(work);
-        cudaFree(coef);
-        if (own_alpha) cudaFree(alpha);
+        void* all[6] = {r2, grid, phi, work, coef, own_alpha ? alpha : nullptr};
+        for (void* q : all)
+            if (q) cudaFreeAsync(q, s);
     }
 };
 
@@ -303,10 +301,11 @@ ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s) {
     WeightBuffers b;
     const size_t gbytes = (size_t)G2 * ld * sizeof(double);
     const size_t pbytes = (size_t)p.M * 2 * Wa * sizeof(double);
-    if (cudaMalloc(&b.r2, N2 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b.grid, gbytes) != cudaSuccess || cudaMalloc(&b.phi, pbytes) != cudaSuccess ||
-        cudaMalloc(&b.coef, sizeof(PolyCoef)) != cudaSuccess ||
-        (fft.ws > 0 && cudaMalloc(&b.work, fft.ws) != cudaSuccess)) {
+    b.s = s;
+    if (pool_malloc(&b.r2, N2 * sizeof(double), s) != cudaSuccess ||
+        pool_malloc(&b.grid, gbytes, s) != cudaSuccess || pool_malloc(&b.phi, pbytes, s) != cudaSuccess ||
+        pool_malloc(&b.coef, sizeof(PolyCoef), s) != cudaSuccess ||
+        (fft.ws > 0 && pool_malloc(&b.work, fft.ws, s) != cudaSuccess)) {
         cudaGetLastError();
         set_error("ftcg_weights: cannot allocate the FP64 lag grid (%zu bytes), the window table "
                   "(%zu bytes) or the FFT workspace (%zu bytes)", gbytes, pbytes, fft.ws);
@@ -314,7 +313,7 @@ ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s) {
     }
     b.alpha = d_alpha_out;
     if (!b.alpha) {
-        if (cudaMalloc(&b.alpha, p.M * sizeof(double)) != cudaSuccess) {
+        if (pool_malloc(&b.alpha, p.M * sizeof(double), s) != cudaSuccess) {
             cudaGetLastError();
             set_error("ftcg_weights: cannot allocate the weight array");
             return FTCG_ERR_OUT_OF_MEMORY;
