@@ -102,8 +102,9 @@ __device__ __forceinline__ void pdl_allow_next() {
 }
 
 // Stream-ordered allocation from the library's per-device pool (pool.cu); bytes == 0 gives
-// nullptr. Free with cudaFreeAsync on a stream, or with cudaFree.
+// nullptr. Free with pool_free on a stream, or with cudaFree.
 cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+cudaError_t pool_free(void* p, cudaStream_t s);
 template <typename T>
 cudaError_t pool_malloc(T** p, size_t bytes, cudaStream_t s) {
     return pool_malloc(reinterpret_cast<void**>(p), bytes, s);

@@ -759,7 +759,7 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     std::vector<double> hb(nbk * 4);
     FTCG_CK(cudaMemcpyAsync(hb.data(), bb, nbk * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FTCG_CK(cudaStreamSynchronize(s));
-    cudaFreeAsync(bb, s);
+    pool_free(bb, s);
     double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
     for (int i = 0; i < nbk; ++i) {
         x0 = std::min(x0, hb[4 * i]);
@@ -810,12 +810,12 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
                                                   d_neighbors, vec);
     cudaError_t e = cudaGetLastError();
     cudaStreamSynchronize(s);
-    cudaFreeAsync(cnt, s);
-    cudaFreeAsync(start, s);
-    cudaFreeAsync(cell, s);
-    cudaFreeAsync(sorted, s);
-    cudaFreeAsync(pts, s);
-    cudaFreeAsync(pts32, s);
+    pool_free(cnt, s);
+    pool_free(start, s);
+    pool_free(cell, s);
+    pool_free(sorted, s);
+    pool_free(pts, s);
+    pool_free(pts32, s);
     FTCG_CK(e);
     return FTCG_SUCCESS;
 }

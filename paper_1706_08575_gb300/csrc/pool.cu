@@ -5,6 +5,7 @@
 
 #include "ftcg_internal.cuh"
 
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
@@ -16,11 +17,22 @@ constexpr uint64_t kPoolKeepBytes = 4ull << 30;
 std::mutex g_pool_mu;
 std::map<int, cudaMemPool_t> g_pools;
 
+bool pool_disabled() {
+    static const bool off = std::getenv("FTCG_NO_POOL") != nullptr;
+    return off;
+}
+
 }  // namespace
+
+cudaError_t pool_free(void* p, cudaStream_t s) {
+    if (!p) return cudaSuccess;
+    return pool_disabled() ? cudaFree(p) : cudaFreeAsync(p, s);
+}
 
 cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) return cudaSuccess;
+    if (pool_disabled()) return cudaMalloc(p, bytes);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

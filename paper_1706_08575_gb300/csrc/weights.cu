@@ -238,7 +238,7 @@ struct WeightBuffers {
     ~WeightBuffers() {
         void* all[6] = {r2, grid, phi, work, coef, own_alpha ? alpha : nullptr};
         for (void* q : all)
-            if (q) cudaFreeAsync(q, s);
+            if (q) pool_free(q, s);
     }
 };
 
