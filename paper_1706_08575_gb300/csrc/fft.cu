@@ -72,6 +72,10 @@ cufftResult plan_columns(cufftHandle* h, int G, int batch) {
 }  // namespace
 
 ftcg_status_t column_occupancy(const Plan* p, cudaStream_t s, std::vector<unsigned char>* occ) {
+    if ((int)p->bin.col_occ.size() == p->G) {     // derived from the binning on the host
+        *occ = p->bin.col_occ;
+        return FTCG_SUCCESS;
+    }
     occ->assign(p->G, 0);
     if (p->M == 0) return FTCG_SUCCESS;
     unsigned char* d_occ = nullptr;

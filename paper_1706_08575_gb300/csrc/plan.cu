@@ -259,6 +259,7 @@ void free_binning(Binning& b) {
     b.colptr = nullptr;
     b.tile_order = nullptr;
     b.n_entries = 0;
+    b.col_occ.clear();
 }
 
 // Launch order of the tiles: decreasing entry count, so that the heaviest tiles start first and
@@ -275,6 +276,26 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cnt(x) > cnt(y); });
     b.n_nonempty = 0;
     while (b.n_nonempty < b.ntiles && cnt(order[b.n_nonempty]) > 0) ++b.n_nonempty;
+    // grid columns that taps reach: an entry in column bin k of tile column tx has its first tap
+    // (of the tile's run) at X0 + k - (w - 1), and the sample's taps of that run follow it
+    std::vector<unsigned char> first(b.G, 0);   // columns where some run of taps starts
+    for (int i = 0; i < b.n_nonempty; ++i) {
+        const int t = order[i];
+        const int X0 = (t % b.ntx) * b.T;
+        const int64_t base = (int64_t)t * b.ncb;
+        for (int k = 0; k < b.ncb; ++k) {
+            if (cp[base + k + 1] == cp[base + k]) continue;
+            int x = X0 + k - (b.W - 1);
+            if (x < 0) x += b.G;
+            if (x >= b.G) x -= b.G;
+            first[x] = 1;
+        }
+    }
+    b.col_occ.assign(b.G, 0);                    // the w columns from each start (mod G)
+    for (int x = 0, run = 0; x < b.G + b.W - 1; ++x) {
+        run = first[x % b.G] ? b.W : run - 1;
+        if (run > 0) b.col_occ[x % b.G] = 1;
+    }
     FTCG_CK(pool_malloc(&b.tile_order, b.ntiles * sizeof(int), s));
     *bytes += b.ntiles * sizeof(int);
     FTCG_CK(cudaMemcpyAsync(b.tile_order, order.data(), b.ntiles * sizeof(int),

@@ -9,6 +9,9 @@
 // Legendre polynomial P_n (three-term recurrence), then the N reciprocals are evaluated in FP64.
 
 #include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "ftcg_internal.cuh"
@@ -84,17 +87,51 @@ double es_beta(int w, double sigma) {
     return 0.97 * pi * (1.0 - 0.5 / sigma) * w;
 }
 
-ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cudaStream_t s) {
-    std::vector<double> x, wt;
-    gauss_legendre(kQuadNodes, x, wt);
-    Quad q;
-    const double pi = 3.14159265358979323846;
-    for (int k = 0; k < kQuadNodes; ++k) {
-        q.th[k] = 0.25 * pi * (x[k] + 1.0);
-        q.wt[k] = 0.25 * pi * wt[k];
+namespace {
+
+// Factors already computed, per (device, N, G, w, beta): plans of the same shape (ping after
+// ping) copy them instead of repeating the FP64 quadrature. Held until the process exits.
+struct FactorKey {
+    int dev, N, G, w;
+    uint64_t beta_bits;
+    bool operator<(const FactorKey& o) const {
+        if (dev != o.dev) return dev < o.dev;
+        if (N != o.N) return N < o.N;
+        if (G != o.G) return G < o.G;
+        if (w != o.w) return w < o.w;
+        return beta_bits < o.beta_bits;
     }
-    k_window_factors<<<(N + 127) / 128, 128, 0, s>>>(d_out, N, G, win.w, win.beta, q);
-    FTCG_CK(cudaGetLastError());
+};
+std::mutex g_factor_mu;
+std::map<FactorKey, double*> g_factors;
+
+}  // namespace
+
+ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cudaStream_t s) {
+    if (N <= 0) return FTCG_SUCCESS;
+    FactorKey key{0, N, G, win.w, 0};
+    FTCG_CK(cudaGetDevice(&key.dev));
+    std::memcpy(&key.beta_bits, &win.beta, sizeof(double));
+    std::lock_guard<std::mutex> lk(g_factor_mu);
+    auto it = g_factors.find(key);
+    if (it == g_factors.end()) {
+        std::vector<double> x, wt;
+        gauss_legendre(kQuadNodes, x, wt);
+        Quad q;
+        const double pi = 3.14159265358979323846;
+        for (int k = 0; k < kQuadNodes; ++k) {
+            q.th[k] = 0.25 * pi * (x[k] + 1.0);
+            q.wt[k] = 0.25 * pi * wt[k];
+        }
+        double* d = nullptr;
+        FTCG_CK(cudaMalloc(&d, (size_t)N * sizeof(double)));
+        k_window_factors<<<(N + 127) / 128, 128, 0, s>>>(d, N, G, win.w, win.beta, q);
+        FTCG_CK(cudaGetLastError());
+        FTCG_CK(cudaStreamSynchronize(s));       // complete before another stream reads it
+        it = g_factors.emplace(key, d).first;
+    }
+    FTCG_CK(cudaMemcpyAsync(d_out, it->second, (size_t)N * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
     return FTCG_SUCCESS;
 }
 
