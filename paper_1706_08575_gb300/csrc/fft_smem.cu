@@ -82,28 +82,6 @@ ftcg_status_t build_smem_fft(Plan* p, const std::vector<unsigned char>& occ, cud
         if (any) blocks.push_back(b);
     }
     p->n_col_blocks = (int)blocks.size();
-    // spreading order: the non-empty tiles (heaviest first), then the empty tiles whose columns the
-    // transform reads (they must hold zeros), then the rest, which the adjoint does not store
-    Binning& bn = p->bin;
-    if (bn.ntiles > 0 && bn.tile_order && bn.n_entries > 0) {
-        std::vector<int> order(bn.ntiles);
-        FTCG_CK(cudaMemcpyAsync(order.data(), bn.tile_order, bn.ntiles * sizeof(int),
-                                cudaMemcpyDeviceToHost, s));
-        FTCG_CK(cudaStreamSynchronize(s));
-        std::vector<int> read, skip;
-        for (int i = bn.n_nonempty; i < bn.ntiles; ++i) {
-            const int tx = order[i] % bn.ntx;
-            bool any = false;
-            for (int x = tx * bn.T; x < std::min(G, tx * bn.T + bn.T); ++x) any = any || occ[x];
-            (any ? read : skip).push_back(order[i]);
-        }
-        std::copy(read.begin(), read.end(), order.begin() + bn.n_nonempty);
-        std::copy(skip.begin(), skip.end(), order.begin() + bn.n_nonempty + read.size());
-        bn.n_read = bn.n_nonempty + (int)read.size();
-        FTCG_CK(cudaMemcpyAsync(bn.tile_order, order.data(), bn.ntiles * sizeof(int),
-                                cudaMemcpyHostToDevice, s));
-        FTCG_CK(cudaStreamSynchronize(s));
-    }
     std::vector<unsigned> mask((G / kColBlock + 31) / 32, 0u);
     for (int b : blocks) mask[b >> 5] |= 1u << (b & 31);
     FTCG_CK(pool_malloc(&p->col_mask, mask.size() * sizeof(unsigned), s));

@@ -296,6 +296,20 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
         run = first[x % b.G] ? b.W : run - 1;
         if (run > 0) b.col_occ[x % b.G] = 1;
     }
+    // launch order: non-empty tiles (heaviest first), then the empty tiles in columns that taps
+    // reach (a pruned inverse transform reads them, so they must hold zeros), then the rest
+    {
+        std::vector<int> read, skip;
+        for (int i = b.n_nonempty; i < b.ntiles; ++i) {
+            const int x0 = (order[i] % b.ntx) * b.T;
+            bool any = false;
+            for (int x = x0; x < std::min(b.G, x0 + b.T) && !any; ++x) any = b.col_occ[x] != 0;
+            (any ? read : skip).push_back(order[i]);
+        }
+        std::copy(read.begin(), read.end(), order.begin() + b.n_nonempty);
+        std::copy(skip.begin(), skip.end(), order.begin() + b.n_nonempty + read.size());
+        b.n_read = b.n_nonempty + (int)read.size();
+    }
     FTCG_CK(pool_malloc(&b.tile_order, b.ntiles * sizeof(int), s));
     *bytes += b.ntiles * sizeof(int);
     FTCG_CK(cudaMemcpyAsync(b.tile_order, order.data(), b.ntiles * sizeof(int),
