@@ -247,6 +247,21 @@ ftcg_status_t ftcg_batch_destroy(ftcg_batch_t batch);
  */
 ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t M,
                             void* d_features, int32_t* d_neighbors, ftcg_stream_t stream);
+/*
+ * ftcg_features_batch -- ftcg_features of n independent rasters in one request (neighbours are
+ * searched within each raster only): raster i has d_lambda[i] (M[i] x 2 float64), d_aux[i]
+ * (NULL, or d_aux itself NULL for all), d_features[i] (M[i] x 48 bfloat16, out) and
+ * d_neighbors[i] (NULL, or d_neighbors itself NULL for all); M[i] = 0 is allowed. The pointer
+ * arrays are host arrays of device pointers; outputs are bit-identical to n single calls. The
+ * bounding boxes of all rasters are read back with one synchronisation, then the sorts and
+ * searches run back to back over a few side streams ordered after and before `stream`; the call
+ * synchronises before it returns. FTCG_ERR_NUMERIC (nothing written) if any raster has a
+ * non-finite coordinate; FTCG_ERR_INVALID_VALUE names the first bad raster.
+ */
+ftcg_status_t ftcg_features_batch(int32_t n, const double* const* d_lambda,
+                                  const double* const* d_aux, const int64_t* M,
+                                  void* const* d_features, int32_t* const* d_neighbors,
+                                  ftcg_stream_t stream);
 
 typedef struct ftcg_mlp_s* ftcg_mlp_t;
 enum { FTCG_MLP_PARAMS = 10561 };

@@ -4,4 +4,4 @@ The compute lives in libftcg.so (C ABI, include/ftcg.h, CUDA kernels for sm_103a
 only builds it and marshals arguments to it.
 """
 from .ftcg import (BF16X2, C64, F32, F64, MLP_PARAMS, PREC_BF16, PREC_FP32, Batch,  # noqa: F401
-                   FtcgError, Mlp, Plan, features, lib, lib_path)
+                   FtcgError, Mlp, Plan, features, features_batch, lib, lib_path)

@@ -20,6 +20,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -49,6 +51,7 @@ __global__ void k_bbox(const double* __restrict__ lam, int64_t M, double* __rest
          i += (int64_t)gridDim.x * blockDim.x) {
         const double x = lam[2 * i], y = lam[2 * i + 1];
         mnx = fmin(mnx, x); mny = fmin(mny, y); mxx = fmax(mxx, x); mxy = fmax(mxy, y);
+        if (isnan(x) || isnan(y)) mxx = INFINITY;   // fmin / fmax skip NaN: make it visible
     }
     s[0][threadIdx.x] = mnx; s[1][threadIdx.x] = mny; s[2][threadIdx.x] = mxx; s[3][threadIdx.x] = mxy;
     __syncthreads();
@@ -737,6 +740,167 @@ ftcg_status_t batch_grads(Mlp* q, const __nv_bfloat16* X, const double* target, 
     return FTCG_SUCCESS;
 }
 
+// ---------------------------------------------------------------------------------------------
+// kNN feature requests (one or many rasters)
+// ---------------------------------------------------------------------------------------------
+struct FeatJob {
+    const double* lam;
+    const double* aux;
+    int64_t M;
+    __nv_bfloat16* out;
+    int32_t* nbr;
+};
+
+// The spatial hash of a raster from the per-block partials of its bounding box: square cells of
+// about one sample each (at most 4096 per axis, also when the samples lie on a line), and the
+// bound on the FP32 offset error (2^-24 of twice the extent, with a 1% margin). False when a
+// coordinate is not finite.
+bool hash_from_box(const double* part, int nblk, int64_t M, Hash* hs, float* err) {
+    double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
+    for (int i = 0; i < nblk; ++i) {
+        x0 = std::min(x0, part[4 * i]);
+        y0 = std::min(y0, part[4 * i + 1]);
+        x1 = std::max(x1, part[4 * i + 2]);
+        y1 = std::max(y1, part[4 * i + 3]);
+    }
+    if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(x1) || !std::isfinite(y1))
+        return false;
+    const double area = std::max((x1 - x0) * (y1 - y0), 1e-300);
+    double h = std::sqrt(area / (double)M);
+    if (!(h > 0)) h = 1.0;
+    h = std::max(h, std::max(x1 - x0, y1 - y0) / 4096.0);
+    if (!(h > 0)) h = 1.0;
+    hs->x0 = x0;
+    hs->y0 = y0;
+    hs->h = h;
+    hs->inv_h = 1.0 / h;
+    hs->nx = std::max(1, (int)std::ceil((x1 - x0) / h + 1e-9));
+    hs->ny = std::max(1, (int)std::ceil((y1 - y0) / h + 1e-9));
+    *err = (float)(2.0 * std::max(x1 - x0, y1 - y0) * 5.9604644775390625e-8 * 1.01);
+    return true;
+}
+
+// The counting sort of one raster into its hash cells and the kNN search, enqueued on s
+// (asynchronous; the temporaries come from the pool and are released on s).
+ftcg_status_t launch_knn(const FeatJob& j, const Hash& hs, float err, cudaStream_t s) {
+    const int64_t M = j.M;
+    const int64_t ncell = (int64_t)hs.nx * hs.ny;
+    int *cnt = nullptr, *start = nullptr, *cell = nullptr, *sorted = nullptr;
+    double2* pts = nullptr;
+    float2* pts32 = nullptr;
+    FTCG_CK(pool_malloc(&cnt, (ncell + 1) * sizeof(int), s));
+    FTCG_CK(pool_malloc(&start, (ncell + 1) * sizeof(int), s));
+    FTCG_CK(pool_malloc(&cell, M * sizeof(int), s));
+    FTCG_CK(pool_malloc(&sorted, M * sizeof(int), s));
+    FTCG_CK(pool_malloc(&pts, M * sizeof(double2), s));
+    FTCG_CK(pool_malloc(&pts32, M * sizeof(float2), s));
+    FTCG_CK(cudaMemsetAsync(cnt, 0, (ncell + 1) * sizeof(int), s));
+    k_cell_count<<<nb(M, 256), 256, 0, s>>>(j.lam, M, hs, cnt, cell);
+    FTCG_TRY(exclusive_scan_i32(cnt, start, ncell + 1, s));
+    FTCG_CK(cudaMemcpyAsync(cnt, start, (ncell + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    k_cell_scatter<<<nb(M, 256), 256, 0, s>>>(M, cell, cnt, sorted);
+    k_gather_pts<<<nb(M, 256), 256, 0, s>>>(j.lam, M, sorted, hs.x0, hs.y0, pts, pts32);
+    // 16-byte row stores need 16-byte aligned outputs (rows are 96 and 64 bytes)
+    const bool vec = (reinterpret_cast<uintptr_t>(j.out) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(j.nbr) & 15) == 0;
+    k_knn<<<nb(M, 128, 152 * 32), 128, 0, s>>>(j.lam, j.aux, M, hs, start, sorted, pts, pts32, err,
+                                                  j.out, j.nbr, vec);
+    const cudaError_t e = cudaGetLastError();
+    pool_free(cnt, s);
+    pool_free(start, s);
+    pool_free(cell, s);
+    pool_free(sorted, s);
+    pool_free(pts, s);
+    pool_free(pts32, s);
+    FTCG_CK(e);
+    return FTCG_SUCCESS;
+}
+
+// Side streams over which the searches of a multi-raster request are spread (created once per
+// device, non-blocking; ordered after and before the caller's stream by events).
+constexpr int kFeatStreams = 4;
+
+ftcg_status_t feat_streams(cudaStream_t* out) {
+    static std::mutex mu;
+    static std::map<int, std::vector<cudaStream_t>> by_dev;
+    int dev = 0;
+    FTCG_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto& v = by_dev[dev];
+    while ((int)v.size() < kFeatStreams) {
+        cudaStream_t st = nullptr;
+        FTCG_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        v.push_back(st);
+    }
+    for (int k = 0; k < kFeatStreams; ++k) out[k] = v[k];
+    return FTCG_SUCCESS;
+}
+
+// Features of n rasters: the bounding boxes of all of them with one synchronisation, then the
+// rasters' sorts and searches back to back (spread over the side streams when n > 1), then one
+// synchronisation. A raster with a non-finite coordinate fails the request before any search.
+ftcg_status_t features_impl(const FeatJob* jobs, int n, cudaStream_t s, const char* what) {
+    std::vector<int> nblk(n, 0), boff(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        nblk[i] = jobs[i].M > 0 ? nb(jobs[i].M, 256, 1024) : 0;
+        boff[i + 1] = boff[i] + nblk[i];
+    }
+    if (boff[n] == 0) return FTCG_SUCCESS;
+    double* bb = nullptr;
+    FTCG_CK(pool_malloc(&bb, (size_t)boff[n] * 4 * sizeof(double), s));
+    for (int i = 0; i < n; ++i)
+        if (nblk[i]) k_bbox<<<nblk[i], 256, 0, s>>>(jobs[i].lam, jobs[i].M, bb + 4 * boff[i]);
+    std::vector<double> hb((size_t)boff[n] * 4);
+    FTCG_CK(cudaGetLastError());
+    FTCG_CK(cudaMemcpyAsync(hb.data(), bb, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FTCG_CK(cudaStreamSynchronize(s));
+    pool_free(bb, s);
+    std::vector<Hash> hs(n);
+    std::vector<float> err(n, 0.f);
+    for (int i = 0; i < n; ++i) {
+        if (!nblk[i]) continue;
+        if (!hash_from_box(hb.data() + 4 * boff[i], nblk[i], jobs[i].M, &hs[i], &err[i])) {
+            if (n == 1)
+                set_error("%s: non-finite coordinates", what);
+            else
+                set_error("%s: raster %d has non-finite coordinates", what, i);
+            return FTCG_ERR_NUMERIC;
+        }
+    }
+    int active = 0;
+    for (int i = 0; i < n; ++i) active += nblk[i] ? 1 : 0;
+    if (active == 1) {
+        for (int i = 0; i < n; ++i)
+            if (nblk[i]) FTCG_TRY(launch_knn(jobs[i], hs[i], err[i], s));
+        FTCG_CK(cudaStreamSynchronize(s));
+        return FTCG_SUCCESS;
+    }
+    cudaStream_t side[kFeatStreams];
+    FTCG_TRY(feat_streams(side));
+    cudaEvent_t ev[kFeatStreams + 1];
+    for (auto& e : ev) FTCG_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ftcg_status_t st = FTCG_SUCCESS;
+    cudaError_t ce = cudaEventRecord(ev[kFeatStreams], s);
+    for (int k = 0; k < kFeatStreams && ce == cudaSuccess; ++k)
+        ce = cudaStreamWaitEvent(side[k], ev[kFeatStreams], 0);
+    for (int i = 0, k = 0; i < n && ce == cudaSuccess && st == FTCG_SUCCESS; ++i) {
+        if (!nblk[i]) continue;
+        st = launch_knn(jobs[i], hs[i], err[i], side[k]);
+        k = (k + 1) % kFeatStreams;
+    }
+    // the caller's stream waits for every side stream, also after a failed launch
+    for (int k = 0; k < kFeatStreams; ++k) {
+        cudaEventRecord(ev[k], side[k]);
+        cudaStreamWaitEvent(s, ev[k], 0);
+    }
+    const cudaError_t se = cudaStreamSynchronize(s);
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (st != FTCG_SUCCESS) return st;
+    FTCG_CK(ce);
+    FTCG_CK(se);
+    return FTCG_SUCCESS;
+}
+
 }  // namespace
 }  // namespace ftcg
 
@@ -749,75 +913,34 @@ ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t
     clear_error();
     if (M < 0 || (M > 0 && (!d_lambda || !d_features)))
         return mlp_fail("ftcg_features: bad arguments");
-    if (M == 0) return FTCG_SUCCESS;
     if (M > (int64_t)INT32_MAX / kNb) return mlp_fail("ftcg_features: M too large");
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int nbk = nb(M, 256, 1024);
-    double* bb = nullptr;
-    FTCG_CK(pool_malloc(&bb, nbk * 4 * sizeof(double), s));
-    k_bbox<<<nbk, 256, 0, s>>>(d_lambda, M, bb);
-    std::vector<double> hb(nbk * 4);
-    FTCG_CK(cudaMemcpyAsync(hb.data(), bb, nbk * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    FTCG_CK(cudaStreamSynchronize(s));
-    pool_free(bb, s);
-    double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
-    for (int i = 0; i < nbk; ++i) {
-        x0 = std::min(x0, hb[4 * i]);
-        y0 = std::min(y0, hb[4 * i + 1]);
-        x1 = std::max(x1, hb[4 * i + 2]);
-        y1 = std::max(y1, hb[4 * i + 3]);
+    const FeatJob job{d_lambda, d_aux, M, reinterpret_cast<__nv_bfloat16*>(d_features), d_neighbors};
+    return features_impl(&job, 1, reinterpret_cast<cudaStream_t>(stream), "ftcg_features");
+}
+
+ftcg_status_t ftcg_features_batch(int32_t n, const double* const* d_lambda,
+                                  const double* const* d_aux, const int64_t* M,
+                                  void* const* d_features, int32_t* const* d_neighbors,
+                                  ftcg_stream_t stream) {
+    clear_error();
+    if (n < 0 || (n > 0 && (!d_lambda || !M || !d_features)))
+        return mlp_fail("ftcg_features_batch: bad arguments");
+    std::vector<FeatJob> jobs(n);
+    for (int i = 0; i < n; ++i) {
+        if (M[i] < 0 || (M[i] > 0 && (!d_lambda[i] || !d_features[i]))) {
+            set_error("ftcg_features_batch: bad arguments for raster %d", i);
+            return FTCG_ERR_INVALID_VALUE;
+        }
+        if (M[i] > (int64_t)INT32_MAX / kNb) {
+            set_error("ftcg_features_batch: raster %d: M too large", i);
+            return FTCG_ERR_INVALID_VALUE;
+        }
+        jobs[i] = FeatJob{d_lambda[i], d_aux ? d_aux[i] : nullptr, M[i],
+                          reinterpret_cast<__nv_bfloat16*>(d_features[i]),
+                          d_neighbors ? d_neighbors[i] : nullptr};
     }
-    if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(x1) || !std::isfinite(y1)) {
-        set_error("ftcg_features: non-finite coordinates");
-        return FTCG_ERR_NUMERIC;
-    }
-    const double area = std::max((x1 - x0) * (y1 - y0), 1e-300);
-    double h = std::sqrt(area / (double)M);           // one sample per bounding-box cell
-    if (!(h > 0)) h = 1.0;
-    Hash hs;
-    hs.x0 = x0;
-    hs.y0 = y0;
-    // at most 4096 cells per axis (also when the samples lie on a line)
-    h = std::max(h, std::max(x1 - x0, y1 - y0) / 4096.0);
-    if (!(h > 0)) h = 1.0;
-    hs.h = h;
-    hs.inv_h = 1.0 / h;
-    hs.nx = std::max(1, (int)std::ceil((x1 - x0) / h + 1e-9));
-    hs.ny = std::max(1, (int)std::ceil((y1 - y0) / h + 1e-9));
-    const int64_t ncell = (int64_t)hs.nx * hs.ny;
-    int *cnt = nullptr, *start = nullptr, *cell = nullptr, *sorted = nullptr;
-    FTCG_CK(pool_malloc(&cnt, (ncell + 1) * sizeof(int), s));
-    FTCG_CK(pool_malloc(&start, (ncell + 1) * sizeof(int), s));
-    FTCG_CK(pool_malloc(&cell, M * sizeof(int), s));
-    FTCG_CK(pool_malloc(&sorted, M * sizeof(int), s));
-    FTCG_CK(cudaMemsetAsync(cnt, 0, (ncell + 1) * sizeof(int), s));
-    k_cell_count<<<nb(M, 256), 256, 0, s>>>(d_lambda, M, hs, cnt, cell);
-    FTCG_TRY(exclusive_scan_i32(cnt, start, ncell + 1, s));
-    FTCG_CK(cudaMemcpyAsync(cnt, start, (ncell + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
-    k_cell_scatter<<<nb(M, 256), 256, 0, s>>>(M, cell, cnt, sorted);
-    double2* pts = nullptr;
-    float2* pts32 = nullptr;
-    FTCG_CK(pool_malloc(&pts, M * sizeof(double2), s));
-    FTCG_CK(pool_malloc(&pts32, M * sizeof(float2), s));
-    k_gather_pts<<<nb(M, 256), 256, 0, s>>>(d_lambda, M, sorted, x0, y0, pts, pts32);
-    // bound on the FP32 offset error: 2^-24 of twice the extent, with a 1% margin
-    const float err = (float)(2.0 * std::max(x1 - x0, y1 - y0) * 5.9604644775390625e-8 * 1.01);
-    // 16-byte row stores need 16-byte aligned outputs (rows are 96 and 64 bytes)
-    const bool vec = (reinterpret_cast<uintptr_t>(d_features) & 15) == 0 &&
-                     (reinterpret_cast<uintptr_t>(d_neighbors) & 15) == 0;
-    k_knn<<<nb(M, 128, 152 * 32), 128, 0, s>>>(d_lambda, d_aux, M, hs, start, sorted, pts, pts32,
-                                                  err, reinterpret_cast<__nv_bfloat16*>(d_features),
-                                                  d_neighbors, vec);
-    cudaError_t e = cudaGetLastError();
-    cudaStreamSynchronize(s);
-    pool_free(cnt, s);
-    pool_free(start, s);
-    pool_free(cell, s);
-    pool_free(sorted, s);
-    pool_free(pts, s);
-    pool_free(pts32, s);
-    FTCG_CK(e);
-    return FTCG_SUCCESS;
+    return features_impl(jobs.data(), n, reinterpret_cast<cudaStream_t>(stream),
+                         "ftcg_features_batch");
 }
 
 ftcg_status_t ftcg_mlp_create(ftcg_mlp_t* out, const float* h_params) {

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("ftcg_batch_info", _I32, [_VP, _VP, _VP, _VP]),
     ("ftcg_batch_destroy", _I32, [_VP]),
     ("ftcg_features", _I32, [_VP, _VP, _I64, _VP, _VP, _VP]),
+    ("ftcg_features_batch", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ftcg_mlp_create", _I32, [ctypes.POINTER(_VP), _VP]),
     ("ftcg_mlp_state", _I32, [_VP, _VP, _VP, _VP, _VP, _I32]),
     ("ftcg_mlp_predict", _I32, [_VP, _VP, _I64, _VP, _VP]),
@@ -364,6 +365,37 @@ def features(lam, aux=None, neighbors=False, stream=None):
     a = aux.contiguous().to(torch.float64) if aux is not None else None
     _check(lib().ftcg_features(_ptr(lam), _ptr(a), M, _ptr(out), _ptr(nb), _stream(stream)))
     return (out, nb) if neighbors else out
+
+
+def features_batch(lams, auxs=None, neighbors=False, stream=None, concat=False):
+    """kNN features of several independent rasters in one request (ftcg_features_batch).
+    Returns the list of per-raster (M_i x 48) bfloat16 tensors, views of one (sum M_i, 48) tensor
+    (returned itself with concat=True, rows in raster order); with neighbors=True a pair
+    (features, neighbour indices) of such results."""
+    import torch
+    n = len(lams)
+    lams = [l.contiguous() for l in lams]
+    for l in lams:
+        if l.dtype != torch.float64 or l.dim() != 2 or l.shape[1] != 2 or not l.is_cuda:
+            raise TypeError("every lam must be a CUDA float64 tensor of shape (M, 2)")
+    if auxs is not None:
+        if len(auxs) != n:
+            raise ValueError("one aux tensor per raster")
+        auxs = [a.contiguous().to(torch.float64) if a is not None else None for a in auxs]
+    Ms = [int(l.shape[0]) for l in lams]
+    dev = lams[0].device if n else torch.device("cuda")
+    cat = torch.empty((sum(Ms), FEAT_WIDTH), dtype=torch.bfloat16, device=dev)
+    parts = list(torch.split(cat, Ms)) if n else []
+    nb_cat = torch.empty((sum(Ms), 16), dtype=torch.int32, device=dev) if neighbors else None
+    nb_parts = list(torch.split(nb_cat, Ms)) if neighbors and n else None
+    M_arr = (ctypes.c_int64 * max(n, 1))(*Ms)
+    _check(lib().ftcg_features_batch(n, _ptr_array(lams),
+                                     _ptr_array(auxs) if auxs is not None else None, M_arr,
+                                     _ptr_array(parts), _ptr_array(nb_parts) if neighbors else None,
+                                     _stream(stream)))
+    if concat:
+        return (cat, nb_cat) if neighbors else cat
+    return (parts, nb_parts) if neighbors else parts
 
 
 class Mlp:

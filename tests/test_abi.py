@@ -81,3 +81,16 @@ def test_null_plan_calls(L):
     assert L.ftcg_weights(None, None, None) == 1
     assert L.ftcg_check(None) == 1
     assert L.ftcg_plan_info(None, None) == 1
+
+
+def test_features_batch_rejects(L):
+    """Argument errors of the multi-raster feature request are found before any device call."""
+    M = (ctypes.c_int64 * 2)(5, 0)
+    null2 = (ctypes.c_void_p * 2)(None, None)
+    assert L.ftcg_features_batch(-1, None, None, None, None, None, None) == 1
+    assert L.ftcg_features_batch(2, None, None, M, null2, None, None) == 1
+    assert L.ftcg_features_batch(2, null2, None, M, null2, None, None) == 1
+    assert b"raster 0" in L.ftcg_last_error()
+    bad = (ctypes.c_int64 * 2)(0, -3)
+    assert L.ftcg_features_batch(2, null2, None, bad, null2, None, None) == 1
+    assert b"raster 1" in L.ftcg_last_error()

@@ -79,6 +79,40 @@ def test_features_unaligned_outputs(F):
     assert torch.equal(nbuf[1:].view(M, 16), nb)
 
 
+def test_features_batch_matches_single_calls(F):
+    """Several rasters in one request (an empty one, one with fewer than 16 other samples, uneven
+    sizes, aux given for some): features and neighbours bit-identical to one call per raster,
+    and neighbours of the small raster checked against the oracle."""
+    import torch
+    from paper_1706_08575_gb300 import FtcgError
+    rng = np.random.default_rng(4)
+    sizes = [1500, 0, 5, 7000, 300, 2500]
+    lams = [dev(rng.random((m, 2)) * 30 - 15) for m in sizes]
+    auxs = [dev(rng.uniform(-0.1, 0.1, m)) if k % 2 == 0 else None for k, m in enumerate(sizes)]
+    parts, nbs = F.features_batch(lams, auxs, neighbors=True)
+    for lam, aux, fp, nbp, m in zip(lams, auxs, parts, nbs, sizes):
+        assert fp.shape == (m, 48) and nbp.shape == (m, 16)
+        if m == 0:
+            continue
+        f1, n1 = F.features(lam, aux, neighbors=True)
+        assert torch.equal(fp, f1) and torch.equal(nbp, n1)
+    _, idx = L.knn_features(lams[4].cpu().numpy(), np.zeros(sizes[4]))
+    assert np.array_equal(nbs[4].cpu().numpy(), idx)
+    cat = F.features_batch(lams, None, concat=True)
+    assert cat.shape == (sum(sizes), 48)
+    assert torch.equal(cat[:1500, :32], parts[0][:, :32])
+    assert F.features_batch([]) == []
+    for v in (float("nan"), float("inf")):
+        bad = lams[3].clone()
+        bad[17, 1] = v
+        with pytest.raises(FtcgError) as ei:
+            F.features_batch([lams[0], bad])
+        assert ei.value.status == 5 and "raster 1" in str(ei.value)
+        with pytest.raises(FtcgError) as ei:
+            F.features(bad)
+        assert ei.value.status == 5
+
+
 def test_forward_and_grads_vs_oracle(F):
     import torch
     rng = np.random.default_rng(1)
