@@ -251,6 +251,7 @@ struct Batch {
     int2* d_items = nullptr;
     int nitems = 0;
     int* d_counter = nullptr;
+    unsigned* d_masks = nullptr;  // shared-memory FFT column-block masks of all pings
     int max_N = 0;
     bool any_halo = false;
     int persistent_ctas = 0;
@@ -274,6 +275,7 @@ void release_batch(Batch* b) {
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_masks) cudaFree(b->d_masks);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     delete b;
 }
@@ -483,15 +485,22 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         d.col_mask = nullptr;
         d.fused = c.smem ? 1 : 0;
         b.any_halo = b.any_halo || bn.halo;
-        std::vector<int> cp((size_t)bn.ntiles * bn.ncb + 1);
-        FTCG_CK(cudaMemcpy(cp.data(), bn.colptr, cp.size() * sizeof(int), cudaMemcpyDeviceToHost));
-        for (int t = 0; t < bn.ntiles; ++t)
-            items.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t});
+        if ((int)bn.tile_cnt.size() == bn.ntiles) {
+            for (int t = 0; t < bn.ntiles; ++t) items.push_back({bn.tile_cnt[t], i, t});
+        } else {
+            std::vector<int> cp((size_t)bn.ntiles * bn.ncb + 1);
+            FTCG_CK(cudaMemcpy(cp.data(), bn.colptr, cp.size() * sizeof(int),
+                               cudaMemcpyDeviceToHost));
+            for (int t = 0; t < bn.ntiles; ++t)
+                items.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t});
+        }
     }
     // shared-memory FFT classes: per ping the column blocks that taps reach (items of the column
     // pass and a bit mask for the row pass), per class the twiddles and the ping list
     std::vector<std::vector<int2>> col_items(b.classes.size());
     std::vector<std::vector<int>> cls_pings(b.classes.size());
+    std::vector<unsigned> masks;                 // all pings' masks, one upload
+    std::vector<size_t> mask_off(b.n, 0);
     for (int i = 0; i < b.n; ++i) {
         const int ci = b.cls_of[i];
         if (!b.classes[ci].smem) continue;
@@ -499,7 +508,9 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         std::vector<unsigned char> occ;
         FTCG_TRY(column_occupancy(p, s, &occ));
         const int nblk = p->G / sfft::kColBlock;
-        std::vector<unsigned> mask((nblk + 31) / 32, 0u);
+        mask_off[i] = masks.size();
+        masks.resize(masks.size() + (nblk + 31) / 32, 0u);
+        unsigned* mask = masks.data() + mask_off[i];
         for (int k = 0; k < nblk; ++k) {
             bool any = false;
             for (int c = 0; c < sfft::kColBlock; ++c) any = any || occ[k * sfft::kColBlock + c];
@@ -507,12 +518,15 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
             col_items[ci].push_back(make_int2(i, k));
             mask[k >> 5] |= 1u << (k & 31);
         }
-        FTCG_CK(cudaMalloc(&p->col_mask, mask.size() * sizeof(unsigned)));
-        FTCG_CK(cudaMemcpy(p->col_mask, mask.data(), mask.size() * sizeof(unsigned),
-                           cudaMemcpyHostToDevice));
-        b.device_bytes += (int64_t)(mask.size() * sizeof(unsigned));
-        b.h_desc[i].col_mask = p->col_mask;
         cls_pings[ci].push_back(i);
+    }
+    if (!masks.empty()) {
+        FTCG_CK(cudaMalloc(&b.d_masks, masks.size() * sizeof(unsigned)));
+        FTCG_CK(cudaMemcpy(b.d_masks, masks.data(), masks.size() * sizeof(unsigned),
+                           cudaMemcpyHostToDevice));
+        b.device_bytes += (int64_t)(masks.size() * sizeof(unsigned));
+        for (int i = 0; i < b.n; ++i)
+            if (b.classes[b.cls_of[i]].smem) b.h_desc[i].col_mask = b.d_masks + mask_off[i];
     }
     for (size_t ci = 0; ci < b.classes.size(); ++ci) {
         auto& c = b.classes[ci];

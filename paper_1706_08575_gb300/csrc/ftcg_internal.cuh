@@ -120,6 +120,8 @@ struct Binning {
     int* tile_order = nullptr;          // tiles by decreasing entry count (launch order)
     int n_nonempty = 0;                 // tiles with at least one entry (a prefix of tile_order)
     std::vector<unsigned char> col_occ; // host: 1 for every grid column some tap reaches
+    std::vector<int> tile_cnt;          // host: entries per tile
+    std::vector<int> h_order;           // host copy of tile_order
     int n_read = 0;                     // tiles the pruned inverse transform reads (a prefix of
                                         // tile_order holding the non-empty ones; 0 = all)
     bool halo = false;                  // FTCG_LAYOUT_HALO: one entry per sample + halo strips

@@ -240,12 +240,12 @@ ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStr
     if (n <= 0) return FTCG_SUCCESS;
     int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     int* bsum = nullptr;
-    FTCG_CK(cudaMallocAsync(&bsum, nb * sizeof(int), s));
+    FTCG_CK(pool_malloc(&bsum, nb * sizeof(int), s));
     k_scan_sums<<<(unsigned)nb, kThreads, 0, s>>>(d_in, n, bsum);
     k_scan_single<<<1, kThreads, 0, s>>>(bsum, nb);
     k_scan_apply<<<(unsigned)nb, kThreads, 0, s>>>(d_in, n, bsum, d_out);
     FTCG_CK(cudaGetLastError());
-    FTCG_CK(cudaFreeAsync(bsum, s));
+    FTCG_CK(pool_free(bsum, s));
     return FTCG_SUCCESS;
 }
 
@@ -270,9 +270,13 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
     FTCG_CK(cudaMemcpyAsync(cp.data(), b.colptr, (nbins + 1) * sizeof(int), cudaMemcpyDeviceToHost,
                             s));
     FTCG_CK(cudaStreamSynchronize(s));
-    std::vector<int> order(b.ntiles);
+    b.tile_cnt.resize(b.ntiles);
+    for (int t = 0; t < b.ntiles; ++t)
+        b.tile_cnt[t] = cp[(int64_t)(t + 1) * b.ncb] - cp[(int64_t)t * b.ncb];
+    std::vector<int>& order = b.h_order;
+    order.resize(b.ntiles);
     std::iota(order.begin(), order.end(), 0);
-    auto cnt = [&](int t) { return cp[(int64_t)(t + 1) * b.ncb] - cp[(int64_t)t * b.ncb]; };
+    auto cnt = [&](int t) { return b.tile_cnt[t]; };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cnt(x) > cnt(y); });
     b.n_nonempty = 0;
     while (b.n_nonempty < b.ntiles && cnt(order[b.n_nonempty]) > 0) ++b.n_nonempty;
@@ -312,9 +316,9 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
     }
     FTCG_CK(pool_malloc(&b.tile_order, b.ntiles * sizeof(int), s));
     *bytes += b.ntiles * sizeof(int);
+    // the host order stays alive with the binning, so the copy needs no synchronisation here
     FTCG_CK(cudaMemcpyAsync(b.tile_order, order.data(), b.ntiles * sizeof(int),
                             cudaMemcpyHostToDevice, s));
-    FTCG_CK(cudaStreamSynchronize(s));
     return FTCG_SUCCESS;
 }
 
@@ -339,8 +343,8 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
     }
     int* hist = nullptr;
     int* offs = nullptr;
-    FTCG_CK(cudaMallocAsync(&hist, nkeys * sizeof(int), s));
-    FTCG_CK(cudaMallocAsync(&offs, nkeys * sizeof(int), s));
+    FTCG_CK(pool_malloc(&hist, nkeys * sizeof(int), s));
+    FTCG_CK(pool_malloc(&offs, nkeys * sizeof(int), s));
     FTCG_CK(cudaMemsetAsync(hist, 0, nkeys * sizeof(int), s));
     k_bin_count<<<grid_for(M), kThreads, 0, s>>>(d_lambda, M, scale, G, T, W, b.ntx, b.ncb, halo,
                                                  hist, d_status, d_samp);
@@ -362,8 +366,8 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
                                                        halo, offs, b.ent);
         FTCG_CK(cudaGetLastError());
     }
-    FTCG_CK(cudaFreeAsync(hist, s));
-    FTCG_CK(cudaFreeAsync(offs, s));
+    FTCG_CK(pool_free(hist, s));
+    FTCG_CK(pool_free(offs, s));
     if (halo) {
         // per tile: the right strip (T + w - 1) x (w - 1) and the bottom strip (w - 1) x T
         b.halo_cells = (T + W - 1) * (W - 1) + (W - 1) * T;
