@@ -239,7 +239,8 @@ def run_reference(args):
 def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=8000, seed=5):
     """Pings of the uneven batch recipe, per-ping end to end (geometry changes every ping):
     plain  = per ping: plan, exact FP64 FTCG weights, FP32 adjoint;
-    learned + batched = one batched plan, kNN features + MLP weights per ping, one batched adjoint.
+    learned + batched = one batched plan, kNN features of all pings in one request, one MLP pass
+    over all their samples, one batched adjoint.
     The network is trained here on exact weights of random jittered polar geometries (about 1M
     samples). `large` = (ping, lam, values) also evaluates the large ping."""
     import numpy as np
@@ -290,8 +291,9 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
     # learned + batched
     t0 = time.perf_counter()
     with F.Batch(lams, [p.N for p in pings], 2.0, 8) as b:
-        alphas = [mlp.predict(F.features(lam, aux)) for lam, aux in zip(lams, auxs)]
-        b.set_weights(alphas)
+        # features of all pings in one request, one network pass over all their rows
+        alpha = mlp.predict(F.features_batch(lams, auxs, concat=True))
+        b.set_weights(list(torch.split(alpha, [p.M for p in pings])))
         imgs = b.adjoint(vals)
         torch.cuda.synchronize()
         t_learned = time.perf_counter() - t0
