@@ -12,10 +12,13 @@
 // it and keeps the faster for the life of the process.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "fft_smem.cuh"
@@ -398,9 +401,65 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
     return FTCG_SUCCESS;
 }
 
+// Builds the pings' plans with up to kPlanThreads host threads, each on its own stream ordered
+// after s: a plan's build waits several times for its own small transfers (entry totals, tile
+// offsets, status word), and other pings' builds fill those waits. Every plan is complete when
+// this returns (make_plan ends with a synchronisation of its stream). Per-ping status and error
+// text go to sts and msgs; the return value reports failures of the thread or stream set-up.
+constexpr int kPlanThreads = 4;
+
+ftcg_status_t make_plans_parallel(const std::vector<Plan*>& pings, const double* const* d_lambda,
+                                  cudaStream_t s, std::vector<ftcg_status_t>& sts,
+                                  std::vector<std::string>& msgs) {
+    const int n = (int)pings.size();
+    const int nt = std::min(kPlanThreads, n);
+    if (nt <= 1) {
+        for (int i = 0; i < n; ++i) {
+            sts[i] = make_plan(pings[i], d_lambda[i], s, false);
+            if (sts[i] != FTCG_SUCCESS) msgs[i] = ftcg_last_error();
+        }
+        return FTCG_SUCCESS;
+    }
+    int dev = 0;
+    FTCG_CK(cudaGetDevice(&dev));
+    cudaEvent_t ready = nullptr;
+    FTCG_CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    std::vector<cudaStream_t> ws(nt, nullptr);
+    cudaError_t ce = cudaEventRecord(ready, s);
+    for (int k = 0; k < nt && ce == cudaSuccess; ++k) {
+        ce = cudaStreamCreateWithFlags(&ws[k], cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ws[k], ready, 0);
+    }
+    if (ce == cudaSuccess) {
+        std::atomic<int> next{0};
+        auto work = [&](int k) {
+            cudaSetDevice(dev);                  // the current device is per host thread
+            for (int i; (i = next.fetch_add(1)) < n;) {
+                clear_error();
+                sts[i] = make_plan(pings[i], d_lambda[i], ws[k], false);
+                if (sts[i] != FTCG_SUCCESS) msgs[i] = ftcg_last_error();
+            }
+        };
+        std::vector<std::thread> th;
+        th.reserve(nt - 1);
+        for (int k = 1; k < nt; ++k) th.emplace_back(work, k);
+        work(0);
+        for (auto& t : th) t.join();
+    }
+    for (cudaStream_t w : ws)
+        if (w) {
+            cudaStreamSynchronize(w);
+            cudaStreamDestroy(w);
+        }
+    cudaEventDestroy(ready);
+    FTCG_CK(ce);
+    return FTCG_SUCCESS;
+}
+
 ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int64_t* M,
                               const int32_t* N, cudaStream_t s) {
-    // per-ping plans (tile side autotuned unless given)
+    // per-ping plans (tile side autotuned unless given): the tuner runs first, ping after ping
+    // (it times trial launches, which concurrent work would disturb), then the plans are built
     std::vector<int> Gs(b.n);
     for (int i = 0; i < b.n; ++i) {
         const int G = (int)std::llround(b.sigma * N[i]);
@@ -419,8 +478,17 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         p->opts.layout = layout;
         p->win = Window{b.w, es_beta(b.w, b.sigma)};
         b.pings.push_back(p);
-        ftcg_status_t st = make_plan(p, d_lambda[i], s, false);
-        if (st != FTCG_SUCCESS && st != FTCG_ERR_NUMERIC) return st;
+    }
+    std::vector<ftcg_status_t> sts(b.n, FTCG_SUCCESS);
+    std::vector<std::string> msgs(b.n);
+    FTCG_TRY(make_plans_parallel(b.pings, d_lambda, s, sts, msgs));
+    for (int i = 0; i < b.n; ++i) {
+        // coordinates that are not finite drop those samples and leave the plan usable
+        if (sts[i] != FTCG_SUCCESS && sts[i] != FTCG_ERR_NUMERIC) {
+            set_error("ftcg_plan_batch: ping %d: %s", i, msgs[i].c_str());
+            return sts[i];
+        }
+        Plan* p = b.pings[i];
         b.entries += p->bin.n_entries;
         b.device_bytes += p->device_bytes;
         b.max_N = std::max(b.max_N, N[i]);
