@@ -169,3 +169,31 @@ def test_batch_bf16_smem_classes(F):
         a_r = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
         ref = O.adjoint(lam, a_r * vr, N, 2.0, 8)
         assert O.rel_l2(img, ref) < TOL
+
+
+def test_batch_of_one_ping(F):
+    """A batch of one ping (its plan is built on the caller's thread) against the oracle."""
+    lam, v, a, N = small_batch(5)[0]
+    with F.Batch([dev(lam)], [N], 2.0, 8) as b:
+        b.set_weights([dev(a)])
+        img = b.adjoint([dev(v)])[0].cpu().numpy()
+    ref = O.adjoint(lam, a.astype(np.float32) * v.astype(np.complex128), N, 2.0, 8)
+    assert O.rel_l2(img, ref) < TOL
+
+
+def test_batch_ping_with_nonfinite_coordinate(F):
+    """A ping with a NaN coordinate among pings planned concurrently: the batch is built, that
+    sample is dropped (the image equals the oracle without it), the other pings are unaffected."""
+    cases = [c for c in small_batch(6) if c[0].shape[0] > 0]
+    lam_bad = cases[2][0].copy()
+    lam_bad[5, 0] = np.nan
+    lams = [dev(c[0]) if k != 2 else dev(lam_bad) for k, c in enumerate(cases)]
+    vals = [dev(c[1]) for c in cases]
+    with F.Batch(lams, [c[3] for c in cases], 2.0, 8) as b:
+        imgs = [x.cpu().numpy() for x in b.adjoint(vals)]
+    for k, ((lam, v, a, N), img) in enumerate(zip(cases, imgs)):
+        keep = np.ones(lam.shape[0], bool)
+        if k == 2:
+            keep[5] = False
+        ref = O.adjoint(lam[keep], v[keep].astype(np.complex128), N, 2.0, 8)
+        assert O.rel_l2(img, ref) < TOL, k
