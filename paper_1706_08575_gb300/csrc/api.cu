@@ -200,6 +200,7 @@ extern "C" {
 
 ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int32_t N,
                         double sigma, int32_t w, const ftcg_opts_t* opts, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!out) return invalid("ftcg_plan: out is NULL");
     *out = nullptr;
@@ -237,9 +238,11 @@ ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int
     }
     *out = reinterpret_cast<ftcg_plan_t>(p);
     return st;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_plan_info(ftcg_plan_t plan, ftcg_plan_info_t* info) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan || !info) return invalid("ftcg_plan_info: NULL argument");
     const Plan* p = reinterpret_cast<const Plan*>(plan);
@@ -254,19 +257,23 @@ ftcg_status_t ftcg_plan_info(ftcg_plan_t plan, ftcg_plan_info_t* info) {
     info->beta = p->win.beta;
     info->device_bytes = p->device_bytes;
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_weights(ftcg_plan_t plan, double* d_alpha_out, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_weights: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
     return compute_weights(*p, d_alpha_out, s);
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_set_weights(ftcg_plan_t plan, const void* d_alpha, int32_t dtype,
                                ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_set_weights: plan is NULL");
     if (dtype != FTCG_WEIGHTS_F64 && dtype != FTCG_WEIGHTS_F32)
@@ -275,10 +282,12 @@ ftcg_status_t ftcg_set_weights(ftcg_plan_t plan, const void* d_alpha, int32_t dt
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
     return launch_set_alpha(*p, d_alpha, dtype, s);
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_spread(ftcg_plan_t plan, const void* d_values, int32_t vdtype, void* d_grid,
                           ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_spread: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -287,20 +296,24 @@ ftcg_status_t ftcg_spread(ftcg_plan_t plan, const void* d_values, int32_t vdtype
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
     return launch_spread(*p, d_values, vdtype, reinterpret_cast<float2*>(d_grid), s);
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_adjoint(ftcg_plan_t plan, const void* d_values, int32_t vdtype, void* d_image,
                            ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_adjoint: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
     FTCG_TRY(check_values(p, d_values, vdtype, "ftcg_adjoint"));
     if (!d_image) return invalid("ftcg_adjoint: image pointer is NULL");
     return adjoint_device(p, d_values, vdtype, d_image, reinterpret_cast<cudaStream_t>(stream));
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t vdtype,
                                 void* h_image, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_adjoint_host: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -331,10 +344,12 @@ ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t 
     }
     FTCG_CK(cudaStreamSynchronize(s));
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_forward(ftcg_plan_t plan, const void* d_image, void* d_values,
                            ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_forward: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -348,9 +363,11 @@ ftcg_status_t ftcg_forward(ftcg_plan_t plan, const void* d_image, void* d_values
     FTCG_CKFFT(cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
                             reinterpret_cast<cufftComplex*>(p->grid), CUFFT_FORWARD));
     return launch_interp(*p, p->grid, reinterpret_cast<float2*>(d_values), s);
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_check(ftcg_plan_t plan) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_check: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -366,10 +383,12 @@ ftcg_status_t ftcg_check(ftcg_plan_t plan) {
         return FTCG_ERR_NUMERIC;
     }
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_plan_entries(ftcg_plan_t plan, int32_t* h_tile, int32_t* h_cx, int32_t* h_cy,
                                 int32_t* h_sample, float* h_dx, float* h_dy) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_plan_entries: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -408,9 +427,11 @@ ftcg_status_t ftcg_plan_entries(ftcg_plan_t plan, int32_t* h_tile, int32_t* h_cx
     delete[] he;
     delete[] hc;
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_profile(ftcg_plan_t plan, int32_t enable) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan) return invalid("ftcg_profile: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -434,9 +455,11 @@ ftcg_status_t ftcg_profile(ftcg_plan_t plan, int32_t enable) {
     p->profiling = enable != 0;
     p->prof_calls = 0;
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls) {
+    FTCG_API_BEGIN
     clear_error();
     if (!plan || !ms) return invalid("ftcg_stage_times: NULL argument");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -456,12 +479,15 @@ ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls) {
     for (int k = 0; k < 3; ++k) ms[k] = (float)(acc[k] / n);
     p->prof_calls = 0;
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_destroy(ftcg_plan_t plan) {
+    FTCG_API_BEGIN
     clear_error();
     release_plan(reinterpret_cast<Plan*>(plan));
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 const char* ftcg_status_string(ftcg_status_t s) {

@@ -436,8 +436,13 @@ ftcg_status_t make_plans_parallel(const std::vector<Plan*>& pings, const double*
             cudaSetDevice(dev);                  // the current device is per host thread
             for (int i; (i = next.fetch_add(1)) < n;) {
                 clear_error();
-                sts[i] = make_plan(pings[i], d_lambda[i], ws[k], false);
-                if (sts[i] != FTCG_SUCCESS) msgs[i] = ftcg_last_error();
+                try {                            // nothing may leave a host thread
+                    sts[i] = make_plan(pings[i], d_lambda[i], ws[k], false);
+                    if (sts[i] != FTCG_SUCCESS) msgs[i] = ftcg_last_error();
+                } catch (...) {
+                    sts[i] = FTCG_ERR_OUT_OF_MEMORY;
+                    msgs[i] = "host exception while building the plan";
+                }
             }
         };
         std::vector<std::thread> th;
@@ -651,6 +656,7 @@ extern "C" {
 ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const* d_lambda,
                               const int64_t* M, const int32_t* N, double sigma, int32_t w,
                               const ftcg_opts_t* opts, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!out) {
         set_error("ftcg_plan_batch: out is NULL");
@@ -690,10 +696,12 @@ ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const*
     }
     *out = reinterpret_cast<ftcg_batch_t>(b);
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_batch_set_weights(ftcg_batch_t batch, const void* const* d_alpha,
                                      int32_t dtype, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!batch) {
         set_error("ftcg_batch_set_weights: batch is NULL");
@@ -709,10 +717,12 @@ ftcg_status_t ftcg_batch_set_weights(ftcg_batch_t batch, const void* const* d_al
     for (int i = 0; i < b->n; ++i)
         FTCG_TRY(launch_set_alpha(*b->pings[i], d_alpha ? d_alpha[i] : nullptr, dtype, s));
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_batch_weights(ftcg_batch_t batch, double* const* d_alpha_out,
                                  ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!batch) {
         set_error("ftcg_batch_weights: batch is NULL");
@@ -728,10 +738,12 @@ ftcg_status_t ftcg_batch_weights(ftcg_batch_t batch, double* const* d_alpha_out,
         else if (st != FTCG_SUCCESS) return st;
     }
     return worst;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_adjoint_batch(ftcg_batch_t batch, const void* const* d_values, int32_t vdtype,
                                  void* const* d_images, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!batch) {
         set_error("ftcg_adjoint_batch: batch is NULL");
@@ -755,10 +767,12 @@ ftcg_status_t ftcg_adjoint_batch(ftcg_batch_t batch, const void* const* d_values
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     b->last = s;
     return batch_enqueue(*b, d_values, vdtype, d_images, s);
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_batch_capture(ftcg_batch_t batch, const void* const* d_values, int32_t vdtype,
                                  void* const* d_images, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!batch) {
         set_error("ftcg_batch_capture: batch is NULL");
@@ -790,9 +804,11 @@ ftcg_status_t ftcg_batch_capture(ftcg_batch_t batch, const void* const* d_values
     cudaGraphDestroy(g);
     FTCG_CK(e);
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_batch_launch(ftcg_batch_t batch, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!batch) {
         set_error("ftcg_batch_launch: batch is NULL");
@@ -807,10 +823,12 @@ ftcg_status_t ftcg_batch_launch(ftcg_batch_t batch, ftcg_stream_t stream) {
     b->last = s;
     FTCG_CK(cudaGraphLaunch(b->gexec, s));
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_batch_info(ftcg_batch_t batch, int32_t* tiles, int64_t* entries,
                               int64_t* device_bytes) {
+    FTCG_API_BEGIN
     clear_error();
     if (!batch) {
         set_error("ftcg_batch_info: batch is NULL");
@@ -822,12 +840,15 @@ ftcg_status_t ftcg_batch_info(ftcg_batch_t batch, int32_t* tiles, int64_t* entri
     if (entries) *entries = b->entries;
     if (device_bytes) *device_bytes = b->device_bytes;
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_batch_destroy(ftcg_batch_t batch) {
+    FTCG_API_BEGIN
     clear_error();
     release_batch(reinterpret_cast<Batch*>(batch));
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 }  // extern "C"

@@ -6,6 +6,8 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -38,6 +40,25 @@ void clear_error();
             return r_ == CUFFT_ALLOC_FAILED ? FTCG_ERR_OUT_OF_MEMORY : FTCG_ERR_CUDA;       \
         }                                                                                   \
     } while (0)
+
+// Every C entry point's body runs inside FTCG_API_BEGIN / FTCG_API_END, so that what the C++
+// library may throw (a failed host allocation in a std::vector, say) becomes a status and a
+// message instead of crossing the C ABI.
+#define FTCG_API_BEGIN try {
+#define FTCG_API_END                                                                        \
+    }                                                                                       \
+    catch (const std::bad_alloc&) {                                                         \
+        ::ftcg::set_error("host allocation failed");                                        \
+        return FTCG_ERR_OUT_OF_MEMORY;                                                      \
+    }                                                                                       \
+    catch (const std::exception& ex_) {                                                     \
+        ::ftcg::set_error("host exception: %s", ex_.what());                                \
+        return FTCG_ERR_INVALID_VALUE;                                                      \
+    }                                                                                       \
+    catch (...) {                                                                           \
+        ::ftcg::set_error("unknown host exception");                                        \
+        return FTCG_ERR_INVALID_VALUE;                                                      \
+    }
 
 #define FTCG_TRY(expr)                                                                      \
     do {                                                                                    \

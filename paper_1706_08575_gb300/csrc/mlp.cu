@@ -910,18 +910,21 @@ extern "C" {
 
 ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t M,
                             void* d_features, int32_t* d_neighbors, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (M < 0 || (M > 0 && (!d_lambda || !d_features)))
         return mlp_fail("ftcg_features: bad arguments");
     if (M > (int64_t)INT32_MAX / kNb) return mlp_fail("ftcg_features: M too large");
     const FeatJob job{d_lambda, d_aux, M, reinterpret_cast<__nv_bfloat16*>(d_features), d_neighbors};
     return features_impl(&job, 1, reinterpret_cast<cudaStream_t>(stream), "ftcg_features");
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_features_batch(int32_t n, const double* const* d_lambda,
                                   const double* const* d_aux, const int64_t* M,
                                   void* const* d_features, int32_t* const* d_neighbors,
                                   ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (n < 0 || (n > 0 && (!d_lambda || !M || !d_features)))
         return mlp_fail("ftcg_features_batch: bad arguments");
@@ -941,9 +944,11 @@ ftcg_status_t ftcg_features_batch(int32_t n, const double* const* d_lambda,
     }
     return features_impl(jobs.data(), n, reinterpret_cast<cudaStream_t>(stream),
                          "ftcg_features_batch");
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_mlp_create(ftcg_mlp_t* out, const float* h_params) {
+    FTCG_API_BEGIN
     clear_error();
     if (!out || !h_params) return mlp_fail("ftcg_mlp_create: NULL argument");
     *out = nullptr;
@@ -963,10 +968,12 @@ ftcg_status_t ftcg_mlp_create(ftcg_mlp_t* out, const float* h_params) {
     cudaMemset(q->v, 0, bytes);
     *out = reinterpret_cast<ftcg_mlp_t>(q);
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_mlp_state(ftcg_mlp_t mlp, float* h_params, float* h_m, float* h_v,
                              int64_t* step, int32_t set) {
+    FTCG_API_BEGIN
     clear_error();
     if (!mlp) return mlp_fail("ftcg_mlp_state: NULL model");
     Mlp* q = reinterpret_cast<Mlp*>(mlp);
@@ -981,10 +988,12 @@ ftcg_status_t ftcg_mlp_state(ftcg_mlp_t mlp, float* h_params, float* h_m, float*
         else *step = q->step;
     }
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_mlp_predict(ftcg_mlp_t mlp, const void* d_features, int64_t M,
                                double* d_alpha_out, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!mlp || M < 0 || (M > 0 && (!d_features || !d_alpha_out)))
         return mlp_fail("ftcg_mlp_predict: bad arguments");
@@ -992,11 +1001,13 @@ ftcg_status_t ftcg_mlp_predict(ftcg_mlp_t mlp, const void* d_features, int64_t M
     Mlp* q = reinterpret_cast<Mlp*>(mlp);
     return launch_forward(q, reinterpret_cast<const __nv_bfloat16*>(d_features), nullptr, M, false,
                           d_alpha_out, reinterpret_cast<cudaStream_t>(stream));
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_mlp_grads(ftcg_mlp_t mlp, const void* d_features, const double* d_target,
                              const int32_t* d_index, int64_t B, float* h_grads, float* h_loss,
                              ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!mlp || B <= 0 || !d_features || !d_target) return mlp_fail("ftcg_mlp_grads: bad arguments");
     Mlp* q = reinterpret_cast<Mlp*>(mlp);
@@ -1008,11 +1019,13 @@ ftcg_status_t ftcg_mlp_grads(ftcg_mlp_t mlp, const void* d_features, const doubl
     if (h_loss) FTCG_CK(cudaMemcpyAsync(h_loss, q->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     FTCG_CK(cudaStreamSynchronize(s));
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_mlp_train_step(ftcg_mlp_t mlp, const void* d_features, const double* d_target,
                                   const int32_t* d_index, int64_t B, float lr, float* h_loss,
                                   ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     clear_error();
     if (!mlp || B <= 0 || !d_features || !d_target || !(lr > 0))
         return mlp_fail("ftcg_mlp_train_step: bad arguments");
@@ -1032,9 +1045,11 @@ ftcg_status_t ftcg_mlp_train_step(ftcg_mlp_t mlp, const void* d_features, const 
         FTCG_CK(cudaStreamSynchronize(s));
     }
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 ftcg_status_t ftcg_mlp_destroy(ftcg_mlp_t mlp) {
+    FTCG_API_BEGIN
     clear_error();
     if (!mlp) return FTCG_SUCCESS;
     Mlp* q = reinterpret_cast<Mlp*>(mlp);
@@ -1047,6 +1062,7 @@ ftcg_status_t ftcg_mlp_destroy(ftcg_mlp_t mlp) {
     cudaFree(q->loss);
     delete q;
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
 
 }  // extern "C"

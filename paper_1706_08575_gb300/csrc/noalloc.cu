@@ -205,6 +205,7 @@ extern "C" ftcg_status_t ftcg_adjoint_small_noalloc(const double* d_lambda, cons
                                                     const double* d_alpha, int64_t M, int32_t N,
                                                     double sigma, int32_t w, void* d_image,
                                                     ftcg_stream_t stream) {
+    FTCG_API_BEGIN
     ftcg::clear_error();
     if (M < 0) return na_fail(FTCG_ERR_INVALID_VALUE, "ftcg_adjoint_small_noalloc: M < 0");
     if (M > 0 && (!d_lambda || !d_values))
@@ -263,4 +264,5 @@ extern "C" ftcg_status_t ftcg_adjoint_small_noalloc(const double* d_lambda, cons
     k_na_cols<<<N, 256, 0, s>>>(ptrs.rows, ptrs.deapod, reinterpret_cast<float2*>(d_image), Gi, N);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
+    FTCG_API_END
 }
