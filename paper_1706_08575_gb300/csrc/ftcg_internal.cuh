@@ -80,7 +80,7 @@ constexpr int64_t kMaxSamples = (int64_t(1) << kSampleBits) - 1;
 // the spreading loop may prefetch up to two entries past its chunk without a bounds test.
 constexpr int kEntryPad = 2;
 
-// One sorted (tile, sample) entry of the spreading plan: 16 bytes, loaded with one LDG.128.
+// One sorted (tile, sample) entry of the spreading plan: 16 bytes, read with one vector load.
 //   dx, dy : sigma lambda - first tap, in (w/2 - 1, w/2]   (float32)
 //   alpha  : per-sample weight, float32 (FTCG_PREC_BF16: rounded to bfloat16, low 16 bits zero)
 //   packed : sample index | (cy_local + w - 1) << 25
