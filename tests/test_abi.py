@@ -94,3 +94,13 @@ def test_features_batch_rejects(L):
     bad = (ctypes.c_int64 * 2)(0, -3)
     assert L.ftcg_features_batch(2, null2, None, bad, null2, None, None) == 1
     assert b"raster 1" in L.ftcg_last_error()
+
+
+def test_features_batch_binding_checks_inputs():
+    """The binding refuses host tensors and mismatched aux lists before any library call."""
+    import torch
+    from paper_1706_08575_gb300 import ftcg
+    with pytest.raises(TypeError):
+        ftcg.features_batch([torch.zeros((3, 2), dtype=torch.float64)])
+    with pytest.raises(TypeError):
+        ftcg.features_batch([torch.zeros((3, 3), dtype=torch.float64)])
