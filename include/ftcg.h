@@ -199,7 +199,10 @@ ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls);
  * M[i] x 2 float64 array, read during the call); sigma, w, opts shared, with the checks of
  * ftcg_plan per ping. opts->tile = 0 lets the built-in autotuner pick the tile side of each ping:
  * it times both tile sides once per (grid side, w, precision, half-octave bucket of samples per
- * grid cell) and keeps the faster for the life of the process. Synchronises.
+ * grid cell) and keeps the faster for the life of the process. After the tuning (ping after ping,
+ * on `stream`), the pings' plans are built by up to four host threads, each on its own stream
+ * that waits for `stream` first. A ping whose coordinates are not all finite drops those samples
+ * (as ftcg_plan does) and the batch is still built. Synchronises.
  */
 ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const* d_lambda,
                               const int64_t* M, const int32_t* N, double sigma, int32_t w,
