@@ -90,3 +90,31 @@ def ls_image(lam, v, N):
                               np.multiply.outer(lam[:, 1], PY.ravel())) / N)
     x, *_ = np.linalg.lstsq(E, np.asarray(v, np.complex128), rcond=None)
     return x.reshape(N, N)
+
+
+def overlap_sum(d, delta, N):
+    """K(d, delta) = sum of exp(2 pi i delta q / N) over the q of {-N/2..N/2-1} for which q + d
+    is also in that set (one axis): the weight a lag d carries in a product of two Gram entries
+    whose samples are delta apart. K(d, 0) = N - |d|, the Fejer lag weight of the diagonal route."""
+    p = O.pixel_range(N)
+    q = p[(p + d >= p[0]) & (p + d <= p[-1])]
+    return np.exp(2j * np.pi * delta * q / N).sum()
+
+
+def gram2_entry_lag(lam, N, a, b):
+    """(T^2)_ab by the lag route: with H(d) = sum_j exp(2 pi i lambda_j.d / N) on the lags
+    d in {-N+1..N-1}^2 (the gridded adjoint of unit strengths that the diagonal weights use),
+    (T^2)_ab = N^-4 sum_d H(d) exp(-2 pi i lambda_a.d / N) K(d_x, delta_x) K(d_y, delta_y),
+    delta = lambda_b - lambda_a. At a = b this is S_a of the diagonal weights. Direct O(M N^2)
+    evaluation of the lag sum, for checking a device route."""
+    lam = np.asarray(lam, np.float64)
+    d = np.arange(-N + 1, N).astype(np.float64)
+    ex = np.exp(2j * np.pi * np.multiply.outer(lam[:, 0], d) / N)
+    ey = np.exp(2j * np.pi * np.multiply.outer(lam[:, 1], d) / N)
+    H = ex.T @ ey                                   # H[d_x, d_y]
+    delta = lam[b] - lam[a]
+    kx = np.array([overlap_sum(t, delta[0], N) for t in range(-N + 1, N)])
+    ky = np.array([overlap_sum(t, delta[1], N) for t in range(-N + 1, N)])
+    ph = np.multiply.outer(np.exp(-2j * np.pi * lam[a, 0] * d / N),
+                           np.exp(-2j * np.pi * lam[a, 1] * d / N))
+    return complex(np.sum(H * ph * np.multiply.outer(kx, ky)) / float(N) ** 4)

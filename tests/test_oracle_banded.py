@@ -120,3 +120,16 @@ def test_planted_mistakes_fail_a_pin(monkeypatch, name, mutant):
         except AssertionError:
             failed += 1
     assert failed > 0
+
+
+def test_gram_squared_by_the_lag_route():
+    """The entries of the banded normal equations, (T^2)_ab, by the lag route against the matrix
+    product T T; on the diagonal they are the weight sums S_k = 1 / alpha_k."""
+    lam, _ = case(4)
+    T = B.gram_matrix(lam, N)
+    T2 = T @ T
+    for a, b in ((10, 10), (10, 11), (10, 16), (3, 0), (35, 29)):
+        assert abs(B.gram2_entry_lag(lam, N, a, b) - T2[a, b]) < 1e-12 * max(1.0, abs(T2[a, a]))
+    alpha, _ = O.weights_brute(lam, N)
+    assert abs(B.gram2_entry_lag(lam, N, 7, 7).real * alpha[7] - 1.0) < 1e-12
+    assert B.overlap_sum(3, 0.0, N) == N - 3
