@@ -104,3 +104,14 @@ def test_features_batch_binding_checks_inputs():
         ftcg.features_batch([torch.zeros((3, 2), dtype=torch.float64)])
     with pytest.raises(TypeError):
         ftcg.features_batch([torch.zeros((3, 3), dtype=torch.float64)])
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the shared library absent, every call path raises."""
+    from paper_1706_08575_gb300 import ftcg
+    monkeypatch.setattr(ftcg, "_lib", None)
+    monkeypatch.setattr(ftcg, "lib_path", lambda: str(tmp_path / "libftcg.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        ftcg.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        ftcg.Mlp(__import__("numpy").zeros(ftcg.MLP_PARAMS, "float32"))
