@@ -246,7 +246,8 @@ ftcg_status_t ftcg_batch_destroy(ftcg_batch_t batch);
  * d_lambda: device M x 2 float64; d_features: device M x 48 bfloat16 (out); d_neighbors: NULL or
  * device M x 16 int32 (out, -1 where fewer than 16 other samples exist). The neighbour sets are
  * exact (a spatial hash with a ring search that stops only when no unvisited sample can be
- * closer). Allocates temporaries and synchronises.
+ * closer). Allocates temporaries and synchronises. FTCG_ERR_NUMERIC (nothing written) if a
+ * coordinate is not finite.
  */
 ftcg_status_t ftcg_features(const double* d_lambda, const double* d_aux, int64_t M,
                             void* d_features, int32_t* d_neighbors, ftcg_stream_t stream);
