@@ -208,6 +208,17 @@ ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const*
                               const int64_t* M, const int32_t* N, double sigma, int32_t w,
                               const ftcg_opts_t* opts, ftcg_stream_t stream);
 
+/*
+ * The tile autotuner's choices as a small JSON file (one entry per line: grid side, w, precision,
+ * density bucket, the requested tile and layout, and the chosen tile side and layout), so that a
+ * later process can reuse them instead of timing trial launches again. ftcg_tuner_save writes the
+ * choices made or loaded so far in this process; ftcg_tuner_load adds a file's entries (they
+ * replace choices with the same key), after checking every entry (nothing is added when one is
+ * invalid: FTCG_ERR_INVALID_VALUE naming the line). Host only: no device work, no stream.
+ */
+ftcg_status_t ftcg_tuner_save(const char* path);
+ftcg_status_t ftcg_tuner_load(const char* path);
+
 /* Per-ping weights: d_alpha is a host array of n device pointers (M[i] entries each, dtype as in
  * ftcg_set_weights) or NULL for alpha = 1 everywhere. Asynchronous. */
 ftcg_status_t ftcg_batch_set_weights(ftcg_batch_t batch, const void* const* d_alpha, int32_t dtype,

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <new>
@@ -141,6 +143,19 @@ std::map<TuneKey, std::pair<int, int>> g_tune;
 int density_bucket(int64_t M, int G) {
     const double d = (double)M / ((double)G * G);
     return d <= 0 ? -100 : (int)std::lround(2.0 * std::log2(d));
+}
+
+// The integer after "key": on a line of the tuner file; false if the key is absent.
+bool json_int(const std::string& line, const char* key, int* out) {
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t at = line.find(k);
+    if (at == std::string::npos) return false;
+    const char* p = line.c_str() + at + k.size();
+    char* end = nullptr;
+    const long v = std::strtol(p, &end, 10);
+    if (end == p || v < INT32_MIN || v > INT32_MAX) return false;
+    *out = (int)v;
+    return true;
 }
 
 // Time the spreading kernel of a plan (values are irrelevant to the cost: zeros).
@@ -847,6 +862,99 @@ ftcg_status_t ftcg_batch_destroy(ftcg_batch_t batch) {
     FTCG_API_BEGIN
     clear_error();
     release_batch(reinterpret_cast<Batch*>(batch));
+    return FTCG_SUCCESS;
+    FTCG_API_END
+}
+
+ftcg_status_t ftcg_tuner_save(const char* path) {
+    FTCG_API_BEGIN
+    clear_error();
+    if (!path) {
+        set_error("ftcg_tuner_save: path is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    std::map<TuneKey, std::pair<int, int>> snap;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        snap = g_tune;
+    }
+    FILE* f = std::fopen(path, "w");
+    if (!f) {
+        set_error("ftcg_tuner_save: cannot open %s for writing", path);
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    std::fprintf(f, "{\"ftcg_tuner\": 1, \"entries\": [\n");
+    size_t k = 0;
+    for (const auto& e : snap) {
+        std::fprintf(f,
+                     "{\"G\": %d, \"w\": %d, \"precision\": %d, \"bucket\": %d, "
+                     "\"tile_req\": %d, \"layout_req\": %d, \"tile\": %d, \"layout\": %d}%s\n",
+                     e.first.G, e.first.w, e.first.prec, e.first.bucket, e.first.tile,
+                     e.first.layout, e.second.first, e.second.second,
+                     ++k < snap.size() ? "," : "");
+    }
+    std::fprintf(f, "]}\n");
+    if (std::fclose(f) != 0) {
+        set_error("ftcg_tuner_save: writing %s failed", path);
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    return FTCG_SUCCESS;
+    FTCG_API_END
+}
+
+ftcg_status_t ftcg_tuner_load(const char* path) {
+    FTCG_API_BEGIN
+    clear_error();
+    if (!path) {
+        set_error("ftcg_tuner_load: path is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    FILE* f = std::fopen(path, "r");
+    if (!f) {
+        set_error("ftcg_tuner_load: cannot open %s", path);
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    std::vector<std::pair<TuneKey, std::pair<int, int>>> got;
+    std::string line;
+    bool header = false, bad = false;
+    int lineno = 0;
+    for (int c; !bad;) {
+        line.clear();
+        while ((c = std::fgetc(f)) != EOF && c != '\n') line.push_back((char)c);
+        if (c == EOF && line.empty()) break;
+        ++lineno;
+        if (line.find("\"ftcg_tuner\": 1") != std::string::npos) header = true;
+        if (line.find("\"G\":") == std::string::npos) continue;
+        TuneKey k{};
+        int tile = 0, layout = 0;
+        const bool ok = json_int(line, "G", &k.G) && json_int(line, "w", &k.w) &&
+                        json_int(line, "precision", &k.prec) &&
+                        json_int(line, "bucket", &k.bucket) &&
+                        json_int(line, "tile_req", &k.tile) &&
+                        json_int(line, "layout_req", &k.layout) && json_int(line, "tile", &tile) &&
+                        json_int(line, "layout", &layout);
+        const bool valid = ok && k.G >= 2 && (k.G & 1) == 0 && k.w >= 2 && k.w <= 16 &&
+                           (k.prec == FTCG_PREC_FP32 || k.prec == FTCG_PREC_BF16) &&
+                           (k.tile == 0 || k.tile == 32 || k.tile == 64) &&
+                           (k.layout >= FTCG_LAYOUT_AUTO && k.layout <= FTCG_LAYOUT_HALO) &&
+                           (tile == 32 || tile == 64) &&
+                           (layout == FTCG_LAYOUT_DUPLICATE || layout == FTCG_LAYOUT_HALO) &&
+                           (k.tile == 0 || k.tile == tile) && (k.layout == 0 || k.layout == layout);
+        if (!valid) {
+            set_error("ftcg_tuner_load: %s line %d is not a valid tuner entry", path, lineno);
+            bad = true;
+            break;
+        }
+        got.push_back({k, {tile, layout}});
+    }
+    std::fclose(f);
+    if (bad) return FTCG_ERR_INVALID_VALUE;
+    if (!header) {
+        set_error("ftcg_tuner_load: %s is not a tuner file", path);
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& e : got) g_tune[e.first] = e.second;
     return FTCG_SUCCESS;
     FTCG_API_END
 }

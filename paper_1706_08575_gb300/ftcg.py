@@ -73,6 +73,8 @@ SIGNATURES = [
     ("ftcg_batch_destroy", _I32, [_VP]),
     ("ftcg_features", _I32, [_VP, _VP, _I64, _VP, _VP, _VP]),
     ("ftcg_features_batch", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ftcg_tuner_save", _I32, [ctypes.c_char_p]),
+    ("ftcg_tuner_load", _I32, [ctypes.c_char_p]),
     ("ftcg_mlp_create", _I32, [ctypes.POINTER(_VP), _VP]),
     ("ftcg_mlp_state", _I32, [_VP, _VP, _VP, _VP, _VP, _I32]),
     ("ftcg_mlp_predict", _I32, [_VP, _VP, _I64, _VP, _VP]),
@@ -348,6 +350,16 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib().ftcg_batch_launch(self._h, _stream(stream)))
+
+
+def tuner_save(path):
+    """Write the tile autotuner's choices of this process to a JSON file (ftcg_tuner_save)."""
+    _check(lib().ftcg_tuner_save(os.fsencode(str(path))))
+
+
+def tuner_load(path):
+    """Add the tile autotuner's choices from a JSON file (ftcg_tuner_load)."""
+    _check(lib().ftcg_tuner_load(os.fsencode(str(path))))
 
 
 MLP_PARAMS = 10561

@@ -115,3 +115,35 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
         ftcg.lib()
     with pytest.raises(RuntimeError, match="not built"):
         ftcg.Mlp(__import__("numpy").zeros(ftcg.MLP_PARAMS, "float32"))
+
+
+def test_tuner_file_round_trip(L, tmp_path):
+    """The autotuner's choices go to a JSON file and come back (host only, no device work); an
+    invalid entry or a foreign file is refused and adds nothing."""
+    import json
+    from paper_1706_08575_gb300 import ftcg
+    entries = [{"G": 2048, "w": 8, "precision": 0, "bucket": -3, "tile_req": 0, "layout_req": 0,
+                "tile": 32, "layout": 2},
+               {"G": 512, "w": 6, "precision": 1, "bucket": 1, "tile_req": 64, "layout_req": 0,
+                "tile": 64, "layout": 1}]
+    src = tmp_path / "tuner.json"
+    src.write_text('{"ftcg_tuner": 1, "entries": [\n' +
+                   ",\n".join(json.dumps(e) for e in entries) + "\n]}\n")
+    ftcg.tuner_load(src)
+    out = tmp_path / "saved.json"
+    ftcg.tuner_save(out)
+    saved = json.loads(out.read_text())
+    assert saved["ftcg_tuner"] == 1
+    for e in entries:
+        assert e in saved["entries"]
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[0], G=1000, tile=48))
+                   + "\n]}\n")
+    assert L.ftcg_tuner_load(str(bad).encode()) == 1
+    assert b"line 2" in L.ftcg_last_error()
+    other = tmp_path / "other.json"
+    other.write_text(json.dumps({"entries": [dict(entries[0], G=4096)]}) + "\n")
+    assert L.ftcg_tuner_load(str(other).encode()) == 1
+    assert L.ftcg_tuner_load(str(tmp_path / "absent.json").encode()) == 1
+    ftcg.tuner_save(out)
+    assert all(e["G"] != 1000 and e["G"] != 4096 for e in json.loads(out.read_text())["entries"])
