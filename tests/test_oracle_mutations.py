@@ -60,7 +60,43 @@ def _beta_off(w, sigma, kind=O.ES):
     return _orig["kernel_beta"](w, sigma, kind) * 0.7
 
 
+def _spread_clipped(lam, c, N, sigma, w, kind=O.ES, beta=None):
+    """Taps past the grid edge clipped to the edge instead of wrapped mod G."""
+    G = O.grid_side(N, sigma)
+    if beta is None:
+        beta = O.kernel_beta(w, sigma, kind)
+    org, u = O.tap_origins(lam, N, sigma, w)
+    wx = O.tap_weights(u[:, 0], org[:, 0], w, beta, kind)
+    wy = O.tap_weights(u[:, 1], org[:, 1], w, beta, kind)
+    grid = np.zeros((G, G), np.complex128)
+    for ty in range(w):
+        iy = np.clip(org[:, 1] + ty, 0, G - 1)
+        for tx in range(w):
+            ix = np.clip(org[:, 0] + tx, 0, G - 1)
+            np.add.at(grid, (iy, ix), np.asarray(c, np.complex128) * wy[:, ty] * wx[:, tx])
+    return grid
+
+
+def _forward_sign(lam, img, N, sigma, w, kind=O.ES, beta=None):
+    """The gridded forward transform with the exponent's sign flipped."""
+    return _orig["forward"](-np.asarray(lam), img, N, sigma, w, kind, beta)
+
+
+def _fejer_unsquared(delta, N):
+    """The Dirichlet magnitude where the squared (Fejer) kernel belongs."""
+    return np.sqrt(_orig["fejer"](delta, N))
+
+
+def _pixels_shifted(lam, c, N, sigma, w, pix, kind=O.ES, beta=None):
+    return _orig["adjoint_pixels"](lam, c, N, sigma, w, np.asarray(pix) + np.array([1, 0]), kind,
+                                   beta)
+
+
 MUTATIONS = {
+    "spread_clip": ("spread", _spread_clipped),
+    "forward_sign": ("forward", _forward_sign),
+    "fejer_unsquared": ("fejer", _fejer_unsquared),
+    "pixels_shift": ("adjoint_pixels", _pixels_shifted),
     "direct_sign": ("direct_adjoint", _sign_flip_direct),
     "drop_tap": ("tap_weights", _drop_last_tap),
     "floor_origin": ("tap_origins", _floor_origin),
