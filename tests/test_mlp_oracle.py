@@ -80,3 +80,50 @@ def test_training_reduces_loss():
         y, c = L.forward(P, X)
         L.adam_step(P, L.backward(P, c, y, t), st, lr=3e-3)
     assert L.loss(L.forward(P, X)[0], t) < 0.2 * l0
+
+
+# ---- planted mistakes: each must make one of the pins above fail --------------------------------
+
+_ORIG = {k: getattr(L, k) for k in ("gelu_grad", "backward", "adam_step", "knn_features")}
+
+
+def _gelu_grad_no_cubic(z):
+    u = L._C * (z + 0.044715 * z ** 3)
+    t = np.tanh(u)
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * L._C
+
+
+def _backward_transposed(P, cache, y, t):
+    """W3 used untransposed when the error flows back through it (square, so no shape error)."""
+    Q = dict(P)
+    Q["W3"] = P["W3"].T
+    return _ORIG["backward"](Q, cache, y, t)
+
+
+def _adam_no_bias_correction(P, g, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    for k in P:
+        m = state.setdefault("m_" + k, np.zeros_like(P[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(P[k]))
+        m[...] = b1 * m + (1 - b1) * g[k]
+        v[...] = b2 * v + (1 - b2) * g[k] * g[k]
+        P[k] = P[k] - lr * m / (np.sqrt(v) + eps)
+    return P
+
+
+def _knn_ties_reversed(lam, aux, k=L.K_NN):
+    """Neighbours at equal distance taken by larger index first."""
+    M = np.asarray(lam).shape[0]
+    X, idx = _ORIG["knn_features"](np.asarray(lam)[::-1], np.asarray(aux)[::-1], k)
+    return X[::-1], (M - 1 - idx)[::-1]
+
+
+@pytest.mark.parametrize("name,mutant,pin", [
+    ("gelu_grad", _gelu_grad_no_cubic, "test_gelu_known_values"),
+    ("backward", _backward_transposed, "test_gradients_finite_differences"),
+    ("adam_step", _adam_no_bias_correction, "test_adam_first_step_is_signed_lr"),
+    ("knn_features", _knn_ties_reversed, "test_knn_ties_by_index"),
+])
+def test_planted_mistake_is_caught(monkeypatch, name, mutant, pin):
+    monkeypatch.setattr(L, name, mutant)
+    with pytest.raises(AssertionError):
+        globals()[pin]()
