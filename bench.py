@@ -1,16 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the FTCG weighted adjoint on one GB300 (prints ONE JSON line on rank 0).
 
-Workload: the large polar ping (2048 range wavenumbers x 1024 jittered angles = 2,097,152
-samples, 1% sound-speed mismatch, 2000 speckle + 20 bright scatterers), N = 1024, sigma = 2,
-w = 8, exact FTCG weights installed. A step is one weighted adjoint of the ping (spread with the
-weights, inverse FFT, window division + crop) with the plan and weights built once per geometry;
-`per_ping` times the plan and the weights too. Inputs are resident in HBM; L2 is flushed (a 256 MB
-write) before every timed step, outside its events.
+Workload: one large polar ping per GPU (2048 range wavenumbers x 1024 jittered angles =
+2,097,152 samples, 1% sound-speed mismatch, 2000 speckle + 20 bright scatterers), N = 1024,
+sigma = 2, w = 8, exact FTCG weights installed. A step is one weighted adjoint of the ping (spread
+with the weights, inverse FFT, window division + crop) with the plan and weights built once per
+geometry; `per_ping` times the plan and the weights too. Inputs are resident in HBM; L2 is
+flushed (a 256 MB write) before every timed step, outside its events.
 
---impl reference times the FP64 CPU oracle on the host cores for the same workload and metric.
-Under torchrun (N > 1) every rank grids its own copy of the ping (independent units, weak
-scaling); only the timing is reduced (max over ranks), there is no collective on the data path.
+--impl reference times the FP64 CPU oracle on the host cores (a spawned process pool over sample
+slices) for the same workload and metric.
+Under torchrun (N > 1) the pings are the independent units: rank r grids its own ping (seed
+170608576 + 100000 r), with no collective on the data path; only the timing is reduced (max
+over ranks) and `value` counts the samples of all ranks (weak scaling). The 512-ping batch extra
+is split across ranks by work (shard_pings).
 """
 from __future__ import annotations
 
@@ -30,8 +33,24 @@ if ROOT not in sys.path:
 
 METRIC = "non-uniform samples gridded/sec on 1 GB300 (+% HBM roofline) at rel-L2 err vs FP64"
 UNIT = "samples/s"
-WORKLOAD = ("large-ping: 2048 kr x 1024 theta polar (M=2097152), kr x1.01, theta jitter 0.02 deg, "
-            "2000 speckle + 20 bright, N=1024, sigma=2, w=8, exact FTCG weights")
+WORKLOAD = ("large ping per GPU (rank r: seed 170608576 + 100000 r): 2048 kr x 1024 theta polar "
+            "(M=2097152), kr x1.01, theta jitter 0.02 deg, 2000 speckle + 20 bright, N=1024, "
+            "sigma=2, w=8, exact FTCG weights")
+L2_NOTE = ("GPU arm: L2 flushed (a write of >= 2 x L2, at least 256 MiB) before every timed step; "
+           "warm_l2 repeats the step without the flush. CPU oracle arm: host memory, no flush")
+
+
+def headline_config(world):
+    """The workload's config, identical on both arms."""
+    return {"workload": WORKLOAD, "M": 2097152, "N": 1024, "sigma": 2.0, "w": 8, "G": 2048,
+            "l2": L2_NOTE,
+            "parallelism": ("1 GPU" if world == 1 else
+                            f"{world} GPUs, one independent ping per rank, no collective")}
+
+
+def rank_ping(rank):
+    import sasgen
+    return sasgen.large_ping(seed=sasgen.BASE_SEED + 1 + 100_000 * rank)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -53,6 +72,17 @@ def reduce_max(value, device=None):
     return float(t.item())
 
 
+def reduce_sum(value, device=None):
+    """Sum of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def barrier(device=None):
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -62,11 +92,30 @@ def barrier(device=None):
             dist.barrier()
 
 
-def shard(n_units, rank, world):
-    """Contiguous balanced split of n_units independent units: the [start, stop) of this rank."""
-    base, extra = divmod(n_units, world)
-    start = rank * base + min(rank, extra)
-    return start, start + base + (1 if rank < extra else 0)
+def shard_pings(costs, world):
+    """Split independent pings across ranks by work: greedy largest-first, each ping to the rank
+    with the least work so far (ties to the lower rank). costs[i] = M_i + G_i^2, the samples
+    spread plus the grid cells stored and transformed. Every rank computes the same split from
+    the same costs; returns one ascending index list per rank. As any such list schedule, the
+    largest rank load is at most the mean load plus one ping's cost."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        load[r] += costs[i]
+        parts[r].append(i)
+    return [sorted(p) for p in parts]
+
+
+def batch_costs(n_pings):
+    """costs of the uneven batch recipe's pings (sizes only, no raster is drawn)."""
+    import sasgen
+    out = []
+    for b in range(n_pings):
+        M, N = sasgen.batch_ping_size(b)
+        out.append(M + (2 * N) ** 2)
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -147,45 +196,143 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-# the CPU oracle leg
+# the CPU oracle leg: oracle/ftcg_oracle.py as it stands, on the host cores
 # ---------------------------------------------------------------------------------------------
-def oracle_adjoint_time(p, v, alpha, m=None, offset=0):
-    """Time the FP64 oracle (spread of m samples + inverse FFT + window division + crop).
-    Returns (seconds, m, t_spread, t_rest)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_spread_part(args):
+    """One worker's share of the oracle's spreading sum: the samples of one slice."""
+    lam, c, N, sigma, w = args
+    from oracle import ftcg_oracle as O
+    return O.spread(lam, c, N, sigma, w)
+
+
+def _pool_ready(_):
+    import numpy  # noqa: F401
+    from oracle import ftcg_oracle  # noqa: F401
+    return 0
+
+
+class OracleRunner:
+    """The FP64 oracle's adjoint (O.adjoint) with its spreading sum split over contiguous sample
+    slices in a spawned process pool (one process per core), the per-slice grids summed, then the
+    oracle's inverse FFT, crop and window division in this process. procs = 1 runs the oracle
+    unchanged in this process."""
+
+    def __init__(self, procs):
+        self.procs = max(1, int(procs))
+        self.pool = None
+        if self.procs > 1:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(self.procs)
+            self.pool.map(_pool_ready, range(self.procs))     # start-up outside any timing
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+    def spread(self, lam, c, N, sigma, w):
+        from oracle import ftcg_oracle as O
+        if self.pool is None:
+            return O.spread(lam, c, N, sigma, w)
+        M = lam.shape[0]
+        cuts = [M * k // self.procs for k in range(self.procs + 1)]
+        parts = [(lam[a:b], c[a:b], N, sigma, w) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        grids = self.pool.map(_oracle_spread_part, parts)
+        g = grids[0]
+        for x in grids[1:]:
+            g += x
+        return g
+
+    def adjoint(self, lam, c, N, sigma, w):
+        """(image, spread seconds, FFT + crop + window division seconds)."""
+        import numpy as np
+
+        from oracle import ftcg_oracle as O
+        t0 = time.perf_counter()
+        g = self.spread(lam, c, N, sigma, w)
+        t1 = time.perf_counter()
+        G = g.shape[0]
+        h = np.fft.ifft2(g) * (G * G)
+        q = np.mod(O.pixel_range(N), G)
+        r = O.deapod_factors(N, sigma, w)
+        img = h[np.ix_(q, q)] * r[:, None] * r[None, :]
+        t2 = time.perf_counter()
+        return img, t1 - t0, t2 - t1
+
+
+def oracle_rate(runner, lam, c, N, sigma, w, budget_s, min_m=4096):
+    """Samples/s of the oracle's adjoint on one raster. The whole raster when it fits the budget,
+    else a contiguous slice of m samples (acquisition order) charged m/M of one full-size inverse
+    FFT, crop and window division. Returns (value, description)."""
+    M = lam.shape[0]
+    _, ts, tr = runner.adjoint(lam[:min(M, min_m)], c[:min(M, min_m)], N, sigma, w)  # warm-up
+    m0 = min(M, max(min_m, M // 16))
+    _, ts0, tr = runner.adjoint(lam[:m0], c[:m0], N, sigma, w)
+    per_sample = ts0 / m0
+    if per_sample * M + tr <= budget_s:
+        _, ts, tr = runner.adjoint(lam, c, N, sigma, w)
+        return M / (ts + tr), f"the whole raster ({M} samples; spread {ts:.2f} s, FFT etc. {tr:.2f} s)"
+    m = int(min(M, max(m0, (budget_s - tr) / per_sample)))
+    _, ts, tr = runner.adjoint(lam[:m], c[:m], N, sigma, w)
+    sec = ts + tr * m / M
+    return m / sec, (f"the spread of the first {m} of {M} samples ({ts:.2f} s) + {m}/{M} of one "
+                     f"full-size inverse FFT, crop and window division ({tr:.2f} s per pass)")
+
+
+def cpu_baselines(p, v, alpha, budget_s=12.0, extra=True):
+    """The oracle as it stands on the host cores: one process, and one process per core, on the
+    large ping and (extra) on the tiny raster, the precision raster and 8 pings of the batch."""
     import numpy as np
 
-    from oracle import ftcg_oracle as O
-    M = p.M
-    m = M if m is None else m
-    sl = slice(offset, offset + m)
-    c = alpha[sl] * v[sl].astype(np.complex128)
-    t0 = time.perf_counter()
-    g = O.spread(p.lam[sl], c, p.N, p.sigma, p.w)
-    t1 = time.perf_counter()
-    G = g.shape[0]
-    h = np.fft.ifft2(g) * (G * G)
-    q = np.mod(O.pixel_range(p.N), G)
-    r = O.deapod_factors(p.N, p.sigma, p.w)
-    _ = h[np.ix_(q, q)] * r[:, None] * r[None, :]
-    t2 = time.perf_counter()
-    return t2 - t0, m, t1 - t0, t2 - t1
-
-
-def cpu_baseline(p, v, alpha, budget_s=20.0):
-    """The oracle as it stands on a bounded sample of the ping: the spread of a contiguous slice of
-    m samples (acquisition order) plus the FFT/deapodisation share m/M of one full-size pass."""
-    _, _, _, t_rest = oracle_adjoint_time(p, v, alpha, m=4096)
-    # calibrate the per-sample spread cost on 1/32 of the ping
-    m0 = p.M // 32
-    _, _, ts0, _ = oracle_adjoint_time(p, v, alpha, m=m0)
-    rate = m0 / ts0
-    m = int(min(p.M, max(m0, rate * budget_s)))
-    _, m, ts, _ = oracle_adjoint_time(p, v, alpha, m=m)
-    sec = ts + t_rest * m / p.M
-    return {"value": m / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"numpy FP64 oracle, 1 thread: spread of the first {m} of {p.M} samples "
-                      f"({ts:.1f} s) + {m}/{p.M} of one 2048^2 inverse FFT, window division and "
-                      f"crop ({t_rest:.2f} s per full pass)"}
+    import sasgen
+    cores = host_cores()
+    one, allc = OracleRunner(1), OracleRunner(cores)
+    out = {}
+    try:
+        c = alpha * v.astype(np.complex128)
+        v1, d1 = oracle_rate(one, p.lam, c, p.N, p.sigma, p.w, budget_s)
+        va, da = oracle_rate(allc, p.lam, c, p.N, p.sigma, p.w, 4 * budget_s)
+        out["large"] = {"one_core": {"value": v1, "sample": d1},
+                        "all_cores": {"value": va, "sample": da}}
+        if extra:
+            rng = np.random.default_rng(9)
+            tiny = sasgen.tiny()
+            ct = sasgen.values_for(tiny)
+            out["tiny"] = {k: {"value": r(tiny.lam, ct, tiny.N, tiny.sigma, tiny.w)[0]}
+                           for k, r in (("one_core", lambda *a: oracle_rate(one, *a, 2.0)),
+                                        ("all_cores", lambda *a: oracle_rate(allc, *a, 2.0)))}
+            ps = sasgen.precision_sweep()
+            cp = rng.standard_normal(ps.M) + 1j * rng.standard_normal(ps.M)
+            v1, d1 = oracle_rate(one, ps.lam, cp, ps.N, ps.sigma, ps.w, budget_s)
+            va, da = oracle_rate(allc, ps.lam, cp, ps.N, ps.sigma, ps.w, 4 * budget_s)
+            out["precision"] = {"one_core": {"value": v1, "sample": d1},
+                                "all_cores": {"value": va, "sample": da}}
+            pings = [sasgen.batch_ping(b) for b in range(8)]
+            tot = sum(q.M for q in pings)
+            for key, runner in (("one_core", one), ("all_cores", allc)):
+                t = 0.0
+                for q in pings:
+                    cq = rng.standard_normal(q.M) + 1j * rng.standard_normal(q.M)
+                    _, ts, tr = runner.adjoint(q.lam, cq, q.N, 2.0, 8)
+                    t += ts + tr
+                out.setdefault("batch_8_pings", {})[key] = {
+                    "value": tot / t, "sample": f"pings 0-7 of the batch recipe ({tot} samples), whole"}
+    finally:
+        one.close()
+        allc.close()
+    large = out["large"]
+    return {"value": large["all_cores"]["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "numpy FP64 oracle, one spawned process per core over sample slices: " +
+                      large["all_cores"]["sample"],
+            "one_core": dict(large["one_core"], cores=1), "configs": out}
 
 
 def run_reference(args):
@@ -195,38 +342,38 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    p = sasgen.large_ping()
-    v = sasgen.values_for(p).astype(np.complex64) if p.M <= 65536 else None
-    if v is None:
-        # values by the direct sum on the host are too slow at this size; the oracle's cost does
-        # not depend on the values, so a seeded stand-in of the same shape is used here
-        rng = np.random.default_rng(p.seed)
-        v = (rng.standard_normal(p.M) + 1j * rng.standard_normal(p.M)).astype(np.complex64)
-    alpha = np.ones(p.M)
-    _, _, _, t_rest = oracle_adjoint_time(p, v, alpha, m=4096)
-    m0 = p.M // 64
-    _, _, ts0, _ = oracle_adjoint_time(p, v, alpha, m=m0)
-    rate = m0 / ts0
-    per_step = min(6.0, 150.0 / max(1, args.steps + args.warmup))
-    m = int(max(4096, min(p.M, rate * max(0.05, per_step - t_rest * 0.0))))
-    m = min(m, p.M)
-    times = []
-    for i in range(args.warmup + args.steps):
-        off = (i * m) % max(1, p.M - m + 1)
-        _, mm, ts, _ = oracle_adjoint_time(p, v, alpha, m=m, offset=off)
-        if i >= args.warmup:
-            times.append(ts + t_rest * mm / p.M)
+    p = rank_ping(0)
+    # the oracle's cost does not depend on the values: a seeded stand-in of the same shape (the
+    # values by the direct sum on the host would take hours at this size)
+    rng = np.random.default_rng(p.seed)
+    c = rng.standard_normal(p.M) + 1j * rng.standard_normal(p.M)
+    cores = host_cores()
+    runner = OracleRunner(cores)
+    try:
+        # the whole ping per step when the run fits a few minutes, else a slice per step
+        _, ts0, tr = runner.adjoint(p.lam[:p.M // 16], c[:p.M // 16], p.N, p.sigma, p.w)
+        per_sample = ts0 / (p.M // 16)
+        per_step = max(0.2, 150.0 / max(1, args.steps + args.warmup))
+        m = int(min(p.M, max(p.M // 16, (per_step - tr) / per_sample)))
+        times = []
+        for i in range(args.warmup + args.steps):
+            off = (i * m) % max(1, p.M - m + 1)
+            _, ts, tr = runner.adjoint(p.lam[off:off + m], c[off:off + m], p.N, p.sigma, p.w)
+            if i >= args.warmup:
+                times.append(ts + tr * m / p.M)
+    finally:
+        runner.close()
     tot = sum(times)
     value = m * len(times) / tot
-    sample = (f"numpy FP64 oracle, 1 thread; each step spreads {m} of {p.M} samples of the ping "
-              f"and is charged {m}/{p.M} of one full 2048^2 inverse FFT + window division + crop "
-              f"({t_rest:.2f} s per pass)")
+    sample = (f"numpy FP64 oracle, {cores} spawned processes over sample slices; each step spreads "
+              f"{m} of the ping's {p.M} samples and is charged {m}/{p.M} of one full 2048^2 "
+              f"inverse FFT + crop + window division ({tr:.2f} s per pass)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "l2": "host"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": headline_config(args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -349,7 +496,9 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
 
 
 SPREAD_SOURCES = ["paper_1706_08575_gb300/csrc/spread_tile.cuh",
-                  "paper_1706_08575_gb300/csrc/spread.cu", "paper_1706_08575_gb300/csrc/plan.cu"]
+                  "paper_1706_08575_gb300/csrc/spread.cu", "paper_1706_08575_gb300/csrc/plan.cu",
+                  "paper_1706_08575_gb300/csrc/spread_mma.cuh",
+                  "paper_1706_08575_gb300/csrc/spread_mma.cu"]
 
 
 def spread_source_hash():
@@ -423,8 +572,6 @@ def precision_sweep_extra(device, reps=20):
     v = torch.randn(p.M, dtype=torch.complex64, device=device, generator=g)
     vb = torch.view_as_real(v).to(torch.bfloat16)
     flush = torch.empty(l2_flush_bytes(device) // 4, dtype=torch.float32, device=device)
-    rng = np.random.default_rng(3)
-    pix = np.concatenate([rng.integers(-p.N // 2, p.N // 2, size=(12, 2)), p.bright_pixels[:4]])
     out = {"workload": "precision raster: 2048 kr x 2048 theta (M=4194304), N=2048, sigma=2, w=8"}
     alpha = None
     for name, prec, vals in [("fp32", F.PREC_FP32, v), ("bf16", F.PREC_BF16, vb)]:
@@ -438,27 +585,36 @@ def precision_sweep_extra(device, reps=20):
                 pl.adjoint(vals, out=img)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(reps)]
+            pl.profile(True)
             for e0, e1 in ev:
                 flush.zero_()
                 e0.record()
                 pl.adjoint(vals, out=img)
                 e1.record()
             torch.cuda.synchronize()
+            (sp_ms, fft_ms, dp_ms), _ = pl.stage_times()
+            pl.profile(False)
             ms = statistics.median(a.elapsed_time(b) for a, b in ev)
-            got = img.cpu().numpy()
             inf = pl.info
+        G = inf.G
+        alg = (20 if name == "fp32" else 14) * p.M + 8 * G * G
+        peak, kind = load_peaks()
+        ach = alg / (sp_ms * 1e-3) / 1e9
         out[name] = {"value": p.M / (ms * 1e-3), "unit": UNIT, "ms_median": ms, "tile": inf.tile,
-                     "layout": inf.layout}
-    ref = O.adjoint_pixels(p.lam, alpha * v.cpu().numpy().astype(np.complex128), p.N, p.sigma,
-                           p.w, pix)
-    # both images against the same FP64 reference (inputs in FP64): the rounding of the stored
-    # values and weights is part of the BF16 error
+                     "layout": inf.layout, "stages_ms": {"spread": sp_ms, "fft": fft_ms,
+                                                         "deapod_crop": dp_ms},
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak, "peak_kind": kind,
+                                  "alg_bytes_per_launch": alg, "traffic": None,
+                                  "kernel": "spreading stage (spread + halo fix-up)"}}
+    # both whole images against the same FP64 reference (inputs in FP64): the rounding of the
+    # stored values and weights is part of the BF16 error
+    ref = O.adjoint(p.lam, alpha * v.cpu().numpy().astype(np.complex128), p.N, p.sigma, p.w)
     for name, prec, vals in [("fp32", F.PREC_FP32, v), ("bf16", F.PREC_BF16, vb)]:
         with F.Plan(lam, p.N, p.sigma, p.w, precision=prec) as pl:
             pl.set_weights(torch.from_numpy(alpha).to(device))
             got = pl.adjoint(vals).cpu().numpy()
-        out[name]["rel_l2_sampled_vs_fp64_oracle"] = O.rel_l2(
-            got[pix[:, 1] + p.N // 2, pix[:, 0] + p.N // 2], ref)
+        out[name]["rel_l2_vs_fp64_oracle"] = O.rel_l2(got, ref)
     return out
 
 
@@ -492,19 +648,25 @@ def tiny_extra(device, reps=50):
             "rel_l2_vs_direct_sum": O.rel_l2(got, ref)}
 
 
-def batch_full_extra(device, n_pings=512, reps=5):
+def batch_full_extra(device, n_pings=512, reps=5, rank=0, world=1):
     """The uneven batch recipe at full size (512 pings, 20k-400k samples, N in {256, 512, 1024}):
-    one batched plan, unit weights, random values; the adjoint replayed from a CUDA graph."""
+    one batched plan per rank over its share of the pings (shard_pings: split by M + G^2), unit
+    weights, random values; the adjoint replayed from a CUDA graph (the inputs, about 9.7 GB
+    per batch, are far larger than L2); the spreading stage's roofline from the batch's own stage
+    events on non-graph calls. With several ranks the time is the maximum over ranks and the
+    samples are those of all ranks."""
     import torch
     import sasgen
     import paper_1706_08575_gb300 as F
+    mine = shard_pings(batch_costs(n_pings), world)[rank]
     t0 = time.perf_counter()
-    pings = [sasgen.batch_ping(b) for b in range(n_pings)]
+    pings = [sasgen.batch_ping(b) for b in mine]
     lams = [torch.from_numpy(p.lam).to(device) for p in pings]
     g = torch.Generator(device=device)
-    g.manual_seed(13)
+    g.manual_seed(13 + rank)
     vals = [torch.randn(p.M, dtype=torch.complex64, device=device, generator=g) for p in pings]
-    M_tot = sum(p.M for p in pings)
+    M_mine = sum(p.M for p in pings)
+    alg = sum(20 * p.M + 8 * (2 * p.N) ** 2 for p in pings)
     t_gen = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -513,9 +675,15 @@ def batch_full_extra(device, n_pings=512, reps=5):
         t_plan = time.perf_counter() - t0
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
+            b.profile(True)
+            for _ in range(reps + 1):
+                b.adjoint(vals, stream=s)
+            (sp_ms, rest_ms), ncalls = b.stage_times()
+            b.profile(False)
             b.capture(vals)
             b.launch()
             s.synchronize()
+            barrier(device)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             for _ in range(reps):
@@ -523,8 +691,18 @@ def batch_full_extra(device, n_pings=512, reps=5):
             e1.record(s)
             s.synchronize()
             ms = e0.elapsed_time(e1) / reps
-    return {"pings": n_pings, "samples": M_tot, "plan_s": t_plan, "generate_s": t_gen,
-            "adjoint_graph": {"value": M_tot / (ms * 1e-3), "unit": UNIT, "ms": ms}}
+    ms_max = reduce_max(ms, device)
+    M_tot = int(round(reduce_sum(M_mine, device)))
+    peak, kind = load_peaks()
+    ach = alg / (sp_ms * 1e-3) / 1e9
+    return {"pings": n_pings, "ranks": world, "samples": M_tot, "plan_s": t_plan,
+            "generate_s": t_gen,
+            "adjoint_graph": {"value": M_tot / (ms_max * 1e-3), "unit": UNIT, "ms": ms_max},
+            "stages_ms_rank0": {"spread": sp_ms, "fft_deapod_crop": rest_ms, "calls": ncalls},
+            "roofline_rank0": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                               "frac": ach / peak, "peak_kind": kind, "alg_bytes_per_launch": alg,
+                               "traffic": None,
+                               "kernel": "spreading stage (persistent spread + halo fix-up)"}}
 
 
 def run_ours(args):
@@ -544,7 +722,7 @@ def run_ours(args):
     import paper_1706_08575_gb300 as F
     import sasgen
 
-    p = sasgen.large_ping()
+    p = rank_ping(rank)
     v_np = sasgen.values_for(p, device=device).astype(np.complex64)
     lam = torch.from_numpy(p.lam).to(device)
     vals = torch.from_numpy(v_np).to(device)
@@ -627,38 +805,44 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_max = reduce_max(statistics.median(e2e_t), device)
 
-    # parity of this very image against the oracle at sampled pixels (FP64, one by one)
+    # parity of this very image against the FP64 oracle, every pixel (O.adjoint on the same
+    # FP32-rounded weights and values)
     rel = None
     if rank == 0:
         from oracle import ftcg_oracle as O
         alpha = plan.weights().cpu().numpy()     # the plan's own weights, for the same product
         plan.adjoint(vals, out=img)
         got_img = img.cpu().numpy()
-        rng = np.random.default_rng(1)
-        pix = np.concatenate([rng.integers(-p.N // 2, p.N // 2, size=(8, 2)), p.bright_pixels])
-        ref = O.adjoint_pixels(p.lam, alpha.astype(np.float32) * v_np.astype(np.complex128), p.N,
-                               p.sigma, p.w, pix)
-        rel = O.rel_l2(got_img[pix[:, 1] + p.N // 2, pix[:, 0] + p.N // 2], ref)
+        ref = O.adjoint(p.lam, alpha.astype(np.float32) * v_np.astype(np.complex128), p.N,
+                        p.sigma, p.w)
+        rel = {"value": O.rel_l2(got_img, ref), "pixels": p.N * p.N,
+               "oracle": "O.adjoint (FP64 gridding, every pixel)"}
 
     info = plan.info
     G = info.G
+    tensor = plan.tensor_core()
     smem_fft = 256 <= G <= 4096 and (G & (G - 1)) == 0
     alg_bytes = 20 * p.M + 8 * G * G              # spreading: 20 B per sample + the grid write
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (sp_ms * 1e-3) / 1e9
     value = world * p.M * args.steps / total_max
 
+    more = {}
+    if not args.no_extras:
+        # every rank grids its share of the batch (the time is the maximum over ranks)
+        try:
+            more["batch_512_pings"] = batch_full_extra(device, rank=rank, world=world)
+        except Exception as e:
+            more["batch_512_pings"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         extras = None
-        more = {}
         if not args.no_extras:
             try:
                 extras = learned_vs_plain(device, large=(p, lam, vals),
                                           n_pings=args.extras_pings)
             except Exception as e:       # the headline line must still print
                 extras = {"error": f"{type(e).__name__}: {e}"}
-            for key, fn in [("precision_sweep", precision_sweep_extra),
-                            ("batch_512_pings", batch_full_extra), ("tiny", tiny_extra)]:
+            for key, fn in [("precision_sweep", precision_sweep_extra), ("tiny", tiny_extra)]:
                 try:
                     more[key] = fn(device)
                 except Exception as e:
@@ -666,27 +850,29 @@ def run_ours(args):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             alpha = plan.weights().cpu().numpy()
-            cpu = cpu_baseline(p, v_np, alpha, budget_s=args.cpu_budget)
+            cpu = cpu_baselines(p, v_np, alpha, budget_s=args.cpu_budget,
+                                extra=not args.no_extras)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "M": p.M, "N": p.N, "sigma": p.sigma, "w": p.w,
-                       "G": G, "tile": info.tile, "entries": info.entries,
-                       "l2": f"flushed ({flush_bytes / 2**20:.0f} MiB write, >= 2 x L2) before "
-                             "every timed step; warm_l2 repeats the step without the flush",
-                       "parallelism": f"replicas x{world}"},
+            "config": headline_config(world),
+            "plan": {"tile": info.tile, "layout": info.layout, "entries": info.entries,
+                     "spread_kernel": "tensor-core (k_spread_mma)" if tensor else
+                                      "register-window (k_spread)",
+                     "l2_flush_mib": flush_bytes / 2**20},
             "stages_ms": {"spread": sp_ms, "fft": fft_ms, "deapod_crop": dp_ms, "calls": ncalls,
                           "note": ("fft = column pass; deapod_crop = row pass fused with the "
                                    "window division and crop") if smem_fft else "cuFFT + k_deapod_crop"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(info.tile),
-                         "kernel": "k_spread (+ k_halo_add in the halo layout: the spreading stage)",
+                         "kernel": ("k_spread_mma" if tensor else "k_spread") +
+                                   " + k_halo_add (the spreading stage)",
                          "peak_kind": peak_kind,
                          "issue": recorded_issue(info.tile),
                          "alg_bytes_per_launch": alg_bytes},
-            "rel_l2_sampled_vs_fp64_oracle": rel,
+            "rel_l2_vs_fp64_oracle": rel,
             "per_ping": {"value": p.M / sum(pp), "unit": UNIT,
                          "plan_ms": 1e3 * pp[0], "weights_ms": 1e3 * pp[1],
                          "adjoint_ms": 1e3 * pp[2]},

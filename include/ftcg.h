@@ -66,6 +66,14 @@ enum { FTCG_PREC_FP32 = 0, FTCG_PREC_BF16 = 1 };
  *              a second kernel that adds them to the neighbouring tiles' cells.
  * AUTO lets the autotuner choose, together with the tile side. */
 enum { FTCG_LAYOUT_AUTO = 0, FTCG_LAYOUT_DUPLICATE = 1, FTCG_LAYOUT_HALO = 2 };
+/* Which spreading kernel a plan uses (same result within the FP32 bound):
+ *   AUTO:   the tensor-core kernel where it applies (halo layout, w <= 8 and a window whose
+ *           per-tap degree-7 polynomials are within 1e-6 of it: w >= 7 for any sigma >= 1.25,
+ *           w = 6 at sigma = 2), otherwise the register-window kernel.
+ *   WINDOW: the register-window kernel (FP32 multiply-adds into a rolling window of rows).
+ *   TENSOR: the tensor-core kernel (per column bin, 8 samples x a 16-row window per
+ *           mma.sync.m16n8k8 in split TF32); NOT_SUPPORTED where it does not apply. */
+enum { FTCG_SPREAD_AUTO = 0, FTCG_SPREAD_WINDOW = 1, FTCG_SPREAD_TENSOR = 2 };
 
 typedef struct {
     int32_t kernel;        /* 0 = ES (the only window of this build)                            */
@@ -73,7 +81,8 @@ typedef struct {
     int32_t tile;          /* fine-grid tile side of the spreading kernel: 0 = auto, 32 or 64 */
     int32_t weight_width;  /* window width of the FP64 weight construction: 0 = 12, else 4..16 */
     int32_t layout;        /* FTCG_LAYOUT_AUTO (default), _DUPLICATE or _HALO                  */
-    int32_t reserved[3];   /* must be zero                                                      */
+    int32_t spread_kernel; /* FTCG_SPREAD_AUTO (default), _WINDOW or _TENSOR                    */
+    int32_t reserved[2];   /* must be zero                                                      */
 } ftcg_opts_t;
 
 typedef struct {
@@ -84,6 +93,9 @@ typedef struct {
     int64_t entries;       /* sorted (tile, sample) entries                                     */
     double beta;           /* window shape parameter                                            */
     int64_t device_bytes;  /* device memory the plan holds                                      */
+    int32_t spread_kernel; /* FTCG_SPREAD_WINDOW or FTCG_SPREAD_TENSOR: the kernel the plan uses */
+    int32_t pad0;
+    int64_t chunks;        /* tensor-core chunks of 8 sample slots (0 for the other kernel)     */
 } ftcg_plan_info_t;
 
 /*
@@ -245,6 +257,16 @@ ftcg_status_t ftcg_batch_launch(ftcg_batch_t batch, ftcg_stream_t stream);
 ftcg_status_t ftcg_batch_info(ftcg_batch_t batch, int32_t* tiles, int64_t* entries,
                               int64_t* device_bytes);
 ftcg_status_t ftcg_batch_destroy(ftcg_batch_t batch);
+/*
+ * Stage profiling of a batch, as ftcg_profile for a plan: with enable != 0 every later
+ * ftcg_adjoint_batch (not the captured graph) records CUDA events on its stream around its two
+ * stages; ftcg_batch_stage_times synchronises on the last one and returns the mean milliseconds
+ * of ms[0] = spreading (the persistent launches and the halo fix-up) and ms[1] = the inverse
+ * FFTs with window division and crop, over the calls recorded since the previous read (count in
+ * *calls; at most 256 between reads).
+ */
+ftcg_status_t ftcg_batch_profile(ftcg_batch_t batch, int32_t enable);
+ftcg_status_t ftcg_batch_stage_times(ftcg_batch_t batch, float* ms, int32_t* calls);
 
 /*
  * Learned weights. A small MLP predicts each sample's FTCG weight (Eq. difopt at r = 1) from its
@@ -321,8 +343,10 @@ ftcg_status_t ftcg_mlp_destroy(ftcg_mlp_t mlp);
  *   N, sigma, w as in ftcg_plan, with the grid side G = sigma N limited to 512: larger sizes
  *             return FTCG_ERR_NOT_SUPPORTED before any work is queued.
  * Scratch lives in fixed device arrays inside the library (about 4 MiB per GPU that loads it,
- * held until the process exits). The first call on a device looks up their addresses (it must
- * come before any stream capture on that device). Every call reuses the same arrays, so calls
+ * held until the process exits). The first call on a device looks up their addresses and loads
+ * this entry point's kernels (it must come before any stream capture on that device). The
+ * addresses are kept for the life of the process: after cudaDeviceReset on that device the
+ * entry point must not be called again. Every call reuses the same arrays, so calls
  * that overlap on the GPU (different streams or unordered threads) race; calls on one stream are
  * safe. Samples with non-finite coordinates are skipped. Asynchronous on `stream`.
  */

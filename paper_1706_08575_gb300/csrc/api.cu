@@ -80,6 +80,11 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
     FTCG_TRY(split_factors(p->deapod, p->deapod2, p->N, s));
     FTCG_TRY(build_binning(p->bin, p->lambda, M, p->sigma, p->G, p->opts.tile, p->w,
                            p->opts.layout == FTCG_LAYOUT_HALO, p->status, p->samp, s, &bytes));
+    if (p->bin.halo && p->opts.spread_kernel != FTCG_SPREAD_WINDOW && p->w <= kMmaMaxW) {
+        double err = 0;
+        if (mma_window_poly(p->w, p->win.beta, &p->bin.poly, &err))
+            FTCG_TRY(build_chunks(p->bin, s, &bytes));
+    }
     if (own_grid) {
         FTCG_CK(pool_malloc(&p->grid, (size_t)p->G * p->G * sizeof(float2), s));
         bytes += (int64_t)p->G * p->G * sizeof(float2);
@@ -110,10 +115,23 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
         return invalid("ftcg_plan: sigma * N must be an even integer");
     if (G < 2 * w) return invalid("ftcg_plan: the grid must hold at least two windows (G >= 2 w)");
     ftcg_opts_t& o = *po;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i] != 0) return invalid("ftcg_plan: opts.reserved must be zero");
     if (o.layout < FTCG_LAYOUT_AUTO || o.layout > FTCG_LAYOUT_HALO)
         return invalid("ftcg_plan: opts.layout must be 0, 1 or 2");
+    if (o.spread_kernel < FTCG_SPREAD_AUTO || o.spread_kernel > FTCG_SPREAD_TENSOR)
+        return invalid("ftcg_plan: opts.spread_kernel must be 0, 1 or 2");
+    if (o.spread_kernel == FTCG_SPREAD_TENSOR) {
+        MmaPoly poly;
+        double err = 0;
+        if (o.layout == FTCG_LAYOUT_DUPLICATE || w > kMmaMaxW ||
+            !mma_window_poly(w, es_beta(w, sigma), &poly, &err)) {
+            set_error("ftcg_plan: the tensor-core spreading kernel needs the halo layout, w <= 8 "
+                      "and a window within 1e-6 of its tap polynomials (w = %d, sigma = %g: %.1e)",
+                      w, sigma, err);
+            return FTCG_ERR_NOT_SUPPORTED;
+        }
+    }
     if (o.kernel != 0) {
         set_error("ftcg_plan: only the ES window (kernel 0) is built");
         return FTCG_ERR_NOT_SUPPORTED;
@@ -256,6 +274,9 @@ ftcg_status_t ftcg_plan_info(ftcg_plan_t plan, ftcg_plan_info_t* info) {
     info->entries = p->bin.n_entries;
     info->beta = p->win.beta;
     info->device_bytes = p->device_bytes;
+    info->spread_kernel = p->bin.mma ? FTCG_SPREAD_TENSOR : FTCG_SPREAD_WINDOW;
+    info->pad0 = 0;
+    info->chunks = p->bin.n_chunks;
     return FTCG_SUCCESS;
     FTCG_API_END
 }

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "fft_smem.cuh"
+#include "spread_mma.cuh"
 #include "spread_tile.cuh"
 
 namespace ftcg {
@@ -42,7 +43,36 @@ struct PingDesc {
     int G, ntx, T, N;
     int halo, halo_cells, ncb, W;
     int fused;                   // 1: the row pass writes the image (no k_deapod_batch)
+    // tensor-core spreading (halo layout, w <= 8): the ping's chunks
+    const MmaEntry* cent;
+    const uint32_t* chdr;
+    const int* tile_chunk;
 };
+
+// The persistent tensor-core spreading launch: CTAs take (ping, tile) items of pings planned
+// for the tensor-core kernel from an atomic counter, heaviest first.
+template <bool VBF, bool ABF>
+__global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
+    k_spread_batch_mma(const PingDesc* __restrict__ desc, const int2* __restrict__ items,
+                       int nitems, int* __restrict__ counter, const __grid_constant__ MmaPoly poly) {
+    extern __shared__ float smem[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();   // the previous item's tile is stored and s_item consumed
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) return;
+        const int2 pt = items[it];
+        const PingDesc d = desc[pt.x];
+        if (d.T == 64)
+            mma::spread_tile<64, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
+                                           d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
+        else
+            mma::spread_tile<32, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
+                                           d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
+    }
+}
 
 template <int GW, int WT, bool VBF, bool ABF, int CPL>
 __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
@@ -128,13 +158,15 @@ size_t spread_smem() {
 // ---- autotuner ----------------------------------------------------------------------------
 struct TuneKey {
     int G, w, prec, bucket, tile, layout;   // tile / layout: the caller's fixed choices (0 = free)
+    int skern;                              // the caller's spreading-kernel choice
     bool operator<(const TuneKey& o) const {
         if (G != o.G) return G < o.G;
         if (w != o.w) return w < o.w;
         if (prec != o.prec) return prec < o.prec;
         if (bucket != o.bucket) return bucket < o.bucket;
         if (tile != o.tile) return tile < o.tile;
-        return layout < o.layout;
+        if (layout != o.layout) return layout < o.layout;
+        return skern < o.skern;
     }
 };
 std::mutex g_tune_mu;
@@ -158,20 +190,33 @@ bool json_int(const std::string& line, const char* key, int* out) {
     return true;
 }
 
+// Device memory and events released on every return path.
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 // Time the spreading kernel of a plan (values are irrelevant to the cost: zeros).
 ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaStream_t s,
                           float* ms) {
-    cudaEvent_t a, b;
-    FTCG_CK(cudaEventCreate(&a));
-    FTCG_CK(cudaEventCreate(&b));
+    EventPair ev;
+    FTCG_CK(cudaEventCreate(&ev.a));
+    FTCG_CK(cudaEventCreate(&ev.b));
     FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s));   // warm-up
-    FTCG_CK(cudaEventRecord(a, s));
+    FTCG_CK(cudaEventRecord(ev.a, s));
     for (int r = 0; r < 3; ++r) FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s));
-    FTCG_CK(cudaEventRecord(b, s));
-    FTCG_CK(cudaEventSynchronize(b));
-    FTCG_CK(cudaEventElapsedTime(ms, a, b));
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    FTCG_CK(cudaEventRecord(ev.b, s));
+    FTCG_CK(cudaEventSynchronize(ev.b));
+    FTCG_CK(cudaEventElapsedTime(ms, ev.a, ev.b));
     return FTCG_SUCCESS;
 }
 
@@ -180,7 +225,8 @@ ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaSt
 ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
                         const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out) {
     const int G = (int)std::llround(sigma * N);
-    const TuneKey key{G, w, opts.precision, density_bucket(M, G), opts.tile, opts.layout};
+    const TuneKey key{G, w, opts.precision, density_bucket(M, G), opts.tile, opts.layout,
+                      opts.spread_kernel};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -193,17 +239,19 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
     std::vector<int> tiles, layouts;
     if (opts.tile) tiles.push_back(opts.tile); else tiles = {32, 64};
     if (opts.layout) layouts.push_back(opts.layout);
+    else if (opts.spread_kernel == FTCG_SPREAD_TENSOR) layouts.push_back(FTCG_LAYOUT_HALO);
     else layouts = {FTCG_LAYOUT_DUPLICATE, FTCG_LAYOUT_HALO};
     if (tiles.size() * layouts.size() == 1) {
         *T_out = tiles[0];
         *layout_out = layouts[0];
         return FTCG_SUCCESS;
     }
-    void* zeros = nullptr;
-    float2* grid = nullptr;
-    FTCG_CK(cudaMalloc(&zeros, (size_t)std::max<int64_t>(M, 1) * sizeof(float2)));
-    FTCG_CK(cudaMemsetAsync(zeros, 0, (size_t)std::max<int64_t>(M, 1) * sizeof(float2), s));
-    FTCG_CK(cudaMalloc(&grid, (size_t)G * G * sizeof(float2)));
+    DevBuf zbuf, gbuf;
+    FTCG_CK(cudaMalloc(&zbuf.p, (size_t)std::max<int64_t>(M, 1) * sizeof(float2)));
+    FTCG_CK(cudaMemsetAsync(zbuf.p, 0, (size_t)std::max<int64_t>(M, 1) * sizeof(float2), s));
+    FTCG_CK(cudaMalloc(&gbuf.p, (size_t)G * G * sizeof(float2)));
+    const void* zeros = zbuf.p;
+    float2* grid = reinterpret_cast<float2*>(gbuf.p);
     int best_T = tiles[0], best_L = layouts[0];
     float best_ms = 1e30f;
     ftcg_status_t st = FTCG_SUCCESS;
@@ -230,8 +278,6 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
         }
         if (st != FTCG_SUCCESS) break;
     }
-    cudaFree(zeros);
-    cudaFree(grid);
     if (st != FTCG_SUCCESS) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -266,9 +312,12 @@ struct Batch {
     std::vector<int> cls_of, slot_of;
     PingDesc* h_desc = nullptr;   // pinned
     PingDesc* d_desc = nullptr;
+    // (ping, tile) work items: the n_mma items of tensor-core pings first, then the others
     int2* d_items = nullptr;
-    int nitems = 0;
-    int* d_counter = nullptr;
+    int nitems = 0, n_mma = 0;
+    int* d_counter = nullptr;     // two counters: tensor-core items, register-window items
+    MmaPoly poly{};               // the window polynomials (every ping has the same w, sigma)
+    int persistent_ctas_mma = 0;
     unsigned* d_masks = nullptr;  // shared-memory FFT column-block masks of all pings
     int max_N = 0;
     bool any_halo = false;
@@ -276,7 +325,12 @@ struct Batch {
     int64_t entries = 0, device_bytes = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t last = nullptr;
+    // stage profiling of ftcg_adjoint_batch: 3 events per recorded call
+    bool profiling = false;
+    int prof_calls = 0;
+    std::vector<cudaEvent_t> prof_ev;
 };
+constexpr int kBatchProfiled = 256;
 
 void release_batch(Batch* b) {
     if (!b) return;
@@ -295,6 +349,7 @@ void release_batch(Batch* b) {
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_masks) cudaFree(b->d_masks);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
     delete b;
 }
 
@@ -315,8 +370,28 @@ ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
     }
     const float beta = (float)es_beta(b.w, b.sigma);
     const float inv_hw = (float)(2.0 / b.w);
-    kern<<<b.persistent_ctas, tile::kSpreadThreads, smem, s>>>(b.d_desc, b.d_items, b.nitems,
-                                                                b.d_counter, b.w, beta, inv_hw);
+    kern<<<b.persistent_ctas, tile::kSpreadThreads, smem, s>>>(
+        b.d_desc, b.d_items + b.n_mma, b.nitems - b.n_mma, b.d_counter + 1, b.w, beta, inv_hw);
+    FTCG_CK(cudaGetLastError());
+    return FTCG_SUCCESS;
+}
+
+template <bool VBF, bool ABF>
+ftcg_status_t launch_batch_spread_mma(Batch& b, cudaStream_t s) {
+    auto kern = k_spread_batch_mma<VBF, ABF>;
+    const size_t smem = mma::tile_smem_bytes(64);
+    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
+    if (b.persistent_ctas_mma == 0) {
+        int dev = 0, sms = 0, per = 0;
+        FTCG_CK(cudaGetDevice(&dev));
+        FTCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FTCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, mma::kThreads, smem));
+        b.persistent_ctas_mma = std::max(1, sms * std::max(1, per));
+    }
+    kern<<<b.persistent_ctas_mma, mma::kThreads, smem, s>>>(b.d_desc, b.d_items, b.n_mma,
+                                                            b.d_counter, b.poly);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
 }
@@ -377,17 +452,28 @@ std::vector<float2> class_twiddles(int G) {
     }
 }
 
+// profile: record the stage events of a profiled batch (not while a graph is being captured)
 ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, void* const* imgs,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool profile = false) {
     for (int i = 0; i < b.n; ++i) {
         b.h_desc[i].vals = vals[i];
         b.h_desc[i].img = reinterpret_cast<float2*>(imgs[i]);
     }
     FTCG_CK(cudaMemcpyAsync(b.d_desc, b.h_desc, b.n * sizeof(PingDesc), cudaMemcpyHostToDevice, s));
-    FTCG_CK(cudaMemsetAsync(b.d_counter, 0, sizeof(int), s));
+    FTCG_CK(cudaMemsetAsync(b.d_counter, 0, 2 * sizeof(int), s));
+    cudaEvent_t* ev = nullptr;
+    if (profile && b.profiling && b.prof_calls < kBatchProfiled)
+        ev = b.prof_ev.data() + 3 * b.prof_calls++;
+    if (ev) FTCG_CK(cudaEventRecord(ev[0], s));
     const bool vbf = vdtype == FTCG_VALUES_BF16X2;
     const bool abf = b.opts.precision == FTCG_PREC_BF16;
-    if (b.nitems > 0) {
+    if (b.n_mma > 0) {
+        if (vbf && abf) FTCG_TRY((launch_batch_spread_mma<true, true>(b, s)));
+        else if (vbf) FTCG_TRY((launch_batch_spread_mma<true, false>(b, s)));
+        else if (abf) FTCG_TRY((launch_batch_spread_mma<false, true>(b, s)));
+        else FTCG_TRY((launch_batch_spread_mma<false, false>(b, s)));
+    }
+    if (b.nitems > b.n_mma) {
         if (vbf && abf) FTCG_TRY((launch_batch_spread_w<true, true>(b, s)));
         else if (vbf) FTCG_TRY((launch_batch_spread_w<true, false>(b, s)));
         else if (abf) FTCG_TRY((launch_batch_spread_w<false, true>(b, s)));
@@ -397,6 +483,7 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
         k_halo_add_batch<<<b.nitems, 256, 0, s>>>(b.d_desc, b.d_items);
         FTCG_CK(cudaGetLastError());
     }
+    if (ev) FTCG_CK(cudaEventRecord(ev[1], s));
     bool any_cufft = false;
     for (auto& c : b.classes) {
         if (c.smem) {
@@ -408,11 +495,13 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
         FTCG_CKFFT(cufftExecC2C(c.fft, reinterpret_cast<cufftComplex*>(c.grids),
                                 reinterpret_cast<cufftComplex*>(c.grids), CUFFT_INVERSE));
     }
-    if (!any_cufft) return FTCG_SUCCESS;
-    const dim3 blocks((b.max_N + 2 * kDeapodThreads - 1) / (2 * kDeapodThreads),
-                      (b.max_N + kDeapodRows - 1) / kDeapodRows, b.n);
-    k_deapod_batch<<<blocks, kDeapodThreads, 0, s>>>(b.d_desc);
-    FTCG_CK(cudaGetLastError());
+    if (any_cufft) {
+        const dim3 blocks((b.max_N + 2 * kDeapodThreads - 1) / (2 * kDeapodThreads),
+                          (b.max_N + kDeapodRows - 1) / kDeapodRows, b.n);
+        k_deapod_batch<<<blocks, kDeapodThreads, 0, s>>>(b.d_desc);
+        FTCG_CK(cudaGetLastError());
+    }
+    if (ev) FTCG_CK(cudaEventRecord(ev[2], s));
     return FTCG_SUCCESS;
 }
 
@@ -549,7 +638,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
     struct Item {
         int cnt, ping, tile;
     };
-    std::vector<Item> items;
+    std::vector<Item> items, items_mma;
     for (int i = 0; i < b.n; ++i) {
         Plan* p = b.pings[i];
         const Binning& bn = p->bin;
@@ -572,15 +661,28 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         d.W = bn.W;
         d.col_mask = nullptr;
         d.fused = c.smem ? 1 : 0;
+        d.cent = bn.cent;
+        d.chdr = bn.chdr;
+        d.tile_chunk = bn.tile_chunk;
+        if (bn.mma) b.poly = bn.poly;
         b.any_halo = b.any_halo || bn.halo;
-        if ((int)bn.tile_cnt.size() == bn.ntiles) {
-            for (int t = 0; t < bn.ntiles; ++t) items.push_back({bn.tile_cnt[t], i, t});
+        std::vector<Item>& list = bn.mma ? items_mma : items;
+        if (c.smem && bn.n_read > 0 && (int)bn.tile_cnt.size() == bn.ntiles &&
+            (int)bn.h_order.size() == bn.ntiles) {
+            // the shared-memory transforms read only the column blocks that taps reach: the
+            // tiles of the pruned launch order (non-empty ones, then empty ones in those columns)
+            for (int k = 0; k < bn.n_read; ++k) {
+                const int t = bn.h_order[k];
+                list.push_back({bn.tile_cnt[t], i, t});
+            }
+        } else if ((int)bn.tile_cnt.size() == bn.ntiles) {
+            for (int t = 0; t < bn.ntiles; ++t) list.push_back({bn.tile_cnt[t], i, t});
         } else {
             std::vector<int> cp((size_t)bn.ntiles * bn.ncb + 1);
             FTCG_CK(cudaMemcpy(cp.data(), bn.colptr, cp.size() * sizeof(int),
                                cudaMemcpyDeviceToHost));
             for (int t = 0; t < bn.ntiles; ++t)
-                items.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t});
+                list.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t});
         }
     }
     // shared-memory FFT classes: per ping the column blocks that taps reach (items of the column
@@ -635,15 +737,19 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
                                     col_items[ci].size() * sizeof(int2) +
                                     cls_pings[ci].size() * sizeof(int));
     }
-    std::stable_sort(items.begin(), items.end(),
-                     [](const Item& x, const Item& y) { return x.cnt > y.cnt; });
-    b.nitems = (int)items.size();
-    std::vector<int2> it2(items.size());
-    for (size_t k = 0; k < items.size(); ++k) it2[k] = make_int2(items[k].ping, items[k].tile);
+    auto heavy_first = [](const Item& x, const Item& y) { return x.cnt > y.cnt; };
+    std::stable_sort(items.begin(), items.end(), heavy_first);
+    std::stable_sort(items_mma.begin(), items_mma.end(), heavy_first);
+    b.n_mma = (int)items_mma.size();
+    b.nitems = (int)(items_mma.size() + items.size());
+    std::vector<int2> it2;
+    it2.reserve(b.nitems);
+    for (const Item& x : items_mma) it2.push_back(make_int2(x.ping, x.tile));
+    for (const Item& x : items) it2.push_back(make_int2(x.ping, x.tile));
     FTCG_CK(cudaMalloc(&b.d_items, std::max<size_t>(1, it2.size()) * sizeof(int2)));
     if (!it2.empty())
         FTCG_CK(cudaMemcpy(b.d_items, it2.data(), it2.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    FTCG_CK(cudaMalloc(&b.d_counter, sizeof(int)));
+    FTCG_CK(cudaMalloc(&b.d_counter, 2 * sizeof(int)));
     b.device_bytes += (int64_t)(it2.size() * sizeof(int2) + b.n * sizeof(PingDesc));
     return FTCG_SUCCESS;
 }
@@ -781,7 +887,61 @@ ftcg_status_t ftcg_adjoint_batch(ftcg_batch_t batch, const void* const* d_values
         }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     b->last = s;
-    return batch_enqueue(*b, d_values, vdtype, d_images, s);
+    return batch_enqueue(*b, d_values, vdtype, d_images, s, true);
+    FTCG_API_END
+}
+
+ftcg_status_t ftcg_batch_profile(ftcg_batch_t batch, int32_t enable) {
+    FTCG_API_BEGIN
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_batch_profile: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    if (enable && b->prof_ev.empty()) {
+        b->prof_ev.reserve(3 * kBatchProfiled);
+        for (int i = 0; i < 3 * kBatchProfiled; ++i) {
+            cudaEvent_t e = nullptr;
+            cudaError_t ce = cudaEventCreate(&e);
+            if (ce != cudaSuccess) {
+                for (cudaEvent_t x : b->prof_ev) cudaEventDestroy(x);
+                b->prof_ev.clear();
+                set_error("ftcg_batch_profile: cudaEventCreate: %s", cudaGetErrorString(ce));
+                return FTCG_ERR_CUDA;
+            }
+            b->prof_ev.push_back(e);
+        }
+    }
+    b->profiling = enable != 0;
+    b->prof_calls = 0;
+    return FTCG_SUCCESS;
+    FTCG_API_END
+}
+
+ftcg_status_t ftcg_batch_stage_times(ftcg_batch_t batch, float* ms, int32_t* calls) {
+    FTCG_API_BEGIN
+    clear_error();
+    if (!batch || !ms) {
+        set_error("ftcg_batch_stage_times: NULL argument");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    const int n = b->prof_calls;
+    ms[0] = ms[1] = 0.f;
+    if (calls) *calls = n;
+    if (n == 0) return FTCG_SUCCESS;
+    FTCG_CK(cudaEventSynchronize(b->prof_ev[3 * (n - 1) + 2]));
+    double acc[2] = {0, 0};
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 2; ++k) {
+            float t = 0.f;
+            FTCG_CK(cudaEventElapsedTime(&t, b->prof_ev[3 * i + k], b->prof_ev[3 * i + k + 1]));
+            acc[k] += t;
+        }
+    for (int k = 0; k < 2; ++k) ms[k] = (float)(acc[k] / n);
+    b->prof_calls = 0;
+    return FTCG_SUCCESS;
     FTCG_API_END
 }
 
@@ -888,9 +1048,10 @@ ftcg_status_t ftcg_tuner_save(const char* path) {
     for (const auto& e : snap) {
         std::fprintf(f,
                      "{\"G\": %d, \"w\": %d, \"precision\": %d, \"bucket\": %d, "
-                     "\"tile_req\": %d, \"layout_req\": %d, \"tile\": %d, \"layout\": %d}%s\n",
+                     "\"tile_req\": %d, \"layout_req\": %d, \"spread_req\": %d, "
+                     "\"tile\": %d, \"layout\": %d}%s\n",
                      e.first.G, e.first.w, e.first.prec, e.first.bucket, e.first.tile,
-                     e.first.layout, e.second.first, e.second.second,
+                     e.first.layout, e.first.skern, e.second.first, e.second.second,
                      ++k < snap.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
@@ -927,6 +1088,7 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
         if (line.find("\"G\":") == std::string::npos) continue;
         TuneKey k{};
         int tile = 0, layout = 0;
+        if (!json_int(line, "spread_req", &k.skern)) k.skern = FTCG_SPREAD_AUTO;   // older files
         const bool ok = json_int(line, "G", &k.G) && json_int(line, "w", &k.w) &&
                         json_int(line, "precision", &k.prec) &&
                         json_int(line, "bucket", &k.bucket) &&
@@ -937,6 +1099,8 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
                            (k.prec == FTCG_PREC_FP32 || k.prec == FTCG_PREC_BF16) &&
                            (k.tile == 0 || k.tile == 32 || k.tile == 64) &&
                            (k.layout >= FTCG_LAYOUT_AUTO && k.layout <= FTCG_LAYOUT_HALO) &&
+                           (k.skern >= FTCG_SPREAD_AUTO && k.skern <= FTCG_SPREAD_TENSOR) &&
+                           (k.skern != FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
                            (tile == 32 || tile == 64) &&
                            (layout == FTCG_LAYOUT_DUPLICATE || layout == FTCG_LAYOUT_HALO) &&
                            (k.tile == 0 || k.tile == tile) && (k.layout == 0 || k.layout == layout);

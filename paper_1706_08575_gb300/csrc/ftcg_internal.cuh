@@ -90,6 +90,27 @@ struct __align__(16) Entry {
     uint32_t packed;
 };
 
+// One slot of a tensor-core spreading chunk (spread_mma.cu): 16 bytes, one vector load.
+//   sx, sy : first-tap offsets relative to the centre of the tap's unit interval,
+//            s = d - (w/2 - 1/2) in (-1/2, 1/2]  (float32; the window's tap polynomials take s)
+//   alpha  : per-sample weight (same storage as Entry::alpha)
+//   packed : sample index | (first-tap row - chunk window row, 0..8) << 25 | padding flag << 31
+struct __align__(16) MmaEntry {
+    float sx, sy;
+    uint32_t alpha;
+    uint32_t packed;
+};
+constexpr uint32_t kMmaPad = 1u << 31;
+constexpr int kMmaChunk = 8;          // samples per chunk (the k extent of one m16n8k8 product)
+constexpr int kMmaMaxW = 8;           // widest window of the tensor-core path
+constexpr int kMmaDeg = 7;            // degree of the per-tap window polynomials
+
+// The window on tap l's unit interval as a polynomial in s (see MmaEntry), coefficients of
+// s^0..s^7 for taps l = 0..7; taps l >= w are zero.
+struct MmaPoly {
+    float c[kMmaMaxW][kMmaDeg + 1];
+};
+
 // The window: ES kernel parameters for one (w, sigma).
 struct Window {
     int w;
@@ -148,6 +169,14 @@ struct Binning {
     bool halo = false;                  // FTCG_LAYOUT_HALO: one entry per sample + halo strips
     int halo_cells = 0;                 // halo cells per tile
     float2* halo_buf = nullptr;         // ntiles * halo_cells overflow values (halo layout)
+    // Tensor-core spreading (halo layout, w <= 8): each tile's entries regrouped into chunks of 8
+    // samples of one column bin whose first-tap rows fit one 16-row window (spread_mma.cu).
+    bool mma = false;
+    int64_t n_chunks = 0;
+    MmaEntry* cent = nullptr;           // n_chunks * 8 slots, tile by tile (padding slots flagged)
+    uint32_t* chdr = nullptr;           // per chunk: first-tap column | window row << 8
+    int* tile_chunk = nullptr;          // ntiles + 1 chunk offsets
+    MmaPoly poly{};
 };
 
 struct Plan {
@@ -213,6 +242,16 @@ ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStr
 ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2* grid,
                             cudaStream_t s, bool pruned = false);
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s);
+// spread_mma.cu: the tensor-core spreading path (halo layout, w <= 8)
+// fit the per-tap window polynomials; returns false if their error exceeds the path's bound
+bool mma_window_poly(int W, double beta, MmaPoly* out, double* max_err);
+ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes);
+void free_chunks(Binning& b);
+ftcg_status_t launch_spread_mma(const Plan& p, const void* vals, bool vbf, float2* grid,
+                                cudaStream_t s, int nt);
+ftcg_status_t launch_set_alpha_mma(const Plan& p, const void* alpha, int dtype, cudaStream_t s);
+// launch a plan's k_halo_add fix-up after a halo-layout spreading kernel (spread.cu)
+ftcg_status_t launch_halo_add(const Plan& p, float2* grid, cudaStream_t s);
 // occ[x] = 1 for every grid column x that some sample's taps reach
 ftcg_status_t column_occupancy(const Plan* p, cudaStream_t s, std::vector<unsigned char>* occ);
 ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes);

@@ -610,14 +610,16 @@ __global__ void k_reduce_parts(const float* __restrict__ part, int nblk, int64_t
     out[i] = acc;
 }
 
+// ob1 = 1 - b1 and ob2 = 1 - b2 are formed in FP64 by the caller: 1.f - 0.999f in FP32 is
+// 1.3e-5 away from 0.001.
 __global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, int n, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+                       float ob1, float ob2, float eps, float c1, float c2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + ob1 * gi;
+    const float vi = b2 * v[i] + ob2 * (gi * gi);
     m[i] = mi;
     v[i] = vi;
     P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -1034,11 +1036,12 @@ ftcg_status_t ftcg_mlp_train_step(ftcg_mlp_t mlp, const void* d_features, const 
     FTCG_TRY(batch_grads(q, reinterpret_cast<const __nv_bfloat16*>(d_features), d_target, d_index,
                          B, s));
     q->step += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - (float)std::pow(0.9, (double)q->step);
-    const float c2 = 1.f - (float)std::pow(0.999, (double)q->step);
-    k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(q->P, q->m, q->v, q->grad, kParams, lr, b1, b2,
-                                                 1e-8f, c1, c2);
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - std::pow(b1, (double)q->step));
+    const float c2 = (float)(1.0 - std::pow(b2, (double)q->step));
+    k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(q->P, q->m, q->v, q->grad, kParams, lr,
+                                                 (float)b1, (float)b2, (float)(1.0 - b1),
+                                                 (float)(1.0 - b2), 1e-8f, c1, c2);
     FTCG_CK(cudaGetLastError());
     if (h_loss) {
         FTCG_CK(cudaMemcpyAsync(h_loss, q->loss, sizeof(float), cudaMemcpyDeviceToHost, s));

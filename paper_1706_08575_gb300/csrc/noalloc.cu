@@ -44,6 +44,7 @@ struct NaPtrs {
     float2* grid;
     float2* rows;
     double* deapod;
+    int sms;          // multiprocessors of the device (sizes the grid-stride spreading launch)
     bool ready;
 };
 NaPtrs g_na[kNaMaxDevices];
@@ -241,6 +242,15 @@ extern "C" ftcg_status_t ftcg_adjoint_small_noalloc(const double* d_lambda, cons
             FTCG_CK(cudaGetSymbolAddress(reinterpret_cast<void**>(&p.grid), na_grid));
             FTCG_CK(cudaGetSymbolAddress(reinterpret_cast<void**>(&p.rows), na_rows));
             FTCG_CK(cudaGetSymbolAddress(reinterpret_cast<void**>(&p.deapod), na_deapod));
+            FTCG_CK(cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev));
+            // load every kernel of this entry point now (with lazy module loading a kernel is
+            // otherwise loaded at its first launch, which a later captured call could be)
+            cudaFuncAttributes fa;
+            FTCG_CK(cudaFuncGetAttributes(&fa, k_na_deapod));
+            FTCG_CK(cudaFuncGetAttributes(&fa, k_na_zero));
+            FTCG_CK(cudaFuncGetAttributes(&fa, k_na_spread));
+            FTCG_CK(cudaFuncGetAttributes(&fa, k_na_rows));
+            FTCG_CK(cudaFuncGetAttributes(&fa, k_na_cols));
             p.ready = true;
             g_na[dev] = p;
         }
@@ -255,7 +265,7 @@ extern "C" ftcg_status_t ftcg_adjoint_small_noalloc(const double* d_lambda, cons
     k_na_zero<<<256, 256, 0, s>>>(ptrs.grid, Gi * Gi);
     if (M > 0) {
         int64_t blocks = (M * 16 + 255) / 256;
-        if (blocks > 152 * 16) blocks = 152 * 16;
+        if (blocks > (int64_t)ptrs.sms * 16) blocks = (int64_t)ptrs.sms * 16;
         k_na_spread<<<(unsigned)blocks, 256, 0, s>>>(
             d_lambda, reinterpret_cast<const float2*>(d_values), d_alpha, M, sigma, Gi, w,
             (float)beta, (float)(2.0 / w), ptrs.grid);

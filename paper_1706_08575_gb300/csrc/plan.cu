@@ -250,6 +250,7 @@ ftcg_status_t exclusive_scan_i32(const int* d_in, int* d_out, int64_t n, cudaStr
 }
 
 void free_binning(Binning& b) {
+    free_chunks(b);
     if (b.ent) cudaFree(b.ent);
     if (b.colptr) cudaFree(b.colptr);
     if (b.tile_order) cudaFree(b.tile_order);

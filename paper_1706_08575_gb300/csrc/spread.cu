@@ -63,11 +63,7 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
                                                 b.ntx, b.W, beta, inv_hw, b.halo_buf,
                                                 b.halo_cells);
     FTCG_CK(cudaGetLastError());
-    if (HALO && b.n_nonempty > 0) {
-        FTCG_CK(launch_pdl(k_halo_add, dim3(b.n_nonempty), dim3(256), 0, s,
-                           (const float2*)b.halo_buf, b.halo_cells, (const int*)b.colptr,
-                           (const int*)b.tile_order, b.ncb, grid, b.G, b.T, b.W, b.ntx));
-    }
+    if (HALO) return launch_halo_add(p, grid, s);
     return FTCG_SUCCESS;
 }
 
@@ -183,6 +179,15 @@ int blocks_for(int64_t n, int threads) {
 
 }  // namespace
 
+ftcg_status_t launch_halo_add(const Plan& p, float2* grid, cudaStream_t s) {
+    const Binning& b = p.bin;
+    if (!b.halo || b.n_nonempty == 0) return FTCG_SUCCESS;
+    FTCG_CK(launch_pdl(k_halo_add, dim3(b.n_nonempty), dim3(256), 0, s,
+                       (const float2*)b.halo_buf, b.halo_cells, (const int*)b.colptr,
+                       (const int*)b.tile_order, b.ncb, grid, b.G, b.T, b.W, b.ntx));
+    return FTCG_SUCCESS;
+}
+
 ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2* grid,
                             cudaStream_t s, bool pruned) {
     if (p.bin.n_entries == 0) {
@@ -192,6 +197,7 @@ ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2*
     // the pruned transform reads only the tiles in the first n_read of the launch order
     const int nt = pruned && p.bin.n_read > 0 ? p.bin.n_read : p.bin.ntiles;
     const bool vbf = vdtype == FTCG_VALUES_BF16X2;
+    if (p.bin.mma) return launch_spread_mma(p, vals, vbf, grid, s, nt);
     const bool abf = p.opts.precision == FTCG_PREC_BF16;
     if (vbf && abf) return dispatch_t<true, true>(p, vals, grid, s, nt);
     if (vbf) return dispatch_t<true, false>(p, vals, grid, s, nt);
@@ -236,7 +242,7 @@ ftcg_status_t launch_set_alpha(const Plan& p, const void* alpha, int dtype, cuda
     k_set_alpha<<<blocks_for(p.bin.n_entries, 256), 256, 0, s>>>(
         p.bin.ent, p.bin.n_entries, alpha, dtype, p.opts.precision == FTCG_PREC_BF16);
     FTCG_CK(cudaGetLastError());
-    return FTCG_SUCCESS;
+    return launch_set_alpha_mma(p, alpha, dtype, s);
 }
 
 }  // namespace ftcg

@@ -68,6 +68,53 @@ __host__ __device__ constexpr size_t tile_smem_bytes() {
            (size_t)(T + WMAX + 1) * sizeof(int);
 }
 
+// Store a finished tile from its shared accumulator planes (row stride LD): the tile's own
+// Tw x Th cells to the grid, coalesced (every cell written once), and in the halo layout the
+// overflow strips to the tile's slots of the halo buffer: right strip (rows 0..Th+w-2, columns
+// Tw..Tw+w-2), then bottom strip (rows Th..Th+w-2, columns 0..Tw-1); the slot layout is fixed
+// by T so that k_halo_add can decode it. Called by every thread of the CTA after a barrier.
+template <bool HALO, int NT>
+__device__ __forceinline__ void store_tile(const float* __restrict__ s_re,
+                                           const float* __restrict__ s_im, int LD,
+                                           float2* __restrict__ grid, int G, int X0, int Y0,
+                                           int Tw, int Th, int T, int W, float2* __restrict__ hb,
+                                           int halo_cells) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int y = warp; y < Th; y += NT / 32) {
+        float2* dst = grid + (int64_t)(Y0 + y) * G + X0;
+        for (int x = lane; x < Tw; x += 32) dst[x] = make_float2(s_re[y * LD + x], s_im[y * LD + x]);
+    }
+    if (HALO) {
+        const int right = (T + W - 1) * (W - 1);
+        for (int k = threadIdx.x; k < halo_cells; k += NT) {
+            int y, x;
+            if (k < right) {
+                y = k / (W - 1);
+                x = Tw + (k - y * (W - 1));
+                if (y >= Th + W - 1) continue;
+            } else {
+                const int kk = k - right;
+                y = Th + kk / T;
+                x = kk - (kk / T) * T;
+                if (x >= Tw) continue;
+            }
+            hb[k] = make_float2(s_re[y * LD + x], s_im[y * LD + x]);
+        }
+    }
+}
+
+// Store zeros over an empty tile's own cells (its halo strips are never read: k_halo_add skips
+// empty tiles).
+template <int NT>
+__device__ __forceinline__ void store_zero_tile(float2* __restrict__ grid, int G, int X0, int Y0,
+                                                int Tw, int Th) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int y = warp; y < Th; y += NT / 32) {
+        float2* dst = grid + (int64_t)(Y0 + y) * G + X0;
+        for (int x = lane; x < Tw; x += 32) dst[x] = make_float2(0.f, 0.f);
+    }
+}
+
 // One tile, by the whole CTA. GW: lanes per group (power of two); CPL: tap columns per lane
 // (lane l owns columns l, l + GW, ..., so GW * CPL >= w); WT: compile-time w (0 = runtime
 // w <= GW * CPL). HALO: the tile's entries are the samples whose first tap lies in it; the
@@ -97,11 +144,7 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
 
     if (colptr[(int64_t)tile * ncb] == colptr[(int64_t)(tile + 1) * ncb]) {
         // an empty tile (common under a polar footprint): store zeros, no accumulator, no halo
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int y = warp; y < Th; y += kSpreadThreads / 32) {
-            float2* dst = grid + (int64_t)(Y0 + y) * G + X0;
-            for (int x = lane; x < Tw; x += 32) dst[x] = make_float2(0.f, 0.f);
-        }
+        store_zero_tile<kSpreadThreads>(grid, G, X0, Y0, Tw, Th);
         return;
     }
     for (int i = threadIdx.x; i < 2 * PT * LD; i += kSpreadThreads) smem[i] = 0.0f;
@@ -236,32 +279,8 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
         flush_all();                              // only groups that held a window flush it
     }
     __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int y = warp; y < Th; y += kSpreadThreads / 32) {
-        float2* dst = grid + (int64_t)(Y0 + y) * G + X0;
-        for (int x = lane; x < Tw; x += 32) dst[x] = make_float2(s_re[y * LD + x], s_im[y * LD + x]);
-    }
-    if (HALO && e1 > e0) {
-        // overflow strips: right (rows 0..Th+w-2, columns Tw..Tw+w-2), bottom (rows Th..Th+w-2,
-        // columns 0..Tw-1); slot layout fixed by T so that k_halo_add can decode it
-        float2* hb = halo_buf + (int64_t)tile * halo_cells;
-        const int right = (T + W - 1) * (W - 1);
-        for (int k = threadIdx.x; k < halo_cells; k += kSpreadThreads) {
-            int y, x;
-            if (k < right) {
-                y = k / (W - 1);
-                x = Tw + (k - y * (W - 1));
-                if (y >= Th + W - 1) continue;
-            } else {
-                const int kk = k - right;
-                y = Th + kk / T;
-                x = kk - (kk / T) * T;
-                if (x >= Tw) continue;
-            }
-            hb[k] = make_float2(s_re[y * LD + x], s_im[y * LD + x]);
-        }
-    }
+    store_tile<HALO, kSpreadThreads>(s_re, s_im, LD, grid, G, X0, Y0, Tw, Th, T, W,
+                                     halo_buf + (int64_t)tile * halo_cells, halo_cells);
 }
 
 // Adds the overflow strips of a halo-layout tile to the grid cells they belong to (wrapping mod

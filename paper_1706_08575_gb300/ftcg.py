@@ -30,19 +30,22 @@ class FtcgError(RuntimeError):
 
 
 LAYOUT_AUTO, LAYOUT_DUPLICATE, LAYOUT_HALO = 0, 1, 2
+SPREAD_AUTO, SPREAD_WINDOW, SPREAD_TENSOR = 0, 1, 2
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("weight_width", ctypes.c_int32),
-                ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("layout", ctypes.c_int32), ("spread_kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int32), ("G", ctypes.c_int32),
                 ("w", ctypes.c_int32), ("tile", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("entries", ctypes.c_int64), ("beta", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("spread_kernel", ctypes.c_int32),
+                ("pad0", ctypes.c_int32), ("chunks", ctypes.c_int64)]
 
 
 _lib = None
@@ -71,6 +74,8 @@ SIGNATURES = [
     ("ftcg_batch_launch", _I32, [_VP, _VP]),
     ("ftcg_batch_info", _I32, [_VP, _VP, _VP, _VP]),
     ("ftcg_batch_destroy", _I32, [_VP]),
+    ("ftcg_batch_profile", _I32, [_VP, _I32]),
+    ("ftcg_batch_stage_times", _I32, [_VP, _VP, _VP]),
     ("ftcg_features", _I32, [_VP, _VP, _I64, _VP, _VP, _VP]),
     ("ftcg_features_batch", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ftcg_tuner_save", _I32, [ctypes.c_char_p]),
@@ -138,14 +143,14 @@ class Plan:
     """A binned geometry: ftcg_plan on lam (torch float64, M x 2, CUDA)."""
 
     def __init__(self, lam, N, sigma=2.0, w=8, tile=0, precision=PREC_FP32, weight_width=0,
-                 stream=None, allow_numeric=False, layout=LAYOUT_AUTO):
+                 stream=None, allow_numeric=False, layout=LAYOUT_AUTO, spread_kernel=SPREAD_AUTO):
         import torch
         if lam.dtype != torch.float64 or lam.dim() != 2 or lam.shape[1] != 2 or not lam.is_cuda:
             raise TypeError("lam must be a CUDA float64 tensor of shape (M, 2)")
         lam = lam.contiguous()
         self.M, self.N, self.sigma, self.w = int(lam.shape[0]), int(N), float(sigma), int(w)
         self.device = lam.device
-        opts = Opts(0, precision, tile, weight_width, layout)
+        opts = Opts(0, precision, tile, weight_width, layout, spread_kernel)
         h = ctypes.c_void_p()
         st = lib().ftcg_plan(ctypes.byref(h), _ptr(lam), self.M, self.N, self.sigma, self.w,
                              ctypes.byref(opts), _stream(stream))
@@ -162,6 +167,10 @@ class Plan:
         info = PlanInfo()
         _check(lib().ftcg_plan_info(self._h, ctypes.byref(info)))
         return info
+
+    def tensor_core(self):
+        """True when the plan spreads with the tensor-core kernel."""
+        return self.info.spread_kernel == SPREAD_TENSOR
 
     def close(self):
         if getattr(self, "_h", None):
@@ -266,7 +275,7 @@ class Batch:
     """Many pings gridded together: ftcg_plan_batch on a list of (M_i, 2) float64 CUDA tensors."""
 
     def __init__(self, lams, Ns, sigma=2.0, w=8, tile=0, precision=PREC_FP32, stream=None,
-                 layout=LAYOUT_AUTO):
+                 layout=LAYOUT_AUTO, spread_kernel=SPREAD_AUTO):
         import torch
         self.n = len(lams)
         self.lams = [l.contiguous() for l in lams]
@@ -278,7 +287,7 @@ class Batch:
         self.device = self.lams[0].device
         M_arr = (ctypes.c_int64 * self.n)(*self.Ms)
         N_arr = (ctypes.c_int32 * self.n)(*self.Ns)
-        opts = Opts(0, precision, tile, 0, layout)
+        opts = Opts(0, precision, tile, 0, layout, spread_kernel)
         h = ctypes.c_void_p()
         st = lib().ftcg_plan_batch(ctypes.byref(h), self.n, _ptr_array(self.lams), M_arr, N_arr,
                                    float(sigma), int(w), ctypes.byref(opts), _stream(stream))
@@ -350,6 +359,18 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib().ftcg_batch_launch(self._h, _stream(stream)))
+
+    def profile(self, enable=True):
+        _check(lib().ftcg_batch_profile(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        """Mean (spread, fft + window division + crop) milliseconds of the ftcg_adjoint_batch
+        calls since the last read, and their count."""
+        ms = (ctypes.c_float * 2)()
+        n = ctypes.c_int32()
+        _check(lib().ftcg_batch_stage_times(self._h, ctypes.cast(ms, ctypes.c_void_p),
+                                            ctypes.byref(n)))
+        return tuple(ms), n.value
 
 
 def tuner_save(path):

@@ -157,18 +157,30 @@ def precision_sweep(seed=BASE_SEED + 2):
     return p
 
 
-def batch_ping(b, seed_base=BASE_SEED + 3):
-    """Ping b of the uneven batch: M ~ U{20k..400k}, span ~ U[5, 20] deg, kr x (1+e) with
-    e ~ U[-2%, 2%], angle jitter N(0, 0.02 deg), N ~ {256, 512, 1024}; 500 speckle + 5 bright;
-    sigma = 2, w = 8; the FOV is sized so that the lambda span fills 90% of N."""
-    seed = seed_base + 1000 * b
-    rng = np.random.default_rng(seed)
+def _batch_ping_draws(rng):
+    """The first draws of a batch ping: (n_kr, n_theta, span, kr error, N)."""
     M = int(rng.integers(20_000, 400_001))
     span = float(rng.uniform(5.0, 20.0))
     e = float(rng.uniform(-0.02, 0.02))
     N = int(rng.choice([256, 512, 1024]))
     n_th = max(2, int(round(math.sqrt(M / 2))))
     n_kr = max(2, int(round(M / n_th)))
+    return n_kr, n_th, span, e, N
+
+
+def batch_ping_size(b, seed_base=BASE_SEED + 3):
+    """(M, N) of batch ping b without drawing its raster (the same draws as batch_ping)."""
+    n_kr, n_th, _, _, N = _batch_ping_draws(np.random.default_rng(seed_base + 1000 * b))
+    return n_kr * n_th, N
+
+
+def batch_ping(b, seed_base=BASE_SEED + 3):
+    """Ping b of the uneven batch: M ~ U{20k..400k}, span ~ U[5, 20] deg, kr x (1+e) with
+    e ~ U[-2%, 2%], angle jitter N(0, 0.02 deg), N ~ {256, 512, 1024}; 500 speckle + 5 bright;
+    sigma = 2, w = 8; the FOV is sized so that the lambda span fills 90% of N."""
+    seed = seed_base + 1000 * b
+    rng = np.random.default_rng(seed)
+    n_kr, n_th, span, e, N = _batch_ping_draws(rng)
     kx, ky = polar_raster(rng, n_kr, n_th, span, kr_scale=1 + e, theta_jitter_deg=0.02)
     kspan = max(kx.max() - kx.min(), ky.max() - ky.min())
     L = 0.9 * 2 * np.pi * N / kspan

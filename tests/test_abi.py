@@ -71,8 +71,9 @@ def test_plan_rejects_opts(L):
     assert _plan(L, opts=ftcg.Opts(0, 0, 48, 0)) == 1                # tile
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 3)) == 1                 # weight width
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 3)) == 1              # layout
+    assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 0, 3)) == 1           # spreading kernel
     o = ftcg.Opts(0, 0, 0, 0)
-    o.reserved[2] = 1
+    o.reserved[1] = 1
     assert _plan(L, opts=o) == 1
 
 
@@ -125,7 +126,9 @@ def test_tuner_file_round_trip(L, tmp_path):
     entries = [{"G": 2048, "w": 8, "precision": 0, "bucket": -3, "tile_req": 0, "layout_req": 0,
                 "tile": 32, "layout": 2},
                {"G": 512, "w": 6, "precision": 1, "bucket": 1, "tile_req": 64, "layout_req": 0,
-                "tile": 64, "layout": 1}]
+                "tile": 64, "layout": 1},
+               {"G": 1024, "w": 8, "precision": 0, "bucket": -1, "tile_req": 0, "layout_req": 0,
+                "spread_req": 2, "tile": 64, "layout": 2}]
     src = tmp_path / "tuner.json"
     src.write_text('{"ftcg_tuner": 1, "entries": [\n' +
                    ",\n".join(json.dumps(e) for e in entries) + "\n]}\n")
@@ -134,13 +137,16 @@ def test_tuner_file_round_trip(L, tmp_path):
     ftcg.tuner_save(out)
     saved = json.loads(out.read_text())
     assert saved["ftcg_tuner"] == 1
-    for e in entries:
-        assert e in saved["entries"]
+    for e in entries:               # files written before the spreading-kernel choice load as 0
+        assert dict(e, spread_req=e.get("spread_req", 0)) in saved["entries"]
     bad = tmp_path / "bad.json"
     bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[0], G=1000, tile=48))
                    + "\n]}\n")
     assert L.ftcg_tuner_load(str(bad).encode()) == 1
     assert b"line 2" in L.ftcg_last_error()
+    bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[2], layout=1))
+                   + "\n]}\n")          # the tensor-core kernel needs the halo layout
+    assert L.ftcg_tuner_load(str(bad).encode()) == 1
     other = tmp_path / "other.json"
     other.write_text(json.dumps({"entries": [dict(entries[0], G=4096)]}) + "\n")
     assert L.ftcg_tuner_load(str(other).encode()) == 1

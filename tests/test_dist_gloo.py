@@ -25,8 +25,9 @@ def _worker(rank, world, port, out):
         r, w, lr = bench.dist_env()
         m = bench.reduce_max(1.5 + rank)
         bench.barrier()
-        spans = [bench.shard(513, k, w) for k in range(w)]
-        out.put((rank, r, w, lr, m, spans[rank], spans))
+        costs = bench.batch_costs(512)
+        parts = bench.shard_pings(costs, w)
+        out.put((rank, r, w, lr, m, parts[rank], parts, costs))
     finally:
         dist.destroy_process_group()
 
@@ -43,19 +44,37 @@ def test_two_rank_reduction_and_shard():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    res.sort()
-    for rank, r, w, lr, m, mine, spans in res:
+    res.sort(key=lambda x: x[0])
+    mine = []
+    for rank, r, w, lr, m, part, parts, costs in res:
         assert (r, w, lr) == (rank, 2, rank)
         assert m == pytest.approx(2.5)
-        assert spans[0][0] == 0 and spans[-1][1] == 513
-        assert spans[0][1] == spans[1][0]
-        assert abs((spans[0][1] - spans[0][0]) - (spans[1][1] - spans[1][0])) <= 1
+        assert parts == res[0][6]                   # both ranks computed the same split
+        mine.append(part)
+    # every ping of the 512-ping batch is gridded exactly once, by one rank
+    assert sorted(mine[0] + mine[1]) == list(range(512))
+    costs = res[0][7]
+    loads = [sum(costs[i] for i in p) for p in mine]
+    assert max(loads) - sum(costs) / 2 <= max(costs)
 
 
-def test_shard_covers_all_units():
+def test_shard_pings_balance():
+    """Coverage and balance of the work split for several world sizes, including more ranks
+    than pings: the largest rank load is within one ping of the ideal share (and of the lower
+    bound max(mean load, largest ping))."""
+    import random
+
     import bench
-    for n in (0, 1, 7, 512):
+    rnd = random.Random(3)
+    for n in (0, 1, 7, 64, 512):
+        costs = [rnd.randint(20_000, 400_000) + rnd.choice([512, 1024, 2048]) ** 2
+                 for _ in range(n)]
         for world in (1, 2, 3, 8):
-            spans = [bench.shard(n, r, world) for r in range(world)]
-            covered = [i for a, b in spans for i in range(a, b)]
-            assert covered == list(range(n))
+            parts = bench.shard_pings(costs, world)
+            assert len(parts) == world
+            assert sorted(i for p in parts for i in p) == list(range(n))
+            if n:
+                loads = [sum(costs[i] for i in p) for p in parts]
+                lower = max(sum(costs) / world, max(costs))
+                assert max(loads) <= lower + max(costs)
+                assert max(loads) <= sum(costs) / world + max(costs)

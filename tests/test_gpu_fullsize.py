@@ -93,3 +93,76 @@ def test_precision_sweep_fp32_sampled(F):
     ref = O.adjoint_pixels(p.lam, v.astype(np.complex128), p.N, p.sigma, p.w, pix)
     got = img[pix[:, 1] + p.N // 2, pix[:, 0] + p.N // 2]
     assert O.rel_l2(got, ref) < TOL
+
+
+# ---- whole images at full size, element by element against the FP64 gridding oracle ------------
+
+def test_large_ping_whole_image(F, large):
+    """The benchmark's ping and launch configuration (default plan: autotuned tile and kernel),
+    seeded weights: every one of the 1,048,576 pixels against O.adjoint."""
+    p, v = large
+    alpha = np.random.default_rng(15).uniform(0.5, 1.5, p.M)
+    with F.Plan(dev(p.lam), p.N, p.sigma, p.w) as pl:
+        pl.set_weights(dev(alpha))
+        img = pl.adjoint(dev(v)).cpu().numpy()
+        pl.check()
+    ref = O.adjoint(p.lam, alpha.astype(np.float32) * v.astype(np.complex128), p.N, p.sigma, p.w)
+    assert O.rel_l2(img, ref) < TOL
+
+
+@pytest.fixture(scope="module")
+def precision(F):
+    p = sasgen.precision_sweep()
+    v = sasgen.values_for(p, device="cuda").astype(np.complex64)
+    alpha = np.random.default_rng(16).uniform(0.5, 1.5, p.M)
+    return p, v, alpha
+
+
+def test_precision_sweep_whole_image_fp32(F, precision):
+    p, v, alpha = precision
+    with F.Plan(dev(p.lam), p.N, p.sigma, p.w) as pl:
+        pl.set_weights(dev(alpha))
+        img = pl.adjoint(dev(v)).cpu().numpy()
+    ref = O.adjoint(p.lam, alpha.astype(np.float32) * v.astype(np.complex128), p.N, p.sigma, p.w)
+    assert O.rel_l2(img, ref) < TOL
+
+
+def test_precision_sweep_whole_image_bf16(F, precision):
+    """BF16 storage at full size: parity (1e-5) against the oracle on the same bf16-rounded values
+    and weights, and the precision bound (5e-3) against the unrounded FP64 inputs."""
+    import torch
+    p, v, alpha = precision
+    vb = torch.view_as_real(torch.from_numpy(v)).to(torch.bfloat16)
+    with F.Plan(dev(p.lam), p.N, p.sigma, p.w, precision=F.PREC_BF16) as pl:
+        pl.set_weights(dev(alpha))
+        img = pl.adjoint(vb.cuda()).cpu().numpy()
+    vr = vb.to(torch.float64).numpy()
+    vr = vr[:, 0] + 1j * vr[:, 1]
+    ar = torch.from_numpy(alpha.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert O.rel_l2(img, O.adjoint(p.lam, ar * vr, p.N, p.sigma, p.w)) < TOL
+    e = O.rel_l2(img, O.adjoint(p.lam, alpha * v.astype(np.complex128), p.N, p.sigma, p.w))
+    assert e < 5e-3, e
+
+
+def test_batch_pings_whole_images(F):
+    """Four full-size pings of the uneven batch recipe with image sides 256, 512 and 1024 in one
+    batched plan (persistent spreading launch, per-size-class transforms), each whole image
+    against O.adjoint."""
+    picks = []
+    b = 0
+    while len(picks) < 4:
+        q = sasgen.batch_ping(b)
+        if q.N not in [x.N for x in picks] or len(picks) == 3:
+            picks.append(q)
+        b += 1
+    assert len({q.N for q in picks}) >= 3
+    rng = np.random.default_rng(17)
+    vals = [(rng.standard_normal(q.M) + 1j * rng.standard_normal(q.M)).astype(np.complex64)
+            for q in picks]
+    alphas = [rng.uniform(0.5, 1.5, q.M) for q in picks]
+    with F.Batch([dev(q.lam) for q in picks], [q.N for q in picks], 2.0, 8) as bt:
+        bt.set_weights([dev(a) for a in alphas])
+        imgs = [i.cpu().numpy() for i in bt.adjoint([dev(x) for x in vals])]
+    for q, x, a, img in zip(picks, vals, alphas, imgs):
+        ref = O.adjoint(q.lam, a.astype(np.float32) * x.astype(np.complex128), q.N, 2.0, 8)
+        assert O.rel_l2(img, ref) < TOL, q.N

@@ -162,6 +162,58 @@ def test_checkpoint_continuation_is_bitwise(F):
     assert np.array_equal(sa["params"], sb["params"]) and sa["step"] == sb["step"] == 5
 
 
+def test_adam_steps_vs_oracle(F):
+    """Two device Adam steps (ftcg_mlp_train_step, bias corrections at t = 1 and t = 2) against
+    mlp_oracle.adam_step given the same gradients (ftcg_mlp_grads at the same parameters and
+    batch: the device reductions have a fixed order, so train_step sees these very gradients)
+    and the device's own moments before the step.
+
+    Bound, with u = 2^-24 (FP32 unit roundoff): the new moments m = b1 m + (1 - b1) g and
+    v = b2 v + (1 - b2) g^2 take at most three rounded operations on constants held within
+    u/2 of their FP64 values, so |m - m_ref| <= 4u (|b1 m| + |(1-b1) g|), and one more for g^2
+    in v (5u). The update d = lr (m / c1) / (sqrt(v / c2) + eps) adds the divisions by the bias
+    corrections, the square root, the addition of eps, the division and the scaling by lr
+    (<= 8u, the square root halving the error of v): |d - d_ref| <= 16u |d_ref|. The new
+    parameter is rounded once more: |P - P_ref| <= u |P_ref| + 16u |d_ref|. The test allows
+    twice these."""
+    import torch
+    rng = np.random.default_rng(9)
+    flat = L.pack(L.init_params(rng)).astype(np.float32)
+    B = 700
+    X = rng.standard_normal((B, 48)).astype(np.float32)
+    X[:, L.D_IN:] = 0
+    Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    t = dev(rng.standard_normal(B) * 0.5)
+    idx = torch.from_numpy(rng.permutation(B).astype(np.int32)).cuda()
+    lr, u = 3e-3, 2.0 ** -24
+    mlp = F.Mlp(flat)
+    st = mlp.state()
+    for step in (1, 2):
+        g, _ = mlp.grads(Xt, t, idx)
+        mlp.train_step(Xt, t, idx, lr)
+        new = mlp.state()
+        assert new["step"] == step
+        P = L.unpack(st["params"])
+        G = L.unpack(g)
+        state = {"t": step - 1}
+        m_old, v_old = L.unpack(st["m"]), L.unpack(st["v"])
+        for k, _ in L.ORDER:
+            state["m_" + k] = m_old[k].copy()
+            state["v_" + k] = v_old[k].copy()
+        ref = L.adam_step({k: P[k].copy() for k, _ in L.ORDER}, G, state, lr=lr)
+        Pn, mn, vn = L.unpack(new["params"]), L.unpack(new["m"]), L.unpack(new["v"])
+        for k, _ in L.ORDER:
+            bm = 4 * u * (0.9 * np.abs(m_old[k]) + 0.1 * np.abs(G[k]))
+            bv = 5 * u * (0.999 * np.abs(v_old[k]) + 0.001 * G[k] ** 2)
+            assert np.all(np.abs(mn[k] - state["m_" + k]) <= 2 * bm + 1e-38), k
+            assert np.all(np.abs(vn[k] - state["v_" + k]) <= 2 * bv + 1e-38), k
+            d = P[k] - ref[k]
+            bp = u * np.abs(ref[k]) + 16 * u * np.abs(d)
+            assert np.all(np.abs(Pn[k] - ref[k]) <= 2 * bp + 1e-38), k
+        st = new
+    mlp.close()
+
+
 def test_trained_network_gain(F, tmp_path):
     """Train on exact weights of random jittered polar geometries, then grid a held-out ping with
     the predicted weights: its image is closer to the exact-weight oracle image than the

@@ -73,3 +73,18 @@ def test_noalloc_rejects_large_grid(F):
     out = torch.empty((512, 512), dtype=torch.complex64, device="cuda")
     assert _noalloc(F, lam, v, None, 512, 2.0, 8, out) == 4      # G = 1024 > 512
     assert b"exceeds" in F.lib().ftcg_last_error()
+
+
+def test_noalloc_at_the_size_limit(F):
+    """G = sigma N = 512, the largest grid the fixed scratch holds (N = 256, sigma = 2)."""
+    import torch
+    lam_np, v_np = sasgen.random_case(61, 20000, 256, 2.0, 8, 256)
+    lam = torch.from_numpy(lam_np).cuda()
+    v = torch.from_numpy(v_np.astype(np.complex64)).cuda()
+    with F.Plan(lam, 256, 2.0, 8) as plan:
+        ref = plan.adjoint(v).cpu().numpy()
+    out = torch.empty((256, 256), dtype=torch.complex64, device="cuda")
+    assert _noalloc(F, lam, v, None, 256, 2.0, 8, out) == 0
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), ref) < TOL
+
