@@ -354,6 +354,49 @@ ftcg_status_t ftcg_adjoint_small_noalloc(const double* d_lambda, const void* d_v
                                          const double* d_alpha, int64_t M, int32_t N, double sigma,
                                          int32_t w, void* d_image, ftcg_stream_t stream);
 
+/*
+ * ftcg_band -- the banded FTCG coefficient matrix C for band r >= 1 (Sec. III-C, Eq. ftcg and
+ * Eq. cr; C_2 of Eq. twodftcg), read as the banded least-squares problem
+ *     C = argmin || T C - I ||_F over C with C_jk = 0 for |j - k| > r - 1 (acquisition order),
+ * T_jk = Dx(lambda_k - lambda_j) Dy(lambda_k - lambda_j) the data-frame Gram matrix on the N x N
+ * pixel lattice (D the Dirichlet kernel N^-1 sum_p exp(2 pi i d p / N)). Column k solves the
+ * normal equations (T^2)[S_k, S_k] c = T[S_k, k] over its 2r - 1 band rows S_k (clipped at the
+ * ends) in FP64 on the device. r = 1 gives the diagonal weights of ftcg_weights; a band covering
+ * every index gives T^+ (Eq. dif3) and the frame approximation (Eq. insert).
+ * The coefficients are installed in the plan: later ftcg_adjoint calls form tau = C v (complex64
+ * values only) and spread tau with unit weights (ftcg_weights / ftcg_set_weights remove the
+ * band again). d_coef_out: NULL or device M x (2r - 1) complex128, row k holding column k of C at
+ * rows k - r + 1 .. k + r - 1 (zero outside 0..M-1).
+ * Limits: 1 <= r <= 12; M <= 8192 (the construction costs O(M^2 r) FP64 work and 16 M^2 bytes
+ * of temporary device memory), NOT_SUPPORTED above; FP32 plans only. Synchronises.
+ * Errors: NUMERIC if some column's band system is not positive definite (rank-deficient band;
+ * that column's coefficients are set to zero).
+ */
+ftcg_status_t ftcg_band(ftcg_plan_t plan, int32_t r, void* d_coef_out, ftcg_stream_t stream);
+
+/*
+ * ftcg_cgls -- the frame approximation (Sec. III-B, Eq. afr / afrm; in 2-D Eq. twodframe and
+ * twodframeB): the minimum-norm least-squares image x = argmin || W^(1/2) (E x - v) ||_2 of the
+ * data frame E_jp = exp(-2 pi i lambda_j . p / N), computed by CGLS from x = 0 with the plan's
+ * gridded operators for E (ftcg_forward) and E^H (ftcg_adjoint with unit weights).
+ *   d_values       device, M complex64, acquisition order.
+ *   d_row_weights  device, M float64 row weights w_j > 0 (for example the FTCG weights of
+ *                  ftcg_weights, which make the first iterate a multiple of the FTCG image and
+ *                  precondition the iteration), or NULL for w = 1 (the plain frame approximation).
+ *   iters          iterations (0..100000); tol >= 0: an iteration whose normal-equation residual
+ *                  || E^H W (v - E x) || has fallen to tol times its initial value freezes x
+ *                  (tol = 0: all iterations run).
+ *   d_image        device, N x N complex64 (output, the last iterate).
+ *   h_resnorms     host, NULL or iters + 1 doubles: the residual norm before each iteration.
+ *   h_iters        host, NULL or the number of iterations that changed x.
+ * FP32 vectors, FP64 reductions; no host synchronisation between iterations, one at the end.
+ * Temporary device memory (2 M + 2 N^2 complex64 values) comes from the library pool; the plan's
+ * installed weights are left as they were. FP32 plans only (NOT_SUPPORTED for BF16 plans).
+ */
+ftcg_status_t ftcg_cgls(ftcg_plan_t plan, const void* d_values, const double* d_row_weights,
+                        int32_t iters, double tol, void* d_image, double* h_resnorms,
+                        int32_t* h_iters, ftcg_stream_t stream);
+
 /* Release a plan and all device memory it holds (synchronises). NULL is accepted. */
 ftcg_status_t ftcg_destroy(ftcg_plan_t plan);
 

@@ -50,6 +50,8 @@ void release_plan(Plan* p) {
     if (p->grid) cudaFree(p->grid);
     if (p->status) cudaFree(p->status);
     if (p->stage_vals) cudaFree(p->stage_vals);
+    if (p->alpha_cur) cudaFree(p->alpha_cur);
+    release_band(p);
     if (p->stage_img) cudaFree(p->stage_img);
     if (p->fft_ok) cufftDestroy(p->fft);
     release_pruned_fft(p);
@@ -162,7 +164,7 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
 
 }  // namespace ftcg
 
-namespace {
+namespace ftcg {
 
 // the full G x G C2C plan (forward operator; adjoint fallback), created on first use
 ftcg_status_t ensure_full_fft(Plan* p) {
@@ -174,8 +176,17 @@ ftcg_status_t ensure_full_fft(Plan* p) {
     return FTCG_SUCCESS;
 }
 
-ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* img, cudaStream_t s) {
+ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* img, cudaStream_t s,
+                             bool use_band) {
     p->last_stream = s;
+    if (use_band && p->band_r > 0 && p->M > 0) {
+        if (vdtype != FTCG_VALUES_C64) {
+            set_error("adjoint with banded coefficients: values must be complex64");
+            return FTCG_ERR_NOT_SUPPORTED;
+        }
+        FTCG_TRY(band_apply(*p, vals, s));     // tau = C v, spread with unit weights
+        vals = p->band_tau;
+    }
     cudaEvent_t* ev = nullptr;
     if (p->profiling && p->prof_calls < kMaxProfiled) ev = p->prof_ev + 4 * p->prof_calls++;
     if (ev) FTCG_CK(cudaEventRecord(ev[0], s));
@@ -199,6 +210,20 @@ ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* im
     if (ev) FTCG_CK(cudaEventRecord(ev[3], s));
     return FTCG_SUCCESS;
 }
+
+ftcg_status_t forward_device(Plan* p, const void* img, void* vals, cudaStream_t s) {
+    p->last_stream = s;
+    FTCG_TRY(ensure_full_fft(p));
+    FTCG_TRY(launch_pad_apod(*p, reinterpret_cast<const float2*>(img), p->grid, s));
+    FTCG_CKFFT(cufftSetStream(p->fft, s));
+    FTCG_CKFFT(cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
+                            reinterpret_cast<cufftComplex*>(p->grid), CUFFT_FORWARD));
+    return launch_interp(*p, p->grid, reinterpret_cast<float2*>(vals), s);
+}
+
+}  // namespace ftcg
+
+namespace {
 
 ftcg_status_t check_values(const Plan* p, const void* v, int32_t vdtype, const char* what) {
     if (vdtype != FTCG_VALUES_C64 && vdtype != FTCG_VALUES_BF16X2) {
@@ -288,6 +313,7 @@ ftcg_status_t ftcg_weights(ftcg_plan_t plan, double* d_alpha_out, ftcg_stream_t 
     Plan* p = reinterpret_cast<Plan*>(plan);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
+    release_band(p);                           // the diagonal weights replace a band
     return compute_weights(*p, d_alpha_out, s);
     FTCG_API_END
 }
@@ -302,6 +328,7 @@ ftcg_status_t ftcg_set_weights(ftcg_plan_t plan, const void* d_alpha, int32_t dt
     Plan* p = reinterpret_cast<Plan*>(plan);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
+    release_band(p);                           // the diagonal weights replace a band
     return launch_set_alpha(*p, d_alpha, dtype, s);
     FTCG_API_END
 }
@@ -376,14 +403,7 @@ ftcg_status_t ftcg_forward(ftcg_plan_t plan, const void* d_image, void* d_values
     Plan* p = reinterpret_cast<Plan*>(plan);
     if (!d_image) return invalid("ftcg_forward: image pointer is NULL");
     if (p->M > 0 && !d_values) return invalid("ftcg_forward: values pointer is NULL");
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    p->last_stream = s;
-    FTCG_TRY(ensure_full_fft(p));
-    FTCG_TRY(launch_pad_apod(*p, reinterpret_cast<const float2*>(d_image), p->grid, s));
-    FTCG_CKFFT(cufftSetStream(p->fft, s));
-    FTCG_CKFFT(cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
-                            reinterpret_cast<cufftComplex*>(p->grid), CUFFT_FORWARD));
-    return launch_interp(*p, p->grid, reinterpret_cast<float2*>(d_values), s);
+    return forward_device(p, d_image, d_values, reinterpret_cast<cudaStream_t>(stream));
     FTCG_API_END
 }
 

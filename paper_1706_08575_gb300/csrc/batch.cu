@@ -205,15 +205,18 @@ struct EventPair {
     }
 };
 
-// Time the spreading kernel of a plan (values are irrelevant to the cost: zeros).
+// Time the spreading kernel of a plan (values are irrelevant to the cost: zeros), in the launch
+// the adjoint makes: only the tiles the shared-memory transform reads when G takes that path.
 ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaStream_t s,
                           float* ms) {
     EventPair ev;
     FTCG_CK(cudaEventCreate(&ev.a));
     FTCG_CK(cudaEventCreate(&ev.b));
-    FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s));   // warm-up
+    const bool pruned = smem_fft_supported(p.G);
+    FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s, pruned));   // warm-up
     FTCG_CK(cudaEventRecord(ev.a, s));
-    for (int r = 0; r < 3; ++r) FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s));
+    for (int r = 0; r < 3; ++r)
+        FTCG_TRY(launch_spread(p, zeros, FTCG_VALUES_C64, grid, s, pruned));
     FTCG_CK(cudaEventRecord(ev.b, s));
     FTCG_CK(cudaEventSynchronize(ev.b));
     FTCG_CK(cudaEventElapsedTime(ms, ev.a, ev.b));

@@ -208,6 +208,13 @@ struct Plan {
     unsigned* col_mask = nullptr;       // the same blocks as a bit mask
     float2* tw = nullptr;
     unsigned* status = nullptr;         // device status word
+    // banded FTCG coefficients (band.cu): M x (2 band_r - 1) complex128 and the values buffer
+    // tau = C v that the adjoint spreads; band_r = 0 when the diagonal weights are in use
+    int band_r = 0;
+    void* band_c = nullptr;
+    void* band_tau = nullptr;
+    float* alpha_cur = nullptr;         // the installed weights in acquisition order (FP32;
+                                        // nullptr while alpha = 1)
     void* stage_vals = nullptr;         // ftcg_adjoint_host staging (device)
     void* stage_img = nullptr;
     cudaStream_t last_stream = nullptr;
@@ -333,7 +340,18 @@ inline bool deapod_vec_ok(const void* grid, const void* img, int N) {
 }
 ftcg_status_t launch_pad_apod(const Plan& p, const float2* img, float2* grid, cudaStream_t s);
 ftcg_status_t launch_interp(const Plan& p, const float2* grid, float2* vals, cudaStream_t s);
-ftcg_status_t launch_set_alpha(const Plan& p, const void* alpha, int dtype, cudaStream_t s);
+// install weights (NULL: alpha = 1) in the plan's entries and keep their FP32 copy in alpha_cur
+ftcg_status_t launch_set_alpha(Plan& p, const void* alpha, int dtype, cudaStream_t s);
+// install weights in the entries only (alpha_cur unchanged)
+ftcg_status_t install_alpha(const Plan& p, const void* alpha, int dtype, cudaStream_t s);
+// api.cu: the plan's operators on device buffers (stream-ordered, no host synchronisation);
+// with use_band the adjoint applies the installed banded coefficients first (tau = C v)
+ftcg_status_t adjoint_device(Plan* p, const void* vals, int32_t vdtype, void* img, cudaStream_t s,
+                             bool use_band = true);
+// band.cu: tau = C v into p.band_tau; release the band
+ftcg_status_t band_apply(const Plan& p, const void* vals, cudaStream_t s);
+void release_band(Plan* p);
+ftcg_status_t forward_device(Plan* p, const void* img, void* vals, cudaStream_t s);
 // window.cu
 ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cudaStream_t s);
 double es_beta(int w, double sigma);

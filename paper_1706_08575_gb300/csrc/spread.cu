@@ -170,6 +170,14 @@ __global__ void k_set_alpha(Entry* __restrict__ ent, int64_t n, const void* __re
     }
 }
 
+__global__ void k_alpha_f32(const void* __restrict__ alpha, int dtype, int64_t M,
+                            float* __restrict__ out) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+         j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = dtype == FTCG_WEIGHTS_F64 ? (float)reinterpret_cast<const double*>(alpha)[j]
+                                           : reinterpret_cast<const float*>(alpha)[j];
+}
+
 int blocks_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -237,12 +245,24 @@ ftcg_status_t launch_interp(const Plan& p, const float2* grid, float2* vals, cud
     return FTCG_SUCCESS;
 }
 
-ftcg_status_t launch_set_alpha(const Plan& p, const void* alpha, int dtype, cudaStream_t s) {
+ftcg_status_t install_alpha(const Plan& p, const void* alpha, int dtype, cudaStream_t s) {
     if (p.bin.n_entries == 0) return FTCG_SUCCESS;
     k_set_alpha<<<blocks_for(p.bin.n_entries, 256), 256, 0, s>>>(
         p.bin.ent, p.bin.n_entries, alpha, dtype, p.opts.precision == FTCG_PREC_BF16);
     FTCG_CK(cudaGetLastError());
     return launch_set_alpha_mma(p, alpha, dtype, s);
+}
+
+ftcg_status_t launch_set_alpha(Plan& p, const void* alpha, int dtype, cudaStream_t s) {
+    if (!alpha) {
+        if (p.alpha_cur) FTCG_CK(pool_free(p.alpha_cur, s));
+        p.alpha_cur = nullptr;
+    } else if (p.M > 0) {
+        if (!p.alpha_cur) FTCG_CK(pool_malloc(&p.alpha_cur, (size_t)p.M * sizeof(float), s));
+        k_alpha_f32<<<blocks_for(p.M, 256), 256, 0, s>>>(alpha, dtype, p.M, p.alpha_cur);
+        FTCG_CK(cudaGetLastError());
+    }
+    return install_alpha(p, alpha, dtype, s);
 }
 
 }  // namespace ftcg

@@ -18,24 +18,23 @@ namespace mma {
 constexpr int kThreads = FTCG_MMA_THREADS;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMinBlocks = FTCG_MMA_MINB;
-// chunks the loop reads ahead of the one it computes: slots two ahead, values one ahead
-constexpr int kPrefetchChunks = 2;
+// padding chunks after the last one (a read past the end stays inside the array)
+constexpr int kPrefetchChunks = 1;
 
-// Dynamic shared memory of one tile: the two accumulator planes of the (T + 7)^2 block.
+// Dynamic shared memory of one tile: the two accumulator planes of the (T + 7)^2 block, then
+// each warp's staging buffers (32 slots of 16 bytes and 32 row offsets).
 __host__ __device__ constexpr size_t tile_smem_bytes(int T) {
-    return (size_t)2 * (T + kMmaMaxW - 1) * (T + kMmaMaxW) * sizeof(float);
+    return (size_t)2 * (T + kMmaMaxW - 1) * (T + kMmaMaxW) * sizeof(float) +
+           (size_t)kWarps * 32 * (16 + sizeof(int));
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// x = hi + lo, both TF32 (lo rounded too, so the MMA reads it without further truncation)
+// x = hi + lo with hi = x rounded to TF32 (10 stored significand bits; the magnitude rounded half
+// away from zero by an integer add on the bit pattern) and lo = x - hi, which is exact in FP32
+// and at most 2^-11 |x|. The MMA reads lo as TF32 (its low 13 bits ignored), so the pair carries
+// x to within 2^-21 |x|.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - __uint_as_float(hi));
+    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
@@ -53,10 +52,34 @@ __device__ __forceinline__ float horner(const float (&c)[kMmaDeg + 1], float s) 
     return p;
 }
 
-template <bool VBF>
-__device__ __forceinline__ float2 chunk_value(const void* __restrict__ vals, uint32_t packed) {
-    return (packed & kMmaPad) ? make_float2(0.f, 0.f)
-                              : tile::load_value<VBF>(vals, packed & kSampleMask);
+// One staged slot: the chunk slot's offsets within its taps' unit interval and its weighted
+// value c = alpha v (zero for padding), 16 bytes; its row offset within the chunk window
+// (0..8) is kept beside it.
+struct __align__(16) StagedSlot {
+    float sx, sy, cr, ci;
+};
+
+// Per-warp staging of kStageChunks chunks (kStageChunks * 8 slots, one per lane when 4).
+constexpr int kStageChunks = 4;
+constexpr int kStageSlots = kStageChunks * kMmaChunk;
+static_assert(kStageSlots == 32, "one staged slot per lane");
+
+// Load slot i (a padding slot, or an index past the warp's range, gives c = 0): the slot and its
+// sample's value; no branch (padding slots name sample 0, whose value is read and discarded).
+template <bool VBF, bool ABF>
+__device__ __forceinline__ void load_slot(const MmaEntry* __restrict__ cent,
+                                          const void* __restrict__ vals, int64_t i, int64_t end,
+                                          StagedSlot& out, int& off) {
+    const bool live = i < end;
+    const MmaEntry e = cent[live ? i : end - 1];
+    const float2 v = tile::load_value<VBF>(vals, e.packed & kSampleMask);
+    float al = ABF ? tile::bf16_bits_to_float(e.alpha) : __uint_as_float(e.alpha);
+    al = (live && !(e.packed & kMmaPad)) ? al : 0.0f;
+    out.sx = e.sx;
+    out.sy = e.sy;
+    out.cr = al * v.x;
+    out.ci = al * v.y;
+    off = (int)((e.packed >> kSampleBits) & 15u);
 }
 
 // One halo-layout tile by the whole CTA (kThreads threads): its chunks [tile_chunk[tile],
@@ -108,77 +131,81 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
         }
     };
 
+    // per-warp staging buffers after the accumulator planes
+    StagedSlot* st_slot = reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) + warp * kStageSlots;
+    int* st_off = reinterpret_cast<int*>(reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) +
+                                         kWarps * kStageSlots) + warp * kStageSlots;
     if (ca < cb) {
-        // software pipeline: the slots of chunk c + 2 and the values of chunk c + 1 are in
-        // flight while chunk c is computed (the chunk array ends with kPrefetchChunks padding
-        // chunks, so the reads ahead need no bounds test; padding slots load no value)
-        MmaEntry e1 = cent[(int64_t)ca * kMmaChunk + t];
-        MmaEntry e2 = cent[(int64_t)ca * kMmaChunk + t + 4];
-        float2 v1 = chunk_value<VBF>(vals, e1.packed);
-        float2 v2 = chunk_value<VBF>(vals, e2.packed);
-        MmaEntry n1 = cent[(int64_t)(ca + 1) * kMmaChunk + t];
-        MmaEntry n2 = cent[(int64_t)(ca + 1) * kMmaChunk + t + 4];
-        for (int c = ca; c < cb; ++c) {
-            const uint32_t h = chdr[c];
-            const float2 nv1 = chunk_value<VBF>(vals, n1.packed);
-            const float2 nv2 = chunk_value<VBF>(vals, n2.packed);
-            const MmaEntry nn1 = cent[(int64_t)(c + 2) * kMmaChunk + t];
-            const MmaEntry nn2 = cent[(int64_t)(c + 2) * kMmaChunk + t + 4];
-            const int cx = (int)(h & 0xffu), yb = (int)((h >> 8) & 0xffu);
-            if (cx != cur_cx || (yb != cur_yb && yb != cur_yb + 8)) {      // a new window
-                if (cur_cx >= 0) {
-                    flush_half(0);
-                    flush_half(1);
-                }
+        // each lane loads one slot of the next kStageChunks chunks (coalesced 16-byte loads, one
+        // value gather per slot); the registers hold the next batch while the current one is
+        // computed from shared memory
+        const int64_t send = (int64_t)cb * kMmaChunk;
+        StagedSlot nxt;
+        int noff;
+        load_slot<VBF, ABF>(cent, vals, (int64_t)ca * kMmaChunk + lane, send, nxt, noff);
+        for (int cbase = ca; cbase < cb; cbase += kStageChunks) {
+            __syncwarp();
+            st_slot[lane] = nxt;
+            st_off[lane] = noff;
+            __syncwarp();
+            if (cbase + kStageChunks < cb)
+                load_slot<VBF, ABF>(cent, vals,
+                                    (int64_t)(cbase + kStageChunks) * kMmaChunk + lane, send, nxt,
+                                    noff);
+            const int nk = min(kStageChunks, cb - cbase);
+            for (int k = 0; k < nk; ++k) {
+                const int c = cbase + k;
+                const uint32_t h = chdr[c];
+                const int cx = (int)(h & 0xffu), yb = (int)((h >> 8) & 0xffu);
+                if (cx != cur_cx || (yb != cur_yb && yb != cur_yb + 8)) {   // a new window
+                    if (cur_cx >= 0) {
+                        flush_half(0);
+                        flush_half(1);
+                    }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) dr[i] = di[i] = 0.f;
-                cur_cx = cx;
-                cur_yb = yb;
-            } else if (yb != cur_yb) {             // the window moves down by 8 rows
-                flush_half(0);
-                dr[0] = dr[2];
-                dr[1] = dr[3];
-                di[0] = di[2];
-                di[1] = di[3];
-                dr[2] = dr[3] = di[2] = di[3] = 0.f;
-                cur_yb = yb;
+                    for (int i = 0; i < 4; ++i) dr[i] = di[i] = 0.f;
+                    cur_cx = cx;
+                    cur_yb = yb;
+                } else if (yb != cur_yb) {         // the window moves down by 8 rows
+                    flush_half(0);
+                    dr[0] = dr[2];
+                    dr[1] = dr[3];
+                    di[0] = di[2];
+                    di[1] = di[3];
+                    dr[2] = dr[3] = di[2] = di[3] = 0.f;
+                    cur_yb = yb;
+                }
+                const StagedSlot e1 = st_slot[k * kMmaChunk + t];
+                const StagedSlot e2 = st_slot[k * kMmaChunk + t + 4];
+                const int off1 = st_off[k * kMmaChunk + t], off2 = st_off[k * kMmaChunk + t + 4];
+                // column factor of tap g times the weighted value; row factor of tap g
+                const float fx1 = horner(cf, e1.sx), fx2 = horner(cf, e2.sx);
+                const float fy1 = horner(cf, e1.sy), fy2 = horner(cf, e2.sy);
+                // A[r][k]: window row r = g or g + 8 takes tap (g - off) mod 8 of sample k, held
+                // by lane ((g - off) & 7, t) (every lane with the same t evaluates the same
+                // samples)
+                const float a1 = __shfl_sync(0xffffffffu, fy1, (((g - off1) & 7) << 2) | t);
+                const float a2 = __shfl_sync(0xffffffffu, fy2, (((g - off2) & 7) << 2) | t);
+                const bool low1 = g >= off1, low2 = g >= off2;
+                uint32_t a1h, a1l, a2h, a2l;
+                split_tf32(a1, a1h, a1l);
+                split_tf32(a2, a2h, a2l);
+                uint32_t b1rh, b1rl, b1ih, b1il, b2rh, b2rl, b2ih, b2il;
+                split_tf32(e1.cr * fx1, b1rh, b1rl);
+                split_tf32(e1.ci * fx1, b1ih, b1il);
+                split_tf32(e2.cr * fx2, b2rh, b2rl);
+                split_tf32(e2.ci * fx2, b2ih, b2il);
+                const uint32_t ah0 = low1 ? a1h : 0u, ah1 = low1 ? 0u : a1h;
+                const uint32_t ah2 = low2 ? a2h : 0u, ah3 = low2 ? 0u : a2h;
+                const uint32_t al0 = low1 ? a1l : 0u, al1 = low1 ? 0u : a1l;
+                const uint32_t al2 = low2 ? a2l : 0u, al3 = low2 ? 0u : a2l;
+                mma_tf32(dr, ah0, ah1, ah2, ah3, b1rh, b2rh);
+                mma_tf32(dr, ah0, ah1, ah2, ah3, b1rl, b2rl);
+                mma_tf32(dr, al0, al1, al2, al3, b1rh, b2rh);
+                mma_tf32(di, ah0, ah1, ah2, ah3, b1ih, b2ih);
+                mma_tf32(di, ah0, ah1, ah2, ah3, b1il, b2il);
+                mma_tf32(di, al0, al1, al2, al3, b1ih, b2ih);
             }
-            const float al1 = ABF ? tile::bf16_bits_to_float(e1.alpha) : __uint_as_float(e1.alpha);
-            const float al2 = ABF ? tile::bf16_bits_to_float(e2.alpha) : __uint_as_float(e2.alpha);
-            // column factor (tap g) with the weight, row factor of tap g of each sample
-            const float fx1 = horner(cf, e1.sx) * al1, fx2 = horner(cf, e2.sx) * al2;
-            const float fy1 = horner(cf, e1.sy), fy2 = horner(cf, e2.sy);
-            const int off1 = (int)((e1.packed >> kSampleBits) & 15u);
-            const int off2 = (int)((e2.packed >> kSampleBits) & 15u);
-            // A[r][k]: window row r = g or g + 8 takes tap (g - off) mod 8 of sample k, held by
-            // lane ((g - off) & 7, t) (every lane with the same t evaluates the same samples)
-            const float a1 = __shfl_sync(0xffffffffu, fy1, (((g - off1) & 7) << 2) | t);
-            const float a2 = __shfl_sync(0xffffffffu, fy2, (((g - off2) & 7) << 2) | t);
-            const bool low1 = g >= off1, low2 = g >= off2;
-            uint32_t a1h, a1l, a2h, a2l;
-            split_tf32(a1, a1h, a1l);
-            split_tf32(a2, a2h, a2l);
-            uint32_t b1rh, b1rl, b1ih, b1il, b2rh, b2rl, b2ih, b2il;
-            split_tf32(v1.x * fx1, b1rh, b1rl);
-            split_tf32(v1.y * fx1, b1ih, b1il);
-            split_tf32(v2.x * fx2, b2rh, b2rl);
-            split_tf32(v2.y * fx2, b2ih, b2il);
-            const uint32_t ah0 = low1 ? a1h : 0u, ah1 = low1 ? 0u : a1h;
-            const uint32_t ah2 = low2 ? a2h : 0u, ah3 = low2 ? 0u : a2h;
-            const uint32_t al0 = low1 ? a1l : 0u, al1r = low1 ? 0u : a1l;
-            const uint32_t al2r = low2 ? a2l : 0u, al3 = low2 ? 0u : a2l;
-            mma_tf32(dr, ah0, ah1, ah2, ah3, b1rh, b2rh);
-            mma_tf32(dr, ah0, ah1, ah2, ah3, b1rl, b2rl);
-            mma_tf32(dr, al0, al1r, al2r, al3, b1rh, b2rh);
-            mma_tf32(di, ah0, ah1, ah2, ah3, b1ih, b2ih);
-            mma_tf32(di, ah0, ah1, ah2, ah3, b1il, b2il);
-            mma_tf32(di, al0, al1r, al2r, al3, b1ih, b2ih);
-            e1 = n1;
-            e2 = n2;
-            v1 = nv1;
-            v2 = nv2;
-            n1 = nn1;
-            n2 = nn2;
         }
         flush_half(0);
         flush_half(1);

@@ -87,6 +87,8 @@ SIGNATURES = [
     ("ftcg_mlp_train_step", _I32, [_VP, _VP, _VP, _VP, _I64, ctypes.c_float, _VP, _VP]),
     ("ftcg_mlp_destroy", _I32, [_VP]),
     ("ftcg_adjoint_small_noalloc", _I32, [_VP, _VP, _VP, _I64, _I32, _D, _I32, _VP, _VP]),
+    ("ftcg_cgls", _I32, [_VP, _VP, _VP, _I32, _D, _VP, _VP, _VP, _VP]),
+    ("ftcg_band", _I32, [_VP, _I32, _VP, _VP]),
     ("ftcg_destroy", _I32, [_VP]),
     ("ftcg_status_string", ctypes.c_char_p, [_I32]),
     ("ftcg_last_error", ctypes.c_char_p, []),
@@ -238,6 +240,32 @@ class Plan:
             out = torch.empty(self.M, dtype=torch.complex64, device=self.device)
         _check(lib().ftcg_forward(self._h, _ptr(image.contiguous()), _ptr(out), _stream(stream)))
         return out
+
+    def band(self, r, stream=None):
+        """Banded FTCG coefficients for band r (installed in the plan); returns them as an
+        M x (2r - 1) complex128 tensor (row k: column k of C at rows k - r + 1 .. k + r - 1)."""
+        import torch
+        out = torch.zeros((self.M, 2 * int(r) - 1), dtype=torch.complex128, device=self.device)
+        _check(lib().ftcg_band(self._h, int(r), _ptr(out), _stream(stream)))
+        return out
+
+    def cgls(self, values, weights=None, iters=50, tol=0.0, out=None, stream=None):
+        """The frame approximation (minimum-norm least squares, row weights optional) by CGLS
+        with this plan's operators. Returns (image, residual norms, iterations that moved x)."""
+        import torch
+        if values.dtype != torch.complex64:
+            raise TypeError("values must be complex64")
+        if out is None:
+            out = torch.empty((self.N, self.N), dtype=torch.complex64, device=self.device)
+        w = None
+        if weights is not None:
+            w = weights.to(torch.float64).contiguous()
+        hist = np.empty(int(iters) + 1, np.float64)
+        done = ctypes.c_int32()
+        _check(lib().ftcg_cgls(self._h, _ptr(values.contiguous()), _ptr(w), int(iters),
+                               float(tol), _ptr(out), hist.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(done), _stream(stream)))
+        return out, hist, done.value
 
     def check(self):
         _check(lib().ftcg_check(self._h))
