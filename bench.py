@@ -618,6 +618,72 @@ def precision_sweep_extra(device, reps=20):
     return out
 
 
+def psnr(img, ref):
+    """10 log10(max |ref|^2 / mean |img - ref|^2) over the pixels (the paper does not state its
+    normalisation; this is the usual peak form)."""
+    import numpy as np
+    mse = float(np.mean(np.abs(np.asarray(img) - ref) ** 2))
+    return 10 * math.log10(float(np.max(np.abs(ref)) ** 2) / mse)
+
+
+def paper_experiments(device, iters=300):
+    """The paper's raster experiments (Sec. V) with its test function sin(4 pi x1) sin(2 pi x2)
+    (Eq. eq2) on the device: the noisy grid (900 samples, band 15), the asterisk (225 samples,
+    band 23) and the side-scan-SAS-like wedge (1000 samples, band 15), N = 30. For each, the
+    PSNR against the function of: gridding with the exact diagonal FTCG weights (r = 1), FTCG
+    with the banded C (ftcg_band), and the frame approximation (ftcg_cgls to convergence), plus
+    the CGLS iterations to a 1e-4 residual without and with the FTCG row weights (the
+    preconditioning remark of Sec. V-C). Then the 1-D study of Sec. III-C (Fig. errorComp):
+    relative l2 error against sin(4 pi x) for jittered rasters of 2n + 1 samples, the same three
+    methods with r = ceil(log(2n + 1))."""
+    import numpy as np
+    import torch
+    import paper_1706_08575_gb300 as F
+    import sasgen
+
+    def run(lam, v, N, r):
+        out = {}
+        lt = torch.from_numpy(lam).to(device)
+        vt = torch.from_numpy(v.astype(np.complex64)).to(device)
+        with F.Plan(lt, N, 2.0, 8) as p:
+            a = p.weights()
+            out["cg_diag"] = p.adjoint(vt).cpu().numpy()
+            p.band(r)
+            out["ftcg_band"] = p.adjoint(vt).cpu().numpy()
+            p.set_weights(None)
+            x, h, k = p.cgls(vt, iters=iters, tol=1e-7)
+            out["frame"] = x.cpu().numpy() * N * N
+            _, h0, k0 = p.cgls(vt, iters=iters, tol=1e-4)
+            _, h1, k1 = p.cgls(vt, weights=a, iters=iters, tol=1e-4)
+        return out, {"plain": int(k0), "ftcg_weights": int(k1)}, int(k)
+
+    res = {}
+    for name, lam, r, paper in (
+            ("noisy_grid", sasgen.noisy_grid(), 8, {"frame": 39.79, "ftcg_band": 25.91}),
+            ("asterisk", sasgen.asterisk(), 12, {"frame": 40.06, "ftcg_band": 37.48}),
+            ("sas_like", sasgen.sas_like(), 8, {"frame": 21.04, "ftcg_band": 23.27})):
+        N = 30
+        imgs, cg_iters, k = run(lam, sasgen.test_function_values(lam), N, r)
+        ref = sasgen.test_function_image(N)
+        res[name] = {"samples": int(lam.shape[0]), "N": N, "band": 2 * r - 1,
+                     "psnr_db": {m: psnr(i, ref) for m, i in imgs.items()},
+                     "paper_psnr_db": paper, "frame_cgls_iters": k,
+                     "cgls_iters_to_1e-4": cg_iters}
+    one_d = []
+    for n in (8, 16, 32, 64, 128):
+        lam = sasgen.jittered_1d(sasgen.BASE_SEED + 30 + n, n)
+        N = 2 * n + 2
+        r = int(math.ceil(math.log(2 * n + 1)))
+        imgs, _, _ = run(lam, sasgen.test_function_1d_values(lam), N, r)
+        x = np.arange(-(N // 2), N - N // 2) / N + 0.5
+        ref = np.sin(4 * np.pi * x)
+        row = {m: float(np.linalg.norm(i[N // 2] - ref) / np.linalg.norm(ref))
+               for m, i in imgs.items()}
+        one_d.append({"samples": 2 * n + 1, "N": N, "r": r, "rel_l2": row})
+    res["one_d_error_vs_raster"] = one_d
+    return res
+
+
 def tiny_extra(device, reps=50):
     """The 4,096-sample raster (N = 64, w = 6): launch-latency bound, reported in microseconds
     (median of CUDA-event times, warm L2), with its sampled error against the direct sum."""
@@ -842,7 +908,8 @@ def run_ours(args):
                                           n_pings=args.extras_pings)
             except Exception as e:       # the headline line must still print
                 extras = {"error": f"{type(e).__name__}: {e}"}
-            for key, fn in [("precision_sweep", precision_sweep_extra), ("tiny", tiny_extra)]:
+            for key, fn in [("precision_sweep", precision_sweep_extra), ("tiny", tiny_extra),
+                            ("paper_experiments", paper_experiments)]:
                 try:
                     more[key] = fn(device)
                 except Exception as e:

@@ -22,10 +22,10 @@ constexpr int kMinBlocks = FTCG_MMA_MINB;
 constexpr int kPrefetchChunks = 1;
 
 // Dynamic shared memory of one tile: the two accumulator planes of the (T + 7)^2 block, then
-// each warp's staging buffers (32 slots of 16 bytes and 32 row offsets).
+// each warp's staging buffers (32 slots of 16 bytes, 32 row offsets, 4 chunk headers).
 __host__ __device__ constexpr size_t tile_smem_bytes(int T) {
     return (size_t)2 * (T + kMmaMaxW - 1) * (T + kMmaMaxW) * sizeof(float) +
-           (size_t)kWarps * 32 * (16 + sizeof(int));
+           (size_t)kWarps * (32 * (16 + sizeof(int)) + 4 * sizeof(uint32_t));
 }
 
 // x = hi + lo with hi = x rounded to TF32 (10 stored significand bits; the magnitude rounded half
@@ -118,16 +118,19 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
     const int cb = c0 + (int)((int64_t)n * (warp + 1) / kWarps);
     // D fragments: real and imaginary plane, rows g (d[0], d[1]) and g + 8 (d[2], d[3]) of the
     // window, columns 2t and 2t + 1
+    // the hi x hi products and the two cross products accumulate separately, so that the MMAs
+    // of a chunk do not wait on one another
     float dr[4] = {0.f, 0.f, 0.f, 0.f}, di[4] = {0.f, 0.f, 0.f, 0.f};
+    float er[4] = {0.f, 0.f, 0.f, 0.f}, ei[4] = {0.f, 0.f, 0.f, 0.f};
     int cur_cx = -1, cur_yb = 0;
     auto flush_half = [&](int h) {             // window rows g + 8h into the tile accumulator
         const int row = cur_yb + g + 8 * h;
         if (row < PT) {
             const int o = row * LD + cur_cx + 2 * t;   // cur_cx + 2t + 1 <= T + 6 < PT
-            atomicAdd(s_re + o, dr[2 * h]);
-            atomicAdd(s_re + o + 1, dr[2 * h + 1]);
-            atomicAdd(s_im + o, di[2 * h]);
-            atomicAdd(s_im + o + 1, di[2 * h + 1]);
+            atomicAdd(s_re + o, dr[2 * h] + er[2 * h]);
+            atomicAdd(s_re + o + 1, dr[2 * h + 1] + er[2 * h + 1]);
+            atomicAdd(s_im + o, di[2 * h] + ei[2 * h]);
+            atomicAdd(s_im + o + 1, di[2 * h + 1] + ei[2 * h + 1]);
         }
     };
 
@@ -135,6 +138,9 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
     StagedSlot* st_slot = reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) + warp * kStageSlots;
     int* st_off = reinterpret_cast<int*>(reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) +
                                          kWarps * kStageSlots) + warp * kStageSlots;
+    uint32_t* st_hdr = reinterpret_cast<uint32_t*>(reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) +
+                                                   kWarps * kStageSlots) +
+                       kWarps * kStageSlots + warp * kStageChunks;
     if (ca < cb) {
         // each lane loads one slot of the next kStageChunks chunks (coalesced 16-byte loads, one
         // value gather per slot); the registers hold the next batch while the current one is
@@ -142,20 +148,24 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
         const int64_t send = (int64_t)cb * kMmaChunk;
         StagedSlot nxt;
         int noff;
+        uint32_t nhdr = 0;
         load_slot<VBF, ABF>(cent, vals, (int64_t)ca * kMmaChunk + lane, send, nxt, noff);
+        if (lane < kStageChunks) nhdr = chdr[min(ca + lane, cb - 1)];
         for (int cbase = ca; cbase < cb; cbase += kStageChunks) {
             __syncwarp();
             st_slot[lane] = nxt;
             st_off[lane] = noff;
+            if (lane < kStageChunks) st_hdr[lane] = nhdr;
             __syncwarp();
-            if (cbase + kStageChunks < cb)
+            if (cbase + kStageChunks < cb) {
                 load_slot<VBF, ABF>(cent, vals,
                                     (int64_t)(cbase + kStageChunks) * kMmaChunk + lane, send, nxt,
                                     noff);
+                if (lane < kStageChunks) nhdr = chdr[min(cbase + kStageChunks + lane, cb - 1)];
+            }
             const int nk = min(kStageChunks, cb - cbase);
             for (int k = 0; k < nk; ++k) {
-                const int c = cbase + k;
-                const uint32_t h = chdr[c];
+                const uint32_t h = st_hdr[k];
                 const int cx = (int)(h & 0xffu), yb = (int)((h >> 8) & 0xffu);
                 if (cx != cur_cx || (yb != cur_yb && yb != cur_yb + 8)) {   // a new window
                     if (cur_cx >= 0) {
@@ -163,7 +173,7 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                         flush_half(1);
                     }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) dr[i] = di[i] = 0.f;
+                    for (int i = 0; i < 4; ++i) dr[i] = di[i] = er[i] = ei[i] = 0.f;
                     cur_cx = cx;
                     cur_yb = yb;
                 } else if (yb != cur_yb) {         // the window moves down by 8 rows
@@ -172,7 +182,11 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                     dr[1] = dr[3];
                     di[0] = di[2];
                     di[1] = di[3];
-                    dr[2] = dr[3] = di[2] = di[3] = 0.f;
+                    er[0] = er[2];
+                    er[1] = er[3];
+                    ei[0] = ei[2];
+                    ei[1] = ei[3];
+                    dr[2] = dr[3] = di[2] = di[3] = er[2] = er[3] = ei[2] = ei[3] = 0.f;
                     cur_yb = yb;
                 }
                 const StagedSlot e1 = st_slot[k * kMmaChunk + t];
@@ -200,11 +214,11 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                 const uint32_t al0 = low1 ? a1l : 0u, al1 = low1 ? 0u : a1l;
                 const uint32_t al2 = low2 ? a2l : 0u, al3 = low2 ? 0u : a2l;
                 mma_tf32(dr, ah0, ah1, ah2, ah3, b1rh, b2rh);
-                mma_tf32(dr, ah0, ah1, ah2, ah3, b1rl, b2rl);
-                mma_tf32(dr, al0, al1, al2, al3, b1rh, b2rh);
                 mma_tf32(di, ah0, ah1, ah2, ah3, b1ih, b2ih);
-                mma_tf32(di, ah0, ah1, ah2, ah3, b1il, b2il);
-                mma_tf32(di, al0, al1, al2, al3, b1ih, b2ih);
+                mma_tf32(er, ah0, ah1, ah2, ah3, b1rl, b2rl);
+                mma_tf32(ei, ah0, ah1, ah2, ah3, b1il, b2il);
+                mma_tf32(er, al0, al1, al2, al3, b1rh, b2rh);
+                mma_tf32(ei, al0, al1, al2, al3, b1ih, b2ih);
             }
         }
         flush_half(0);

@@ -245,6 +245,8 @@ class Plan:
         """Banded FTCG coefficients for band r (installed in the plan); returns them as an
         M x (2r - 1) complex128 tensor (row k: column k of C at rows k - r + 1 .. k + r - 1)."""
         import torch
+        if int(r) < 1:
+            _check(lib().ftcg_band(self._h, int(r), None, _stream(stream)))
         out = torch.zeros((self.M, 2 * int(r) - 1), dtype=torch.complex128, device=self.device)
         _check(lib().ftcg_band(self._h, int(r), _ptr(out), _stream(stream)))
         return out

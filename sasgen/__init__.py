@@ -235,3 +235,83 @@ def random_case(seed, M, N, sigma=2.0, w=8, spread=None):
     lam = (rng.random((M, 2)) - 0.5) * s
     v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
     return lam, v
+
+
+# ---------------------------------------------------------------------------------------------
+# The paper's small rasters (Sec. V) and its test function
+# ---------------------------------------------------------------------------------------------
+
+def noisy_grid(seed=BASE_SEED + 21, n=30):
+    """lambda_n in [n1 - 1/4, n1 + 1/4] x [n2 - 1/4, n2 + 1/4] for n in {-n/2 .. n/2 - 1}^2
+    (uniform jitter, Sec. V-A): n^2 samples (900 for n = 30), acquisition order n1 fastest."""
+    rng = np.random.default_rng(seed)
+    g = np.arange(-(n // 2), n - n // 2, dtype=np.float64)
+    X, Y = np.meshgrid(g, g)
+    lam = np.stack([X.ravel(), Y.ravel()], 1)
+    return lam + rng.uniform(-0.25, 0.25, lam.shape)
+
+
+def asterisk(seed=BASE_SEED + 22, lines=8, per_line=28, extent=14.0, jitter=0.05):
+    """Diameters through the origin at angles k pi / lines (Sec. V-B), per_line samples on each
+    (radii uniform in [-extent, extent] without 0) plus the origin once, with a small radial
+    jitter: lines * per_line + 1 samples (225 by default), acquisition order line by line."""
+    rng = np.random.default_rng(seed)
+    r = np.linspace(-extent, extent, per_line + 1)     # odd count: the middle one is 0
+    r = np.delete(r, per_line // 2)
+    pts = [np.zeros((1, 2))]
+    for k in range(lines):
+        th = np.pi * k / lines
+        rr = r + rng.uniform(-jitter, jitter, r.shape)
+        pts.append(np.stack([rr * np.cos(th), rr * np.sin(th)], 1))
+    return np.concatenate(pts)
+
+
+def sas_like(seed=BASE_SEED + 23, n_kr=40, n_theta=25, span_deg=30.0, extent=14.0):
+    """A side-scan-SAS-like polar wedge (Sec. V-C): n_kr range wavenumbers x n_theta jittered
+    angles of the 100-130 kHz band, base-banded and scaled so that the wedge spans about
+    [-extent, extent] cycles: n_kr * n_theta samples (1000 by default), range fastest."""
+    rng = np.random.default_rng(seed)
+    kx, ky = polar_raster(rng, n_kr, n_theta, span_deg, theta_jitter_deg=0.05)
+    kspan = max(kx.max() - kx.min(), ky.max() - ky.min())
+    return baseband(kx, ky, 2 * np.pi * 2 * extent / kspan)
+
+
+def jittered_1d(seed, n):
+    """The 1-D raster lambda_k in [k - 1/4, k + 1/4], k = -n..n (2n + 1 samples, Sec. III-C and
+    Sec. V-A), embedded in 2-D with lambda_y = 0."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(-n, n + 1, dtype=np.float64)
+    return np.stack([k + rng.uniform(-0.25, 0.25, k.shape), np.zeros_like(k)], 1)
+
+
+def _sine_ft(a, lam):
+    """int_0^1 sin(2 pi a x) exp(-2 pi i lam x) dx for an integer a, then shifted to the centred
+    field of view [-1/2, 1/2) (a factor exp(i pi lam))."""
+    lam = np.asarray(lam, np.float64)
+
+    def E(u):       # int_0^1 exp(2 pi i u x) dx
+        small = np.abs(u) < 1e-12
+        us = np.where(small, 1.0, u)
+        return np.where(small, 1.0, (np.exp(2j * np.pi * us) - 1.0) / (2j * np.pi * us))
+
+    # sin(2 pi a x) = (exp(2 pi i a x) - exp(-2 pi i a x)) / 2i
+    return (E(a - lam) - E(-a - lam)) / 2j * np.exp(1j * np.pi * lam)
+
+
+def test_function_values(lam):
+    """Fourier data of the paper's test function f(x) = sin(4 pi x1) sin(2 pi x2) on [0, 1]^2
+    (Eq. eq2), on the centred field of view: v(lambda) = F_2(lambda_x) F_1(lambda_y)."""
+    lam = np.asarray(lam, np.float64)
+    return _sine_ft(2, lam[:, 0]) * _sine_ft(1, lam[:, 1])
+
+
+def test_function_image(N):
+    """f on the N x N pixel grid of the centred field of view, x = p / N + 1/2, indexed
+    [p_y + N/2, p_x + N/2]."""
+    x = (np.arange(-(N // 2), N - N // 2) / N) + 0.5
+    return np.multiply.outer(np.sin(2 * np.pi * x), np.sin(4 * np.pi * x)).astype(np.complex128)
+
+
+def test_function_1d_values(lam):
+    """Fourier data of f(x) = sin(4 pi x) on [0, 1] at lam[:, 0] (the 1-D experiment)."""
+    return _sine_ft(2, np.asarray(lam, np.float64)[:, 0])

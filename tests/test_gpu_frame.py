@@ -89,7 +89,7 @@ def test_first_weighted_iterate_is_the_ftcg_image(F):
     scale = np.vdot(img, x1) / np.vdot(img, img)
     assert O.rel_l2(x1, scale * img) < 1e-5
     assert scale.real > 0 and abs(scale.imag) < 1e-5 * abs(scale)
-    assert np.array_equal(again, img.astype(np.complex64))
+    assert O.rel_l2(again, img) < 1e-6           # the same weights (atomics reorder sums)
 
 
 def test_cgls_tolerance_and_history(F):
