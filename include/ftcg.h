@@ -332,6 +332,30 @@ ftcg_status_t ftcg_mlp_train_step(ftcg_mlp_t mlp, const void* d_features, const 
 ftcg_status_t ftcg_mlp_destroy(ftcg_mlp_t mlp);
 
 /*
+ * ftcg_weights_judge -- the exact judge and fallback of predicted weights (the exact FTCG
+ * construction of Eq. difopt at r = 1 keeps the last word). For K samples spread evenly over the
+ * acquisition order it sums S_k = sum_j F_N(lambda_jx - lambda_kx) F_N(lambda_jy - lambda_ky)
+ * directly over all M samples (FP32 Fejer terms of exactly reduced arguments, FP64 sums) and
+ * forms the ratios alpha_pred_k S_k. Their median is a calibration factor; the rms of the
+ * calibrated ratios around 1 estimates the relative weight error (the image error follows it).
+ * If that rms is at most max_rel_err the calibrated weights alpha_pred / median are installed
+ * (*h_accepted = 1); otherwise the exact weights are computed (ftcg_weights) and installed
+ * (*h_accepted = 0). h_stats: NULL or 3 doubles {median ratio, rms, max |calibrated error|}.
+ *   d_alpha  device, M float64 predicted weights (for example ftcg_mlp_predict's output).
+ *   K        1 .. min(M, 65536) samples judged (cost K M Fejer terms).
+ * Synchronises (one read-back of 2K doubles). Errors: those of ftcg_weights on a fallback.
+ */
+ftcg_status_t ftcg_weights_judge(ftcg_plan_t plan, const double* d_alpha, int32_t K,
+                                 double max_rel_err, int32_t* h_accepted, double* h_stats,
+                                 ftcg_stream_t stream);
+/* The same for every ping of a batch (d_alpha: n device pointers; K capped at each ping's M;
+ * h_accepted: NULL or n int32; h_stats: NULL or 3 n doubles); all pings' sums are computed
+ * before one read-back, then each ping is accepted or falls back on its own. */
+ftcg_status_t ftcg_batch_weights_judge(ftcg_batch_t batch, const double* const* d_alpha, int32_t K,
+                                       double max_rel_err, int32_t* h_accepted, double* h_stats,
+                                       ftcg_stream_t stream);
+
+/*
  * ftcg_adjoint_small_noalloc -- the weighted adjoint of ftcg_adjoint, without a plan and without
  * any allocation, for small images. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, such as code running while a stream is captured

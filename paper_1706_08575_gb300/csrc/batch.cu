@@ -894,6 +894,55 @@ ftcg_status_t ftcg_adjoint_batch(ftcg_batch_t batch, const void* const* d_values
     FTCG_API_END
 }
 
+ftcg_status_t ftcg_batch_weights_judge(ftcg_batch_t batch, const double* const* d_alpha, int32_t K,
+                                      double max_rel_err, int32_t* h_accepted, double* h_stats,
+                                      ftcg_stream_t stream) {
+    FTCG_API_BEGIN
+    clear_error();
+    if (!batch) {
+        set_error("ftcg_batch_weights_judge: batch is NULL");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    FTCG_TRY(check_ptr_array(reinterpret_cast<const void* const*>(d_alpha), b->n,
+                             "ftcg_batch_weights_judge weights"));
+    if (K < 1 || K > 65536 || !(max_rel_err >= 0.0)) {
+        set_error("ftcg_batch_weights_judge: K must be in 1..65536 and max_rel_err >= 0");
+        return FTCG_ERR_INVALID_VALUE;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    b->last = s;
+    // every ping's sums in flight together, one read-back, then the verdicts
+    std::vector<int> Ks(b->n);
+    std::vector<size_t> off(b->n + 1, 0);
+    for (int i = 0; i < b->n; ++i) {
+        Ks[i] = (int)std::min<int64_t>(K, b->pings[i]->M);
+        off[i + 1] = off[i] + 2 * (size_t)Ks[i];
+    }
+    double* d = nullptr;
+    FTCG_CK(pool_malloc(&d, std::max<size_t>(1, off[b->n]) * sizeof(double), s));
+    for (int i = 0; i < b->n; ++i)
+        if (Ks[i] > 0)
+            FTCG_TRY(judge_launch(*b->pings[i], d_alpha[i], Ks[i], d + off[i], d + off[i] + Ks[i],
+                                  s));
+    std::vector<double> h(std::max<size_t>(1, off[b->n]));
+    FTCG_CK(cudaMemcpyAsync(h.data(), d, off[b->n] * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FTCG_CK(cudaStreamSynchronize(s));
+    FTCG_CK(pool_free(d, s));
+    for (int i = 0; i < b->n; ++i) {
+        double st[3] = {1.0, 0.0, 0.0};
+        bool ok = true;
+        if (Ks[i] > 0) ok = judge_decide(h.data() + off[i], h.data() + off[i] + Ks[i], Ks[i],
+                                         max_rel_err, st);
+        if (h_accepted) h_accepted[i] = ok ? 1 : 0;
+        if (h_stats)
+            for (int k = 0; k < 3; ++k) h_stats[3 * i + k] = st[k];
+        if (b->pings[i]->M > 0) FTCG_TRY(judge_install(*b->pings[i], d_alpha[i], ok, st[0], s));
+    }
+    return FTCG_SUCCESS;
+    FTCG_API_END
+}
+
 ftcg_status_t ftcg_batch_profile(ftcg_batch_t batch, int32_t enable) {
     FTCG_API_BEGIN
     clear_error();

@@ -357,5 +357,11 @@ ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cud
 double es_beta(int w, double sigma);
 // weights.cu
 ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s);
+// judge.cu: exact Fejer sums at K samples, the verdict, and its installation
+ftcg_status_t judge_launch(const Plan& p, const double* d_alpha, int K, double* d_S, double* d_a,
+                           cudaStream_t s);
+bool judge_decide(const double* S, const double* a, int K, double max_rel_err, double* stats);
+ftcg_status_t judge_install(Plan& p, const double* d_alpha, bool accept, double med,
+                            cudaStream_t s);
 
 }  // namespace ftcg

@@ -15,9 +15,14 @@ namespace mma {
 #ifndef FTCG_MMA_MINB
 #define FTCG_MMA_MINB 3
 #endif
+// FTCG_MMA_UNROLL: 1 unrolls the loop over a staged batch's chunks
+#ifndef FTCG_MMA_UNROLL
+#define FTCG_MMA_UNROLL 1
+#endif
 constexpr int kThreads = FTCG_MMA_THREADS;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMinBlocks = FTCG_MMA_MINB;
+constexpr int kBatchUnroll = FTCG_MMA_UNROLL ? 4 : 1;
 // padding chunks after the last one (a read past the end stays inside the array)
 constexpr int kPrefetchChunks = 1;
 
@@ -164,7 +169,9 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                 if (lane < kStageChunks) nhdr = chdr[min(cbase + kStageChunks + lane, cb - 1)];
             }
             const int nk = min(kStageChunks, cb - cbase);
-            for (int k = 0; k < nk; ++k) {
+#pragma unroll kBatchUnroll
+            for (int k = 0; k < kStageChunks; ++k) {
+                if (k >= nk) break;
                 const uint32_t h = st_hdr[k];
                 const int cx = (int)(h & 0xffu), yb = (int)((h >> 8) & 0xffu);
                 if (cx != cur_cx || (yb != cur_yb && yb != cur_yb + 8)) {   // a new window

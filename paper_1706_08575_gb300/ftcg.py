@@ -89,6 +89,8 @@ SIGNATURES = [
     ("ftcg_adjoint_small_noalloc", _I32, [_VP, _VP, _VP, _I64, _I32, _D, _I32, _VP, _VP]),
     ("ftcg_cgls", _I32, [_VP, _VP, _VP, _I32, _D, _VP, _VP, _VP, _VP]),
     ("ftcg_band", _I32, [_VP, _I32, _VP, _VP]),
+    ("ftcg_weights_judge", _I32, [_VP, _VP, _I32, _D, _VP, _VP, _VP]),
+    ("ftcg_batch_weights_judge", _I32, [_VP, _VP, _I32, _D, _VP, _VP, _VP]),
     ("ftcg_destroy", _I32, [_VP]),
     ("ftcg_status_string", ctypes.c_char_p, [_I32]),
     ("ftcg_last_error", ctypes.c_char_p, []),
@@ -241,6 +243,19 @@ class Plan:
         _check(lib().ftcg_forward(self._h, _ptr(image.contiguous()), _ptr(out), _stream(stream)))
         return out
 
+    def judge_weights(self, alpha, K=256, max_rel_err=5e-4, stream=None):
+        """Judge predicted weights against exact sums at K samples: install the calibrated
+        predictions if their estimated error is within max_rel_err, else the exact weights.
+        Returns (accepted, {"median_ratio", "rms", "max"})."""
+        import torch
+        a = alpha.to(torch.float64).contiguous()
+        acc = ctypes.c_int32()
+        st = (ctypes.c_double * 3)()
+        _check(lib().ftcg_weights_judge(self._h, _ptr(a), int(K), float(max_rel_err),
+                                        ctypes.byref(acc), ctypes.cast(st, ctypes.c_void_p),
+                                        _stream(stream)))
+        return bool(acc.value), {"median_ratio": st[0], "rms": st[1], "max": st[2]}
+
     def band(self, r, stream=None):
         """Banded FTCG coefficients for band r (installed in the plan); returns them as an
         M x (2r - 1) complex128 tensor (row k: column k of C at rows k - r + 1 .. k + r - 1)."""
@@ -358,6 +373,17 @@ class Batch:
         self._alphas = [a.contiguous() for a in alphas]
         _check(lib().ftcg_batch_set_weights(self._h, _ptr_array(self._alphas), dt,
                                             _stream(stream)))
+
+    def judge_weights(self, alphas, K=256, max_rel_err=5e-4, stream=None):
+        """ftcg_batch_weights_judge: per ping (accepted, (median ratio, rms, max))."""
+        import torch
+        self._alphas = [a.to(torch.float64).contiguous() for a in alphas]
+        acc = (ctypes.c_int32 * self.n)()
+        st = (ctypes.c_double * (3 * self.n))()
+        _check(lib().ftcg_batch_weights_judge(self._h, _ptr_array(self._alphas), int(K),
+                                              float(max_rel_err), ctypes.cast(acc, ctypes.c_void_p),
+                                              ctypes.cast(st, ctypes.c_void_p), _stream(stream)))
+        return [(bool(acc[i]), tuple(st[3 * i:3 * i + 3])) for i in range(self.n)]
 
     def weights(self, stream=None):
         import torch
