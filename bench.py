@@ -212,6 +212,13 @@ def _oracle_spread_part(args):
     return O.spread(lam, c, N, sigma, w)
 
 
+def _oracle_adjoint_whole(args):
+    """One worker's whole oracle adjoint of one raster (pings are independent units)."""
+    lam, c, N, sigma, w = args
+    from oracle import ftcg_oracle as O
+    return O.adjoint(lam, c, N, sigma, w)
+
+
 def _pool_ready(_):
     import numpy  # noqa: F401
     from oracle import ftcg_oracle  # noqa: F401
@@ -250,6 +257,17 @@ class OracleRunner:
         for x in grids[1:]:
             g += x
         return g
+
+    def adjoint_many(self, items):
+        """Whole oracle adjoints of independent rasters [(lam, c, N, sigma, w)], one per worker
+        at a time; returns (images, seconds)."""
+        from oracle import ftcg_oracle as O
+        t0 = time.perf_counter()
+        if self.pool is None:
+            imgs = [O.adjoint(*it) for it in items]
+        else:
+            imgs = self.pool.map(_oracle_adjoint_whole, items, chunksize=1)
+        return imgs, time.perf_counter() - t0
 
     def adjoint(self, lam, c, N, sigma, w):
         """(image, spread seconds, FFT + crop + window division seconds)."""
@@ -315,16 +333,17 @@ def cpu_baselines(p, v, alpha, budget_s=12.0, extra=True):
             va, da = oracle_rate(allc, ps.lam, cp, ps.N, ps.sigma, ps.w, 4 * budget_s)
             out["precision"] = {"one_core": {"value": v1, "sample": d1},
                                 "all_cores": {"value": va, "sample": da}}
-            pings = [sasgen.batch_ping(b) for b in range(8)]
+            nb = max(8, host_cores())
+            pings = [sasgen.batch_ping(b) for b in range(nb)]
             tot = sum(q.M for q in pings)
+            items = [(q.lam, rng.standard_normal(q.M) + 1j * rng.standard_normal(q.M), q.N, 2.0,
+                      8) for q in pings]
             for key, runner in (("one_core", one), ("all_cores", allc)):
-                t = 0.0
-                for q in pings:
-                    cq = rng.standard_normal(q.M) + 1j * rng.standard_normal(q.M)
-                    _, ts, tr = runner.adjoint(q.lam, cq, q.N, 2.0, 8)
-                    t += ts + tr
-                out.setdefault("batch_8_pings", {})[key] = {
-                    "value": tot / t, "sample": f"pings 0-7 of the batch recipe ({tot} samples), whole"}
+                _, t = runner.adjoint_many(items)
+                out.setdefault("batch_pings", {})[key] = {
+                    "value": tot / t,
+                    "sample": f"pings 0-{nb - 1} of the batch recipe ({tot} samples), whole, "
+                              + ("one process" if key == "one_core" else "one ping per process")}
     finally:
         one.close()
         allc.close()
@@ -459,6 +478,21 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
         errs = [float(torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r))
                 for a, r in zip(imgs, plain_imgs)]
         tiles, entries, _ = b.info()
+    # learned + batched with the exact judge (K = 256 exact sums per ping; calibrated predictions
+    # kept where the estimated error is within 5e-4, the exact weights computed otherwise)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with F.Batch(lams, [p.N for p in pings], 2.0, 8) as b:
+        alpha = mlp.predict(F.features_batch(lams, auxs, concat=True))
+        verdict = b.judge_weights(list(torch.split(alpha, [p.M for p in pings])), K=256,
+                                  max_rel_err=5e-4)
+        jimgs = b.adjoint(vals)
+        torch.cuda.synchronize()
+        t_judged = time.perf_counter() - t0
+        jerrs = [float(torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r))
+                 for a, r in zip(jimgs, plain_imgs)]
+    accepted = sum(1 for ok, _ in verdict if ok)
+    est = [st[1] for _, st in verdict]
     large_eval = None
     if large is not None:
         p, lam, v = large
@@ -483,7 +517,16 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
     mlp.close()
     return {"pings": n_pings, "samples": M_tot,
             "plain_single_ping_fp32": {"value": M_tot / t_plain, "unit": UNIT, "s": t_plain},
-            "learned_batched": {"value": M_tot / t_learned, "unit": UNIT, "s": t_learned},
+            "learned_batched_judged": {
+                "value": M_tot / t_judged, "unit": UNIT, "s": t_judged,
+                "speedup_vs_plain": t_plain / t_judged,
+                "accepted_pings": accepted, "fallback_pings": n_pings - accepted,
+                "judge_estimated_weight_error": {"median": float(np.median(est)),
+                                                 "max": float(np.max(est))},
+                "image_rel_l2_vs_exact": {"median": float(np.median(jerrs)),
+                                          "max": float(np.max(jerrs))}},
+            "learned_batched": {"value": M_tot / t_learned, "unit": UNIT, "s": t_learned,
+                                "note": "predicted weights installed without the judge"},
             "speedup": t_plain / t_learned,
             "batched_adjoint_graph": {"value": M_tot / t_graph, "unit": UNIT, "ms": 1e3 * t_graph},
             "image_rel_l2_learned_vs_exact": {"median": float(np.median(errs)),
@@ -962,6 +1005,41 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_learned_kernels(args):
+    """Only the learned-weight kernels on the large ping, for profiling: the kNN features and one
+    network forward pass (random network parameters; the cost does not depend on them), repeated
+    `steps` times after `warmup`; prints their mean times as one JSON line (not the headline)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_1706_08575_gb300 as F
+    import sasgen
+    from paper_1706_08575_gb300 import learn
+    p = rank_ping(0)
+    lam = torch.from_numpy(p.lam).cuda()
+    aux = torch.from_numpy(learn.kr_feature(p.kr)).cuda()
+    mlp = F.Mlp(learn.init_params(0))
+    for _ in range(args.warmup):
+        mlp.predict(F.features(lam, aux))
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf = tp = 0.0
+    for _ in range(args.steps):
+        e[0].record()
+        feats = F.features(lam, aux)
+        e[1].record()
+        mlp.predict(feats)
+        e[2].record()
+        torch.cuda.synchronize()
+        tf += e[0].elapsed_time(e[1])
+        tp += e[1].elapsed_time(e[2])
+    mlp.close()
+    print(json.dumps({"learned_kernels": "large ping", "M": p.M, "features_ms": tf / args.steps,
+                      "predict_ms": tp / args.steps, "steps": args.steps}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -972,10 +1050,14 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--extras-pings", type=int, default=64)
+    ap.add_argument("--only", choices=["learned-kernels"], default=None,
+                    help="run one part alone for profiling (prints its own line, not the headline)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.only == "learned-kernels":
+        run_learned_kernels(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

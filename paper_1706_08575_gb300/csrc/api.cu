@@ -268,7 +268,8 @@ ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int
     p->last_stream = s;
     if (o.tile == 0 || o.layout == FTCG_LAYOUT_AUTO) {
         ftcg_status_t tst =
-            tune_tile(d_lambda, M, N, sigma, w, o, s, &p->opts.tile, &p->opts.layout);
+            tune_tile(d_lambda, M, N, sigma, w, o, s, &p->opts.tile, &p->opts.layout,
+                      &p->opts.spread_kernel);
         if (tst != FTCG_SUCCESS) {
             delete p;
             return tst;

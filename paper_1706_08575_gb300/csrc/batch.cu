@@ -169,8 +169,12 @@ struct TuneKey {
         return skern < o.skern;
     }
 };
+// the tuner's choice for a key: tile side, layout and spreading kernel
+struct TuneVal {
+    int T, layout, skern;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune;
+std::map<TuneKey, TuneVal> g_tune;
 
 int density_bucket(int64_t M, int G) {
     const double d = (double)M / ((double)G * G);
@@ -226,7 +230,8 @@ ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaSt
 }  // namespace
 
 ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
-                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out) {
+                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out,
+                        int* skern_out) {
     const int G = (int)std::llround(sigma * N);
     const TuneKey key{G, w, opts.precision, density_bucket(M, G), opts.tile, opts.layout,
                       opts.spread_kernel};
@@ -234,8 +239,9 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            *T_out = it->second.first;
-            *layout_out = it->second.second;
+            *T_out = it->second.T;
+            *layout_out = it->second.layout;
+            *skern_out = it->second.skern;
             return FTCG_SUCCESS;
         }
     }
@@ -244,9 +250,24 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
     if (opts.layout) layouts.push_back(opts.layout);
     else if (opts.spread_kernel == FTCG_SPREAD_TENSOR) layouts.push_back(FTCG_LAYOUT_HALO);
     else layouts = {FTCG_LAYOUT_DUPLICATE, FTCG_LAYOUT_HALO};
-    if (tiles.size() * layouts.size() == 1) {
+    // the kernels to try with a layout: both in the halo layout where the tensor-core kernel
+    // applies and the caller left the choice open, otherwise the caller's (or the only) one
+    MmaPoly poly;
+    double perr = 0;
+    const bool tensor_ok = w <= kMmaMaxW && mma_window_poly(w, es_beta(w, sigma), &poly, &perr);
+    auto kernels = [&](int layout) -> std::vector<int> {
+        if (layout == FTCG_LAYOUT_HALO && tensor_ok && opts.spread_kernel == FTCG_SPREAD_AUTO)
+            return {FTCG_SPREAD_TENSOR, FTCG_SPREAD_WINDOW};
+        if (layout == FTCG_LAYOUT_HALO && opts.spread_kernel == FTCG_SPREAD_TENSOR)
+            return {FTCG_SPREAD_TENSOR};
+        return {FTCG_SPREAD_WINDOW};
+    };
+    size_t ncand = 0;
+    for (int layout : layouts) ncand += tiles.size() * kernels(layout).size();
+    if (ncand == 1) {
         *T_out = tiles[0];
         *layout_out = layouts[0];
+        *skern_out = kernels(layouts[0])[0];
         return FTCG_SUCCESS;
     }
     DevBuf zbuf, gbuf;
@@ -255,39 +276,46 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
     FTCG_CK(cudaMalloc(&gbuf.p, (size_t)G * G * sizeof(float2)));
     const void* zeros = zbuf.p;
     float2* grid = reinterpret_cast<float2*>(gbuf.p);
-    int best_T = tiles[0], best_L = layouts[0];
+    TuneVal best{tiles[0], layouts[0], kernels(layouts[0])[0]};
     float best_ms = 1e30f;
     ftcg_status_t st = FTCG_SUCCESS;
     for (int T : tiles) {
         for (int layout : layouts) {
-            Plan* p = new (std::nothrow) Plan();
-            if (!p) { st = FTCG_ERR_OUT_OF_MEMORY; break; }
-            p->M = M; p->N = N; p->G = G; p->w = w; p->sigma = sigma;
-            p->opts = opts;
-            p->opts.tile = T;
-            p->opts.layout = layout;
-            p->win = Window{w, es_beta(w, sigma)};
-            st = make_plan(p, d_lambda, s, false);
-            float ms = 1e30f;
-            if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC)
-                st = time_spread(*p, zeros, grid, s, &ms);
-            release_plan(p);
-            if (st != FTCG_SUCCESS) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_T = T;
-                best_L = layout;
+            for (int kern : kernels(layout)) {
+                Plan* p = new (std::nothrow) Plan();
+                if (!p) {
+                    st = FTCG_ERR_OUT_OF_MEMORY;
+                    break;
+                }
+                p->M = M; p->N = N; p->G = G; p->w = w; p->sigma = sigma;
+                p->opts = opts;
+                p->opts.tile = T;
+                p->opts.layout = layout;
+                p->opts.spread_kernel = kern;
+                p->win = Window{w, es_beta(w, sigma)};
+                st = make_plan(p, d_lambda, s, false);
+                float ms = 1e30f;
+                if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC)
+                    st = time_spread(*p, zeros, grid, s, &ms);
+                release_plan(p);
+                if (st != FTCG_SUCCESS) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = TuneVal{T, layout, kern};
+                }
             }
+            if (st != FTCG_SUCCESS) break;
         }
         if (st != FTCG_SUCCESS) break;
     }
     if (st != FTCG_SUCCESS) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = {best_T, best_L};
+        g_tune[key] = best;
     }
-    *T_out = best_T;
-    *layout_out = best_L;
+    *T_out = best.T;
+    *layout_out = best.layout;
+    *skern_out = best.skern;
     return FTCG_SUCCESS;
 }
 
@@ -576,9 +604,10 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
     for (int i = 0; i < b.n; ++i) {
         const int G = (int)std::llround(b.sigma * N[i]);
         Gs[i] = G;
-        int T = b.opts.tile, layout = b.opts.layout;
+        int T = b.opts.tile, layout = b.opts.layout, skern = b.opts.spread_kernel;
         if (T == 0 || layout == 0)
-            FTCG_TRY(tune_tile(d_lambda[i], M[i], N[i], b.sigma, b.w, b.opts, s, &T, &layout));
+            FTCG_TRY(tune_tile(d_lambda[i], M[i], N[i], b.sigma, b.w, b.opts, s, &T, &layout,
+                               &skern));
         Plan* p = new (std::nothrow) Plan();
         if (!p) {
             set_error("ftcg_plan_batch: host allocation failed");
@@ -588,6 +617,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         p->opts = b.opts;
         p->opts.tile = T;
         p->opts.layout = layout;
+        p->opts.spread_kernel = skern;
         p->win = Window{b.w, es_beta(b.w, b.sigma)};
         b.pings.push_back(p);
     }
@@ -1085,7 +1115,7 @@ ftcg_status_t ftcg_tuner_save(const char* path) {
         set_error("ftcg_tuner_save: path is NULL");
         return FTCG_ERR_INVALID_VALUE;
     }
-    std::map<TuneKey, std::pair<int, int>> snap;
+    std::map<TuneKey, TuneVal> snap;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         snap = g_tune;
@@ -1101,9 +1131,9 @@ ftcg_status_t ftcg_tuner_save(const char* path) {
         std::fprintf(f,
                      "{\"G\": %d, \"w\": %d, \"precision\": %d, \"bucket\": %d, "
                      "\"tile_req\": %d, \"layout_req\": %d, \"spread_req\": %d, "
-                     "\"tile\": %d, \"layout\": %d}%s\n",
+                     "\"tile\": %d, \"layout\": %d, \"spread\": %d}%s\n",
                      e.first.G, e.first.w, e.first.prec, e.first.bucket, e.first.tile,
-                     e.first.layout, e.first.skern, e.second.first, e.second.second,
+                     e.first.layout, e.first.skern, e.second.T, e.second.layout, e.second.skern,
                      ++k < snap.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
@@ -1127,7 +1157,7 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
         set_error("ftcg_tuner_load: cannot open %s", path);
         return FTCG_ERR_INVALID_VALUE;
     }
-    std::vector<std::pair<TuneKey, std::pair<int, int>>> got;
+    std::vector<std::pair<TuneKey, TuneVal>> got;
     std::string line;
     bool header = false, bad = false;
     int lineno = 0;
@@ -1139,8 +1169,9 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
         if (line.find("\"ftcg_tuner\": 1") != std::string::npos) header = true;
         if (line.find("\"G\":") == std::string::npos) continue;
         TuneKey k{};
-        int tile = 0, layout = 0;
+        int tile = 0, layout = 0, spread = FTCG_SPREAD_AUTO;
         if (!json_int(line, "spread_req", &k.skern)) k.skern = FTCG_SPREAD_AUTO;   // older files
+        if (!json_int(line, "spread", &spread)) spread = FTCG_SPREAD_AUTO;
         const bool ok = json_int(line, "G", &k.G) && json_int(line, "w", &k.w) &&
                         json_int(line, "precision", &k.prec) &&
                         json_int(line, "bucket", &k.bucket) &&
@@ -1153,6 +1184,9 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
                            (k.layout >= FTCG_LAYOUT_AUTO && k.layout <= FTCG_LAYOUT_HALO) &&
                            (k.skern >= FTCG_SPREAD_AUTO && k.skern <= FTCG_SPREAD_TENSOR) &&
                            (k.skern != FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
+                           (spread >= FTCG_SPREAD_AUTO && spread <= FTCG_SPREAD_TENSOR) &&
+                           (spread != FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
+                           (k.skern == FTCG_SPREAD_AUTO || spread == k.skern) &&
                            (tile == 32 || tile == 64) &&
                            (layout == FTCG_LAYOUT_DUPLICATE || layout == FTCG_LAYOUT_HALO) &&
                            (k.tile == 0 || k.tile == tile) && (k.layout == 0 || k.layout == layout);
@@ -1161,7 +1195,7 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
             bad = true;
             break;
         }
-        got.push_back({k, {tile, layout}});
+        got.push_back({k, TuneVal{tile, layout, spread}});
     }
     std::fclose(f);
     if (bad) return FTCG_ERR_INVALID_VALUE;

@@ -229,9 +229,11 @@ constexpr int kMaxProfiled = 1024;
 // api.cu: argument checks of ftcg_plan (fills the default tile) and plan construction.
 ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, ftcg_opts_t* o);
 ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool own_grid);
-// batch.cu: the tile-side autotuner (cached per grid side, w, precision and density bucket).
+// batch.cu: the autotuner of tile side, layout and spreading kernel (cached per grid side, w,
+// precision and density bucket).
 ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
-                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out);
+                        const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out,
+                        int* skern_out);
 void release_plan(Plan* p);
 
 // ---------------------------------------------------------------------------------------------

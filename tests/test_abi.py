@@ -128,7 +128,9 @@ def test_tuner_file_round_trip(L, tmp_path):
                {"G": 512, "w": 6, "precision": 1, "bucket": 1, "tile_req": 64, "layout_req": 0,
                 "tile": 64, "layout": 1},
                {"G": 1024, "w": 8, "precision": 0, "bucket": -1, "tile_req": 0, "layout_req": 0,
-                "spread_req": 2, "tile": 64, "layout": 2}]
+                "spread_req": 2, "tile": 64, "layout": 2, "spread": 2},
+               {"G": 8192, "w": 8, "precision": 0, "bucket": -8, "tile_req": 0, "layout_req": 0,
+                "spread_req": 0, "tile": 32, "layout": 2, "spread": 1}]
     src = tmp_path / "tuner.json"
     src.write_text('{"ftcg_tuner": 1, "entries": [\n' +
                    ",\n".join(json.dumps(e) for e in entries) + "\n]}\n")
@@ -138,7 +140,8 @@ def test_tuner_file_round_trip(L, tmp_path):
     saved = json.loads(out.read_text())
     assert saved["ftcg_tuner"] == 1
     for e in entries:               # files written before the spreading-kernel choice load as 0
-        assert dict(e, spread_req=e.get("spread_req", 0)) in saved["entries"]
+        assert dict(e, spread_req=e.get("spread_req", 0),
+                    spread=e.get("spread", e.get("spread_req", 0))) in saved["entries"]
     bad = tmp_path / "bad.json"
     bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[0], G=1000, tile=48))
                    + "\n]}\n")
