@@ -1050,13 +1050,21 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--extras-pings", type=int, default=64)
-    ap.add_argument("--only", choices=["learned-kernels"], default=None,
+    ap.add_argument("--only", choices=["learned-kernels", "batch"], default=None,
                     help="run one part alone for profiling (prints its own line, not the headline)")
+    ap.add_argument("--batch-pings", type=int, default=512)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
     if args.only == "learned-kernels":
         run_learned_kernels(args)
+    elif args.only == "batch":
+        import torch
+        import __graft_entry__ as ge
+        ge.build()
+        print(json.dumps({"batch": batch_full_extra(torch.device("cuda", 0),
+                                                    n_pings=args.batch_pings,
+                                                    reps=args.steps)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
