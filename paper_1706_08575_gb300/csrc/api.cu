@@ -547,6 +547,11 @@ const char* ftcg_status_string(ftcg_status_t s) {
 
 const char* ftcg_last_error(void) { return g_err; }
 
-const char* ftcg_version(void) { return "ftcg 0.1 sm_103a"; }
+// FTCG_SOURCE_HASH: a hash of the sources the library was built from (set by the build script;
+// "unknown" when built otherwise), so that a library can be matched to its sources.
+#ifndef FTCG_SOURCE_HASH
+#define FTCG_SOURCE_HASH "unknown"
+#endif
+const char* ftcg_version(void) { return "ftcg 0.2 sm_103a ftcg-src-hash:" FTCG_SOURCE_HASH; }
 
 }  // extern "C"

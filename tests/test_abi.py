@@ -156,3 +156,15 @@ def test_tuner_file_round_trip(L, tmp_path):
     assert L.ftcg_tuner_load(str(tmp_path / "absent.json").encode()) == 1
     ftcg.tuner_save(out)
     assert all(e["G"] != 1000 and e["G"] != 4096 for e in json.loads(out.read_text())["entries"])
+
+
+def test_library_carries_its_source_hash():
+    """The built library names the sources it was built from; build() rebuilds when they differ
+    (a library left over from other sources is never reused)."""
+    from paper_1706_08575_gb300 import build as B
+    from paper_1706_08575_gb300 import ftcg
+    h = B.source_hash()
+    assert len(h) == 16
+    assert B.built_hash() == h
+    assert ftcg.lib().ftcg_version().decode().endswith("ftcg-src-hash:" + h)
+    assert B.up_to_date()

@@ -125,3 +125,21 @@ def test_band_limits_and_weights_replace_the_band(F):
         with pytest.raises(F.FtcgError) as ei:
             p.band(2)
         assert ei.value.status == 4
+
+
+def test_band_at_the_tiny_configuration(F):
+    """The tiny configuration (4096 polar samples, N = 64) at r = ceil(log(2N + 1)) = 5, the band
+    the paper suggests: coefficients against the oracle's banded least squares, and the image."""
+    p = sasgen.tiny()
+    v = sasgen.values_for(p).astype(np.complex64)
+    r = int(np.ceil(np.log(2 * p.N + 1)))
+    assert r == 5
+    with F.Plan(dev(p.lam), p.N, p.sigma, p.w) as pl:
+        band = pl.band(r).cpu().numpy()
+        img = pl.adjoint(dev(v)).cpu().numpy()
+    T = B.gram_matrix(p.lam, p.N)
+    ref = B.banded_c(T, r)
+    C = dense_c(band, r)
+    assert np.max(np.abs(C - ref)) < 1e-9 * np.max(np.abs(ref))
+    ref_img = B.ftcg_image(p.lam, v.astype(np.complex128), p.N, p.sigma, p.w, ref)
+    assert O.rel_l2(img, ref_img) < 1e-5
