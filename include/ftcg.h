@@ -67,12 +67,14 @@ enum { FTCG_PREC_FP32 = 0, FTCG_PREC_BF16 = 1 };
  * AUTO lets the autotuner choose, together with the tile side. */
 enum { FTCG_LAYOUT_AUTO = 0, FTCG_LAYOUT_DUPLICATE = 1, FTCG_LAYOUT_HALO = 2 };
 /* Which spreading kernel a plan uses (same result within the FP32 bound):
- *   AUTO:   the tensor-core kernel where it applies (halo layout, w <= 8 and a window whose
- *           per-tap degree-7 polynomials are within 1e-6 of it: w >= 7 for any sigma >= 1.25,
- *           w = 6 at sigma = 2), otherwise the register-window kernel.
- *   WINDOW: the register-window kernel (FP32 multiply-adds into a rolling window of rows).
- *   TENSOR: the tensor-core kernel (per column bin, 8 samples x a 16-row window per
- *           mma.sync.m16n8k8 in split TF32); NOT_SUPPORTED where it does not apply. */
+ *   AUTO:    where the autotuner runs (tile side or layout left to it), it times the kernels
+ *            that apply and keeps the faster; with the tile side and layout given, the
+ *            tensor-core kernel where it applies, otherwise the register-window kernel.
+ *   WINDOW:  the register-window kernel (FP32 multiply-adds into a rolling window of rows).
+ *   TENSOR:  the tensor-core kernel (per column bin, 8 samples x a 16-row window per
+ *            mma.sync.m16n8k8 in split TF32); it applies in the halo layout with w <= 8 and a
+ *            window whose per-tap degree-7 polynomials are within 1e-6 of it (w >= 7 for any
+ *            sigma >= 1.25, w = 6 at sigma = 2); NOT_SUPPORTED elsewhere. */
 enum { FTCG_SPREAD_AUTO = 0, FTCG_SPREAD_WINDOW = 1, FTCG_SPREAD_TENSOR = 2 };
 
 typedef struct {
@@ -335,9 +337,11 @@ ftcg_status_t ftcg_mlp_destroy(ftcg_mlp_t mlp);
  * ftcg_weights_judge -- the exact judge and fallback of predicted weights (the exact FTCG
  * construction of Eq. difopt at r = 1 keeps the last word). For K samples spread evenly over the
  * acquisition order it sums S_k = sum_j F_N(lambda_jx - lambda_kx) F_N(lambda_jy - lambda_ky)
- * directly over all M samples (FP32 Fejer terms of exactly reduced arguments, FP64 sums) and
- * forms the ratios alpha_pred_k S_k. Their median is a calibration factor; the rms of the
- * calibrated ratios around 1 estimates the relative weight error (the image error follows it).
+ * directly over all M samples (FP32 Fejer terms of lags reduced exactly modulo N, compensated
+ * FP32 sums per thread combined in FP64; about 1e-7 relative) and forms the ratios
+ * alpha_pred_k S_k. Their median is a calibration factor; the rms of the calibrated ratios around
+ * 1 estimates the relative weight error (the image error follows it). Samples with a non-finite
+ * coordinate are left out of the sums and of the ratios.
  * If that rms is at most max_rel_err the calibrated weights alpha_pred / median are installed
  * (*h_accepted = 1); otherwise the exact weights are computed (ftcg_weights) and installed
  * (*h_accepted = 0). h_stats: NULL or 3 doubles {median ratio, rms, max |calibrated error|}.

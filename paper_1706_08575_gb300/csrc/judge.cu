@@ -8,13 +8,21 @@
 // the image error follows. Within the caller's bound the calibrated predictions are installed;
 // otherwise the exact FP64 weights (ftcg_weights) are computed and installed instead.
 //
-// Each Fejer term is evaluated in FP32 after exact FP64 reductions of its arguments (the lag
-// modulo N, then its fractional part for sin(pi d)), so every sine argument lies in
-// [-1/2, 1/2] and the term carries a relative error of a few FP32 ulps; terms are summed in FP64.
-// That is ample for judging errors of 1e-4 and above.
+// The sums are the judge's whole cost (K M terms), so they avoid FP64 arithmetic, which runs at a
+// small fraction of the FP32 rate here. Each coordinate is first reduced once, in FP64, modulo N
+// (F_N has period N) and split into an integer n and a fraction f in [-1/2, 1/2], rounded to FP32.
+// A lag d = lambda_j - lambda_k is then the exact integer n_j - n_k, wrapped into [-N/2, N/2], plus
+// the FP32 difference f_j - f_k: its absolute error is a few 1e-8 at any distance, and F_N is
+// smooth on that scale (near d = 0 both sines of the quotient carry the same relative error).
+// sin(pi d) = +-sin(pi (f_j - f_k)) since the integer part only flips the sign; the term is then
+// (sin(pi df) / (N sin(pi d / N)))^2 in FP32, a few ulps. Each thread sums its terms in FP32 with
+// Kahan compensation; the threads' sums are combined in FP64. Samples with a non-finite or huge
+// coordinate are left out of the sums (as the gridding leaves them out), and a judged sample of
+// that kind gets S = NaN, which the verdict skips.
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "ftcg_internal.cuh"
@@ -24,31 +32,74 @@ namespace ftcg {
 namespace {
 
 constexpr int kJudgeThreads = 256;
+constexpr int kJudgeSkip = INT32_MIN;      // n of a sample left out of the sums
 
-__device__ __forceinline__ float fejer32(double d, int N) {
-    const double dr = d - N * rint(d / N);             // exact: |dr| <= N/2, F_N is N-periodic
-    if (dr == 0.0) return 1.0f;
-    const float sf = sinpif((float)(dr - rint(dr)));   // sin(pi d) up to sign
-    const float sq = sinpif((float)(dr / N));          // |dr / N| <= 1/2
+// Per sample {n_x, n_y, f_x, f_y} (the fractions as FP32 bits): lambda mod N = n + f.
+__global__ void k_judge_prep(const double* __restrict__ lam, int64_t M, int N,
+                             int4* __restrict__ pts) {
+    const double invN = 1.0 / N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int n[2];
+        float f[2];
+        bool ok = true;
+        for (int a = 0; a < 2; ++a) {
+            const double x = lam[2 * i + a];
+            ok = ok && isfinite(x) && fabs(x) < 1099511627776.0;     // 2^40
+            const double r = ok ? x - N * rint(x * invN) : 0.0;      // |r| <= N/2 (+ rounding)
+            const double q = rint(r);
+            n[a] = (int)q;
+            f[a] = (float)(r - q);
+        }
+        pts[i] = ok ? make_int4(n[0], n[1], __float_as_int(f[0]), __float_as_int(f[1]))
+                    : make_int4(kJudgeSkip, kJudgeSkip, 0, 0);
+    }
+}
+
+// F_N of one axis for the lag dn + df (dn an integer in [-N, N], |df| < 1).
+__device__ __forceinline__ float fejer_axis(int dn, float df, int N, float invN) {
+    if (dn > N / 2) dn -= N;
+    else if (dn < -(N / 2)) dn += N;
+    float dr = (float)dn + df;
+    if (dr > 0.5f * N) dr -= N;                          // exact (Sterbenz); now |dr| <= N/2
+    else if (dr < -0.5f * N) dr += N;
+    if (dr == 0.0f) return 1.0f;
+    const float sf = sinpif(df);                         // sin(pi d) up to sign
+    const float sq = sinpif(dr * invN);
     const float r = sf / ((float)N * sq);
     return r * r;
 }
 
-__global__ void k_fejer_sums(const double* __restrict__ lam, int64_t M, int N, int K,
-                             double* __restrict__ S) {
+__global__ void __launch_bounds__(kJudgeThreads)
+    k_fejer_sums(const int4* __restrict__ pts, int64_t M, int N, int K, double* __restrict__ S) {
     const int64_t k = ((int64_t)blockIdx.x * 2 + 1) * M / (2 * (int64_t)K);
-    const double kx = lam[2 * k], ky = lam[2 * k + 1];
-    double acc = 0.0;
-    for (int64_t j = threadIdx.x; j < M; j += kJudgeThreads)
-        acc += (double)(fejer32(lam[2 * j] - kx, N) * fejer32(lam[2 * j + 1] - ky, N));
+    const int4 pk = pts[k];
+    if (pk.x == kJudgeSkip) {
+        if (threadIdx.x == 0) S[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    const float fkx = __int_as_float(pk.z), fky = __int_as_float(pk.w);
+    const float invN = 1.0f / N;
+    float s = 0.0f, c = 0.0f;                            // Kahan sum and its compensation
+    for (int64_t j = threadIdx.x; j < M; j += kJudgeThreads) {
+        const int4 q = pts[j];
+        if (q.x == kJudgeSkip) continue;
+        const float t = fejer_axis(q.x - pk.x, __int_as_float(q.z) - fkx, N, invN) *
+                        fejer_axis(q.y - pk.y, __int_as_float(q.w) - fky, N, invN);
+        const float y = t - c;
+        const float u = s + y;
+        c = (u - s) - y;
+        s = u;
+    }
+    double acc = (double)s - (double)c;
     __shared__ double part[kJudgeThreads / 32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kJudgeThreads / 32; ++w) s += part[w];
-        S[blockIdx.x] = s;
+        double t = 0.0;
+        for (int w = 0; w < kJudgeThreads / 32; ++w) t += part[w];
+        S[blockIdx.x] = t;
     }
 }
 
@@ -71,27 +122,42 @@ __global__ void k_scale_alpha(const double* __restrict__ a, int64_t M, double s,
 // at the same samples.
 ftcg_status_t judge_launch(const Plan& p, const double* d_alpha, int K, double* d_S,
                            double* d_a, cudaStream_t s) {
-    k_fejer_sums<<<K, kJudgeThreads, 0, s>>>(p.lambda, p.M, p.N, K, d_S);
+    int4* pts = nullptr;
+    FTCG_CK(pool_malloc(&pts, (size_t)p.M * sizeof(int4), s));
+    const int64_t b = std::min<int64_t>((p.M + 255) / 256, 152 * 8);
+    k_judge_prep<<<(unsigned)std::max<int64_t>(1, b), 256, 0, s>>>(p.lambda, p.M, p.N, pts);
+    k_fejer_sums<<<K, kJudgeThreads, 0, s>>>(pts, p.M, p.N, K, d_S);
     k_gather_alpha<<<(K + 127) / 128, 128, 0, s>>>(d_alpha, p.M, K, d_a);
-    FTCG_CK(cudaGetLastError());
+    const cudaError_t launched = cudaGetLastError();
+    FTCG_CK(pool_free(pts, s));
+    FTCG_CK(launched);
     return FTCG_SUCCESS;
 }
 
 // Decide from the host copies of S and alpha_pred: stats = {median ratio, rms and max of the
 // calibrated relative errors}; true when the rms is within max_rel_err.
 bool judge_decide(const double* S, const double* a, int K, double max_rel_err, double* stats) {
-    std::vector<double> r(K);
-    for (int i = 0; i < K; ++i) r[i] = a[i] * S[i];           // alpha_pred / alpha_exact
+    std::vector<double> r;
+    r.reserve(K);
+    for (int i = 0; i < K; ++i) {
+        const double q = a[i] * S[i];                         // alpha_pred / alpha_exact
+        if (std::isfinite(q)) r.push_back(q);                 // samples left out: S = NaN
+    }
+    if (r.empty()) {
+        stats[0] = stats[1] = stats[2] = std::nan("");
+        return false;
+    }
+    const size_t n = r.size();
     std::vector<double> sorted(r);
     std::sort(sorted.begin(), sorted.end());
-    const double med = K % 2 ? sorted[K / 2] : 0.5 * (sorted[K / 2 - 1] + sorted[K / 2]);
+    const double med = n % 2 ? sorted[n / 2] : 0.5 * (sorted[n / 2 - 1] + sorted[n / 2]);
     double ss = 0.0, mx = 0.0;
-    for (int i = 0; i < K; ++i) {
-        const double e = r[i] / med - 1.0;
+    for (double q : r) {
+        const double e = q / med - 1.0;
         ss += e * e;
         mx = std::max(mx, std::fabs(e));
     }
-    const double rms = std::sqrt(ss / K);
+    const double rms = std::sqrt(ss / n);
     stats[0] = med;
     stats[1] = rms;
     stats[2] = mx;
@@ -137,7 +203,11 @@ extern "C" ftcg_status_t ftcg_weights_judge(ftcg_plan_t plan, const double* d_al
     double *dS = nullptr, *da = nullptr;
     FTCG_CK(pool_malloc(&dS, (size_t)2 * K * sizeof(double), s));
     da = dS + K;
-    FTCG_TRY(judge_launch(*p, d_alpha, K, dS, da, s));
+    const ftcg_status_t launched = judge_launch(*p, d_alpha, K, dS, da, s);
+    if (launched != FTCG_SUCCESS) {
+        pool_free(dS, s);
+        return launched;
+    }
     std::vector<double> h(2 * (size_t)K);
     FTCG_CK(cudaMemcpyAsync(h.data(), dS, 2 * (size_t)K * sizeof(double), cudaMemcpyDeviceToHost,
                             s));

@@ -58,6 +58,29 @@ def test_batch_vs_oracle_and_single(F, layout):
         assert O.rel_l2(img, single) < 1e-6
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["window", "tensor"])
+def test_batch_each_spread_kernel(F, kernel):
+    """The persistent batched launch with each spreading kernel forced (halo layout), over pings
+    of both FFT paths (cuFFT below G = 256, shared-memory passes from 256) and an empty ping,
+    against the oracle."""
+    rng = np.random.default_rng(20 + kernel)
+    cases = []
+    for i, N in enumerate([32, 128, 64, 256, 48]):
+        M = 0 if i == 2 else int(rng.integers(800, 6000))
+        lam, v = sasgen.random_case(300 + 10 * kernel + i, M, N, 2.0, 8, spread=1.2 * N)
+        cases.append((lam, v.astype(np.complex64), rng.uniform(0.3, 1.7, M), N))
+    with F.Batch([dev(c[0]) for c in cases], [c[3] for c in cases], 2.0, 8,
+                 layout=F.LAYOUT_HALO, spread_kernel=kernel) as b:
+        b.set_weights([dev(c[2]) for c in cases])
+        imgs = [x.cpu().numpy() for x in b.adjoint([dev(c[1]) for c in cases])]
+    for (lam, v, a, N), img in zip(cases, imgs):
+        if lam.shape[0] == 0:
+            assert np.count_nonzero(img) == 0
+            continue
+        ref = O.adjoint(lam, a.astype(np.float32) * v.astype(np.complex128), N, 2.0, 8)
+        assert O.rel_l2(img, ref) < TOL
+
+
 def test_batch_graph_replay(F):
     import torch
     cases = [c for c in small_batch(2) if c[0].shape[0] > 0]

@@ -78,3 +78,20 @@ def test_batch_judge_per_ping(F):
         ref = O.adjoint(q.lam, a.cpu().numpy().astype(np.float32) *
                         x.cpu().numpy().astype(np.complex128), q.N, 2.0, 8)
         assert O.rel_l2(img, ref) < 1e-5
+
+
+
+def test_judge_leaves_out_nonfinite_samples(F):
+    """A raster holding non-finite coordinates (the gridding drops them, their exact weight is 0):
+    the judge leaves them out of the sums and of the ratios, so a scaled exact prediction is still
+    accepted with its factor, and its sums still match the brute-force sums over the finite
+    samples."""
+    lam, _ = sasgen.random_case(8, 3000, 48, 2.0, 8, 40)
+    lam = lam.copy()
+    bad = [5, 1500, 2999]
+    lam[bad] = [[np.nan, 0.0], [0.0, np.inf], [np.nan, np.nan]]
+    with F.Plan(dev(lam), 48, 2.0, 8, allow_numeric=True) as p:
+        a = p.weights()
+        assert np.all(a.cpu().numpy()[bad] == 0)
+        ok, st = p.judge_weights(a * 0.7, K=3000, max_rel_err=5e-4)
+    assert ok and abs(st["median_ratio"] - 0.7) < 1e-6 * 0.7 and st["rms"] < 1e-6
