@@ -211,21 +211,24 @@ ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls);
  *
  * ftcg_plan_batch -- plan n pings. d_lambda, M, N: host arrays of n entries (d_lambda[i] a device
  * M[i] x 2 float64 array, read during the call); sigma, w, opts shared, with the checks of
- * ftcg_plan per ping. opts->tile = 0 lets the built-in autotuner pick the tile side of each ping:
- * it times both tile sides once per (grid side, w, precision, half-octave bucket of samples per
- * grid cell) and keeps the faster for the life of the process. After the tuning (ping after ping,
- * on `stream`), the pings' plans are built by up to four host threads, each on its own stream
- * that waits for `stream` first. A ping whose coordinates are not all finite drops those samples
- * (as ftcg_plan does) and the batch is still built. Synchronises.
+ * ftcg_plan per ping. opts->tile = 0 or opts->layout = 0 lets the built-in autotuner pick the
+ * tile side, layout and spreading kernel of each ping: the pings are grouped by (grid side, w,
+ * precision, half-octave bucket of samples per grid cell), and for every group not decided yet
+ * each candidate is timed as the batched spreading launch over up to 16 of the group's pings;
+ * the fastest is kept for the life of the process. After the tuning (on `stream`), the pings'
+ * plans are built by up to four host threads, each on its own stream that waits for `stream`
+ * first. A ping whose coordinates are not all finite drops those samples (as ftcg_plan does) and
+ * the batch is still built. Synchronises.
  */
 ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const* d_lambda,
                               const int64_t* M, const int32_t* N, double sigma, int32_t w,
                               const ftcg_opts_t* opts, ftcg_stream_t stream);
 
 /*
- * The tile autotuner's choices as a small JSON file (one entry per line: grid side, w, precision,
- * density bucket, the requested tile and layout, and the chosen tile side and layout), so that a
- * later process can reuse them instead of timing trial launches again. ftcg_tuner_save writes the
+ * The autotuner's choices as a small JSON file (one entry per line: grid side, w, precision,
+ * density bucket, the requested tile, layout and spreading kernel, whether the choice was timed
+ * for single plans (batch 0) or batches (batch 1), and the chosen tile side, layout and kernel),
+ * so that a later process can reuse them instead of timing trial launches again. ftcg_tuner_save writes the
  * choices made or loaded so far in this process; ftcg_tuner_load adds a file's entries (they
  * replace choices with the same key), after checking every entry (nothing is added when one is
  * invalid: FTCG_ERR_INVALID_VALUE naming the line). Host only: no device work, no stream.

@@ -7,9 +7,11 @@
 // G follows, then one window-division + crop launch for all pings. The whole sequence is
 // stream-ordered with no host synchronisation and can be captured once in a CUDA graph.
 //
-// The tile side of each ping is chosen by a small autotuner: for every (G, w, precision,
-// half-octave bucket of samples per cell) it times both tile sides on the first ping that needs
-// it and keeps the faster for the life of the process.
+// The tile side, layout and spreading kernel of each ping are chosen by a small autotuner: for
+// every (G, w, precision, half-octave bucket of samples per cell) it times the candidates and
+// keeps the fastest for the life of the process. A single plan is timed on its own launch; the
+// pings of a batch are timed as a batched launch over up to 16 pings of the same class, since a
+// batch pays per tile and per column bin, not for how one small ping fills the GPU.
 
 #include <algorithm>
 #include <atomic>
@@ -159,6 +161,7 @@ size_t spread_smem() {
 struct TuneKey {
     int G, w, prec, bucket, tile, layout;   // tile / layout: the caller's fixed choices (0 = free)
     int skern;                              // the caller's spreading-kernel choice
+    int batch;                              // 1: chosen for pings of a batch (timed batched)
     bool operator<(const TuneKey& o) const {
         if (G != o.G) return G < o.G;
         if (w != o.w) return w < o.w;
@@ -166,7 +169,8 @@ struct TuneKey {
         if (bucket != o.bucket) return bucket < o.bucket;
         if (tile != o.tile) return tile < o.tile;
         if (layout != o.layout) return layout < o.layout;
-        return skern < o.skern;
+        if (skern != o.skern) return skern < o.skern;
+        return batch < o.batch;
     }
 };
 // the tuner's choice for a key: tile side, layout and spreading kernel
@@ -229,12 +233,39 @@ ftcg_status_t time_spread(const Plan& p, const void* zeros, float2* grid, cudaSt
 
 }  // namespace
 
+// The (tile side, layout, spreading kernel) candidates the tuner times for the caller's options:
+// in the halo layout both kernels where the tensor-core kernel applies and the caller left the
+// choice open, otherwise the caller's (or the only) kernel.
+std::vector<TuneVal> tune_candidates(int w, double sigma, const ftcg_opts_t& opts) {
+    std::vector<int> tiles, layouts;
+    if (opts.tile) tiles.push_back(opts.tile); else tiles = {32, 64};
+    if (opts.layout) layouts.push_back(opts.layout);
+    else if (opts.spread_kernel == FTCG_SPREAD_TENSOR) layouts.push_back(FTCG_LAYOUT_HALO);
+    else layouts = {FTCG_LAYOUT_DUPLICATE, FTCG_LAYOUT_HALO};
+    MmaPoly poly;
+    double perr = 0;
+    const bool tensor_ok = w <= kMmaMaxW && mma_window_poly(w, es_beta(w, sigma), &poly, &perr);
+    std::vector<TuneVal> out;
+    for (int T : tiles)
+        for (int layout : layouts) {
+            if (layout == FTCG_LAYOUT_HALO && tensor_ok && opts.spread_kernel == FTCG_SPREAD_AUTO) {
+                out.push_back({T, layout, FTCG_SPREAD_TENSOR});
+                out.push_back({T, layout, FTCG_SPREAD_WINDOW});
+            } else if (layout == FTCG_LAYOUT_HALO && opts.spread_kernel == FTCG_SPREAD_TENSOR) {
+                out.push_back({T, layout, FTCG_SPREAD_TENSOR});
+            } else {
+                out.push_back({T, layout, FTCG_SPREAD_WINDOW});
+            }
+        }
+    return out;
+}
+
 ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, int w,
                         const ftcg_opts_t& opts, cudaStream_t s, int* T_out, int* layout_out,
                         int* skern_out) {
     const int G = (int)std::llround(sigma * N);
     const TuneKey key{G, w, opts.precision, density_bucket(M, G), opts.tile, opts.layout,
-                      opts.spread_kernel};
+                      opts.spread_kernel, 0};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -245,29 +276,11 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
             return FTCG_SUCCESS;
         }
     }
-    std::vector<int> tiles, layouts;
-    if (opts.tile) tiles.push_back(opts.tile); else tiles = {32, 64};
-    if (opts.layout) layouts.push_back(opts.layout);
-    else if (opts.spread_kernel == FTCG_SPREAD_TENSOR) layouts.push_back(FTCG_LAYOUT_HALO);
-    else layouts = {FTCG_LAYOUT_DUPLICATE, FTCG_LAYOUT_HALO};
-    // the kernels to try with a layout: both in the halo layout where the tensor-core kernel
-    // applies and the caller left the choice open, otherwise the caller's (or the only) one
-    MmaPoly poly;
-    double perr = 0;
-    const bool tensor_ok = w <= kMmaMaxW && mma_window_poly(w, es_beta(w, sigma), &poly, &perr);
-    auto kernels = [&](int layout) -> std::vector<int> {
-        if (layout == FTCG_LAYOUT_HALO && tensor_ok && opts.spread_kernel == FTCG_SPREAD_AUTO)
-            return {FTCG_SPREAD_TENSOR, FTCG_SPREAD_WINDOW};
-        if (layout == FTCG_LAYOUT_HALO && opts.spread_kernel == FTCG_SPREAD_TENSOR)
-            return {FTCG_SPREAD_TENSOR};
-        return {FTCG_SPREAD_WINDOW};
-    };
-    size_t ncand = 0;
-    for (int layout : layouts) ncand += tiles.size() * kernels(layout).size();
-    if (ncand == 1) {
-        *T_out = tiles[0];
-        *layout_out = layouts[0];
-        *skern_out = kernels(layouts[0])[0];
+    const std::vector<TuneVal> cand = tune_candidates(w, sigma, opts);
+    if (cand.size() == 1) {
+        *T_out = cand[0].T;
+        *layout_out = cand[0].layout;
+        *skern_out = cand[0].skern;
         return FTCG_SUCCESS;
     }
     DevBuf zbuf, gbuf;
@@ -276,39 +289,30 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
     FTCG_CK(cudaMalloc(&gbuf.p, (size_t)G * G * sizeof(float2)));
     const void* zeros = zbuf.p;
     float2* grid = reinterpret_cast<float2*>(gbuf.p);
-    TuneVal best{tiles[0], layouts[0], kernels(layouts[0])[0]};
+    TuneVal best = cand[0];
     float best_ms = 1e30f;
-    ftcg_status_t st = FTCG_SUCCESS;
-    for (int T : tiles) {
-        for (int layout : layouts) {
-            for (int kern : kernels(layout)) {
-                Plan* p = new (std::nothrow) Plan();
-                if (!p) {
-                    st = FTCG_ERR_OUT_OF_MEMORY;
-                    break;
-                }
-                p->M = M; p->N = N; p->G = G; p->w = w; p->sigma = sigma;
-                p->opts = opts;
-                p->opts.tile = T;
-                p->opts.layout = layout;
-                p->opts.spread_kernel = kern;
-                p->win = Window{w, es_beta(w, sigma)};
-                st = make_plan(p, d_lambda, s, false);
-                float ms = 1e30f;
-                if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC)
-                    st = time_spread(*p, zeros, grid, s, &ms);
-                release_plan(p);
-                if (st != FTCG_SUCCESS) break;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = TuneVal{T, layout, kern};
-                }
-            }
-            if (st != FTCG_SUCCESS) break;
+    for (const TuneVal& c : cand) {
+        Plan* p = new (std::nothrow) Plan();
+        if (!p) {
+            set_error("tuner: host allocation failed");
+            return FTCG_ERR_OUT_OF_MEMORY;
         }
-        if (st != FTCG_SUCCESS) break;
+        p->M = M; p->N = N; p->G = G; p->w = w; p->sigma = sigma;
+        p->opts = opts;
+        p->opts.tile = c.T;
+        p->opts.layout = c.layout;
+        p->opts.spread_kernel = c.skern;
+        p->win = Window{w, es_beta(w, sigma)};
+        ftcg_status_t st = make_plan(p, d_lambda, s, false);
+        float ms = 1e30f;
+        if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC) st = time_spread(*p, zeros, grid, s, &ms);
+        release_plan(p);
+        if (st != FTCG_SUCCESS) return st;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
     }
-    if (st != FTCG_SUCCESS) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = best;
@@ -483,20 +487,10 @@ std::vector<float2> class_twiddles(int G) {
     }
 }
 
-// profile: record the stage events of a profiled batch (not while a graph is being captured)
-ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, void* const* imgs,
-                            cudaStream_t s, bool profile = false) {
-    for (int i = 0; i < b.n; ++i) {
-        b.h_desc[i].vals = vals[i];
-        b.h_desc[i].img = reinterpret_cast<float2*>(imgs[i]);
-    }
-    FTCG_CK(cudaMemcpyAsync(b.d_desc, b.h_desc, b.n * sizeof(PingDesc), cudaMemcpyHostToDevice, s));
+// The spreading stage of a batch whose descriptors (values included) are on the device: the
+// persistent tensor-core and register-window launches, then the halo fix-up.
+ftcg_status_t batch_spread(Batch& b, bool vbf, cudaStream_t s) {
     FTCG_CK(cudaMemsetAsync(b.d_counter, 0, 2 * sizeof(int), s));
-    cudaEvent_t* ev = nullptr;
-    if (profile && b.profiling && b.prof_calls < kBatchProfiled)
-        ev = b.prof_ev.data() + 3 * b.prof_calls++;
-    if (ev) FTCG_CK(cudaEventRecord(ev[0], s));
-    const bool vbf = vdtype == FTCG_VALUES_BF16X2;
     const bool abf = b.opts.precision == FTCG_PREC_BF16;
     if (b.n_mma > 0) {
         if (vbf && abf) FTCG_TRY((launch_batch_spread_mma<true, true>(b, s)));
@@ -514,6 +508,22 @@ ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, v
         k_halo_add_batch<<<b.nitems, 256, 0, s>>>(b.d_desc, b.d_items);
         FTCG_CK(cudaGetLastError());
     }
+    return FTCG_SUCCESS;
+}
+
+// profile: record the stage events of a profiled batch (not while a graph is being captured)
+ftcg_status_t batch_enqueue(Batch& b, const void* const* vals, int32_t vdtype, void* const* imgs,
+                            cudaStream_t s, bool profile = false) {
+    for (int i = 0; i < b.n; ++i) {
+        b.h_desc[i].vals = vals[i];
+        b.h_desc[i].img = reinterpret_cast<float2*>(imgs[i]);
+    }
+    FTCG_CK(cudaMemcpyAsync(b.d_desc, b.h_desc, b.n * sizeof(PingDesc), cudaMemcpyHostToDevice, s));
+    cudaEvent_t* ev = nullptr;
+    if (profile && b.profiling && b.prof_calls < kBatchProfiled)
+        ev = b.prof_ev.data() + 3 * b.prof_calls++;
+    if (ev) FTCG_CK(cudaEventRecord(ev[0], s));
+    FTCG_TRY(batch_spread(b, vdtype == FTCG_VALUES_BF16X2, s));
     if (ev) FTCG_CK(cudaEventRecord(ev[1], s));
     bool any_cufft = false;
     for (auto& c : b.classes) {
@@ -596,18 +606,43 @@ ftcg_status_t make_plans_parallel(const std::vector<Plan*>& pings, const double*
     return FTCG_SUCCESS;
 }
 
+// The tuner key of a ping of batch b (batch = 1: chosen by timing batched launches).
+TuneKey batch_key(const Batch& b, int64_t M, int G) {
+    return TuneKey{G, b.w, b.opts.precision, density_bucket(M, G), b.opts.tile, b.opts.layout,
+                   b.opts.spread_kernel, 1};
+}
+
+ftcg_status_t tune_batch(const Batch& b, const double* const* d_lambda, const int64_t* M,
+                         const int32_t* N, cudaStream_t s);
+
 ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int64_t* M,
                               const int32_t* N, cudaStream_t s) {
-    // per-ping plans (tile side autotuned unless given): the tuner runs first, ping after ping
-    // (it times trial launches, which concurrent work would disturb), then the plans are built
+    // per-ping plans: the tile side, layout and spreading kernel (unless given) come from the
+    // batch tuner, which times batched launches per class of pings before any plan is built
+    // (concurrent work would disturb its timings); then the plans are built
+    const bool tuning = b.opts.tile == 0 || b.opts.layout == 0;
+    if (tuning) FTCG_TRY(tune_batch(b, d_lambda, M, N, s));
     std::vector<int> Gs(b.n);
     for (int i = 0; i < b.n; ++i) {
         const int G = (int)std::llround(b.sigma * N[i]);
         Gs[i] = G;
         int T = b.opts.tile, layout = b.opts.layout, skern = b.opts.spread_kernel;
-        if (T == 0 || layout == 0)
-            FTCG_TRY(tune_tile(d_lambda[i], M[i], N[i], b.sigma, b.w, b.opts, s, &T, &layout,
-                               &skern));
+        if (tuning) {
+            bool found = false;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tune.find(batch_key(b, M[i], G));
+                if (it != g_tune.end()) {
+                    T = it->second.T;
+                    layout = it->second.layout;
+                    skern = it->second.skern;
+                    found = true;
+                }
+            }
+            if (!found)
+                FTCG_TRY(tune_tile(d_lambda[i], M[i], N[i], b.sigma, b.w, b.opts, s, &T, &layout,
+                                   &skern));
+        }
         Plan* p = new (std::nothrow) Plan();
         if (!p) {
             set_error("ftcg_plan_batch: host allocation failed");
@@ -797,6 +832,110 @@ ftcg_status_t check_ptr_array(const void* const* a, int n, const char* what) {
             set_error("%s: pointer %d is NULL", what, i);
             return FTCG_ERR_INVALID_VALUE;
         }
+    return FTCG_SUCCESS;
+}
+
+// Spreading-stage time of one candidate over a sub-batch of pings (values: zeros).
+ftcg_status_t time_batch_candidate(const Batch& parent, const TuneVal& c,
+                                   const std::vector<const double*>& L,
+                                   const std::vector<int64_t>& m, const std::vector<int32_t>& n,
+                                   const void* zeros, cudaStream_t s, float* ms) {
+    Batch* sub = new (std::nothrow) Batch();
+    if (!sub) {
+        set_error("tuner: host allocation failed");
+        return FTCG_ERR_OUT_OF_MEMORY;
+    }
+    sub->n = (int)L.size();
+    sub->w = parent.w;
+    sub->sigma = parent.sigma;
+    sub->opts = parent.opts;
+    sub->opts.tile = c.T;
+    sub->opts.layout = c.layout;
+    sub->opts.spread_kernel = c.skern;
+    sub->last = s;
+    ftcg_status_t st = plan_batch_impl(*sub, L.data(), m.data(), n.data(), s);
+    if (st == FTCG_SUCCESS) {
+        for (int i = 0; i < sub->n; ++i) sub->h_desc[i].vals = zeros;
+        EventPair ev;
+        cudaError_t ce = cudaMemcpyAsync(sub->d_desc, sub->h_desc, sub->n * sizeof(PingDesc),
+                                         cudaMemcpyHostToDevice, s);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&ev.a);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&ev.b);
+        if (ce != cudaSuccess) {
+            set_error("tuner: %s", cudaGetErrorString(ce));
+            st = FTCG_ERR_CUDA;
+        }
+        if (st == FTCG_SUCCESS) st = batch_spread(*sub, false, s);               // warm-up
+        if (st == FTCG_SUCCESS) {
+            cudaError_t e = cudaEventRecord(ev.a, s);
+            for (int r = 0; r < 3 && e == cudaSuccess && st == FTCG_SUCCESS; ++r)
+                st = batch_spread(*sub, false, s);
+            if (e == cudaSuccess && st == FTCG_SUCCESS) e = cudaEventRecord(ev.b, s);
+            if (e == cudaSuccess && st == FTCG_SUCCESS) e = cudaEventSynchronize(ev.b);
+            if (e == cudaSuccess && st == FTCG_SUCCESS) e = cudaEventElapsedTime(ms, ev.a, ev.b);
+            if (e != cudaSuccess) {
+                set_error("tuner: %s", cudaGetErrorString(e));
+                st = FTCG_ERR_CUDA;
+            }
+        }
+    }
+    release_batch(sub);
+    return st;
+}
+
+// The batch tuner: the pings are grouped by tuner key (grid side, w, precision, half-octave
+// density bucket and the caller's fixed choices); for every key not decided yet, each candidate
+// (tile side, layout, kernel) is timed as the persistent spreading launch over up to
+// kTuneBatchPings pings of the group, planned for that candidate. Batched timings count what a
+// batch pays per item (per-tile and per-column-bin work) rather than how one small ping's launch
+// fills the GPU, which decides the single-ping tuner. Pings without samples take the first
+// candidate.
+constexpr int kTuneBatchPings = 16;
+
+ftcg_status_t tune_batch(const Batch& b, const double* const* d_lambda, const int64_t* M,
+                         const int32_t* N, cudaStream_t s) {
+    std::map<TuneKey, std::vector<int>> groups;
+    for (int i = 0; i < b.n; ++i) {
+        const int G = (int)std::llround(b.sigma * N[i]);
+        groups[batch_key(b, M[i], G)].push_back(i);
+    }
+    const std::vector<TuneVal> cand = tune_candidates(b.w, b.sigma, b.opts);
+    for (const auto& g : groups) {
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (g_tune.count(g.first)) continue;
+        }
+        TuneVal best = cand[0];
+        if (cand.size() > 1 && M[g.second[0]] > 0) {
+            const int size = (int)g.second.size();
+            const int k = std::min(size, kTuneBatchPings);
+            std::vector<const double*> L(k);
+            std::vector<int64_t> m(k);
+            std::vector<int32_t> n(k);
+            int64_t max_m = 1;
+            for (int j = 0; j < k; ++j) {
+                const int i = g.second[(int64_t)j * size / k];
+                L[j] = d_lambda[i];
+                m[j] = M[i];
+                n[j] = N[i];
+                max_m = std::max(max_m, M[i]);
+            }
+            DevBuf zbuf;
+            FTCG_CK(cudaMalloc(&zbuf.p, (size_t)max_m * sizeof(float2)));
+            FTCG_CK(cudaMemsetAsync(zbuf.p, 0, (size_t)max_m * sizeof(float2), s));
+            float best_ms = 1e30f;
+            for (const TuneVal& c : cand) {
+                float ms = 1e30f;
+                FTCG_TRY(time_batch_candidate(b, c, L, m, n, zbuf.p, s, &ms));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[g.first] = best;
+    }
     return FTCG_SUCCESS;
 }
 
@@ -1131,10 +1270,10 @@ ftcg_status_t ftcg_tuner_save(const char* path) {
         std::fprintf(f,
                      "{\"G\": %d, \"w\": %d, \"precision\": %d, \"bucket\": %d, "
                      "\"tile_req\": %d, \"layout_req\": %d, \"spread_req\": %d, "
-                     "\"tile\": %d, \"layout\": %d, \"spread\": %d}%s\n",
+                     "\"batch\": %d, \"tile\": %d, \"layout\": %d, \"spread\": %d}%s\n",
                      e.first.G, e.first.w, e.first.prec, e.first.bucket, e.first.tile,
-                     e.first.layout, e.first.skern, e.second.T, e.second.layout, e.second.skern,
-                     ++k < snap.size() ? "," : "");
+                     e.first.layout, e.first.skern, e.first.batch, e.second.T, e.second.layout,
+                     e.second.skern, ++k < snap.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
     if (std::fclose(f) != 0) {
@@ -1172,6 +1311,7 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
         int tile = 0, layout = 0, spread = FTCG_SPREAD_AUTO;
         if (!json_int(line, "spread_req", &k.skern)) k.skern = FTCG_SPREAD_AUTO;   // older files
         if (!json_int(line, "spread", &spread)) spread = FTCG_SPREAD_AUTO;
+        if (!json_int(line, "batch", &k.batch)) k.batch = 0;
         const bool ok = json_int(line, "G", &k.G) && json_int(line, "w", &k.w) &&
                         json_int(line, "precision", &k.prec) &&
                         json_int(line, "bucket", &k.bucket) &&
@@ -1187,6 +1327,7 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
                            (spread >= FTCG_SPREAD_AUTO && spread <= FTCG_SPREAD_TENSOR) &&
                            (spread != FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
                            (k.skern == FTCG_SPREAD_AUTO || spread == k.skern) &&
+                           (k.batch == 0 || k.batch == 1) &&
                            (tile == 32 || tile == 64) &&
                            (layout == FTCG_LAYOUT_DUPLICATE || layout == FTCG_LAYOUT_HALO) &&
                            (k.tile == 0 || k.tile == tile) && (k.layout == 0 || k.layout == layout);

@@ -130,7 +130,9 @@ def test_tuner_file_round_trip(L, tmp_path):
                {"G": 1024, "w": 8, "precision": 0, "bucket": -1, "tile_req": 0, "layout_req": 0,
                 "spread_req": 2, "tile": 64, "layout": 2, "spread": 2},
                {"G": 8192, "w": 8, "precision": 0, "bucket": -8, "tile_req": 0, "layout_req": 0,
-                "spread_req": 0, "tile": 32, "layout": 2, "spread": 1}]
+                "spread_req": 0, "tile": 32, "layout": 2, "spread": 1},
+               {"G": 8192, "w": 8, "precision": 0, "bucket": -8, "tile_req": 0, "layout_req": 0,
+                "spread_req": 0, "batch": 1, "tile": 64, "layout": 2, "spread": 2}]
     src = tmp_path / "tuner.json"
     src.write_text('{"ftcg_tuner": 1, "entries": [\n' +
                    ",\n".join(json.dumps(e) for e in entries) + "\n]}\n")
@@ -140,7 +142,7 @@ def test_tuner_file_round_trip(L, tmp_path):
     saved = json.loads(out.read_text())
     assert saved["ftcg_tuner"] == 1
     for e in entries:               # files written before the spreading-kernel choice load as 0
-        assert dict(e, spread_req=e.get("spread_req", 0),
+        assert dict(e, spread_req=e.get("spread_req", 0), batch=e.get("batch", 0),
                     spread=e.get("spread", e.get("spread_req", 0))) in saved["entries"]
     bad = tmp_path / "bad.json"
     bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[0], G=1000, tile=48))
@@ -149,6 +151,9 @@ def test_tuner_file_round_trip(L, tmp_path):
     assert b"line 2" in L.ftcg_last_error()
     bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[2], layout=1))
                    + "\n]}\n")          # the tensor-core kernel needs the halo layout
+    assert L.ftcg_tuner_load(str(bad).encode()) == 1
+    bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[4], batch=2))
+                   + "\n]}\n")
     assert L.ftcg_tuner_load(str(bad).encode()) == 1
     other = tmp_path / "other.json"
     other.write_text(json.dumps({"entries": [dict(entries[0], G=4096)]}) + "\n")
