@@ -440,10 +440,14 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
     g.manual_seed(seed)
     vals = [torch.randn(p.M, dtype=torch.complex64, device=device, generator=g) for p in pings]
     M_tot = sum(p.M for p in pings)
-    # warm the tile autotuner cache and the kernels
+    # warm the kernels and the autotuner's choices for every ping class, single-ping and batched
+    # (both arms then time planning without trial launches)
     with F.Plan(lams[0], pings[0].N, 2.0, 8) as pl:
         pl.weights()
         pl.adjoint(vals[0])
+    for lam, p in zip(lams, pings):
+        F.Plan(lam, p.N, 2.0, 8).close()
+    F.Batch(lams, [p.N for p in pings], 2.0, 8).close()
     # plain: one ping after another
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -835,6 +839,34 @@ def batch_full_extra(device, n_pings=512, reps=5, rank=0, world=1):
                                "kernel": "spreading stage (persistent spread + halo fix-up)"}}
 
 
+def run_weights_only(args):
+    """The exact FP64 weights of the large ping, --steps calls after --warmup (CUDA-event times
+    per call); for profiling the weight kernels alone."""
+    import statistics
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_1706_08575_gb300 as F
+    import sasgen
+    device = torch.device("cuda", 0)
+    p = sasgen.large_ping()
+    with F.Plan(torch.from_numpy(p.lam).to(device), p.N, p.sigma, p.w) as pl:
+        out = torch.empty(p.M, dtype=torch.float64, device=device)
+        for _ in range(args.warmup):
+            pl.weights(out=out)
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pl.weights(out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"weights_only": {"workload": "large ping", "M": p.M, "N": p.N,
+                                       "ms_median": statistics.median(ms), "calls": len(ms)}}),
+          flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -1071,7 +1103,8 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--extras-pings", type=int, default=64)
-    ap.add_argument("--only", choices=["learned-kernels", "batch"], default=None,
+    ap.add_argument("--only", choices=["learned-kernels", "batch", "weights", "learned"],
+                    default=None,
                     help="run one part alone for profiling (prints its own line, not the headline)")
     ap.add_argument("--batch-pings", type=int, default=512)
     args = ap.parse_args(argv)
@@ -1086,6 +1119,14 @@ def main(argv=None):
         print(json.dumps({"batch": batch_full_extra(torch.device("cuda", 0),
                                                     n_pings=args.batch_pings,
                                                     reps=args.steps)}), flush=True)
+    elif args.only == "weights":
+        run_weights_only(args)
+    elif args.only == "learned":
+        import torch
+        import __graft_entry__ as ge
+        ge.build()
+        print(json.dumps({"learned_vs_plain_per_ping": learned_vs_plain(
+            torch.device("cuda", 0), n_pings=args.extras_pings)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
