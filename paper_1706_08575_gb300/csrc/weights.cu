@@ -13,11 +13,15 @@
 // non-finite S flags FTCG_ERR_NUMERIC.
 //
 // The W1 grid is real (unit strengths, real window), so H is Hermitian, and so is H c (c and the
-// window factors are real and even); the result of W3's transform is then real. The transforms
-// are therefore a real-to-complex FFT (D2Z, exponent sign -, which gives conj(H) for a real grid)
-// and a complex-to-real FFT (Z2D, sign +): conj(sum_m H(m) c(m) e^{-...}) = the real S grid. Both
-// are in place on a real grid padded to G + 2 doubles per row. W1 stores each sample's 2 w window
-// values so that W3 reads them instead of evaluating the window again.
+// window factors are real and even); the result of W3's transform is then real. The forward
+// transform (exponent sign -, which gives conj(H) for a real grid) is taken column-first: real-to-
+// complex along y, keeping the half spectrum m_y >= 0, then complex along x; the inverse (sign +)
+// is complex along x, then complex-to-real along y: conj(sum_m H(m) c(m) e^{-...}) = the real S
+// grid. Both are pruned to what the method uses: the y transforms run only over the column blocks
+// that some footprint reaches (W3 reads nothing else; a polar wedge reaches about half of them),
+// and the x transforms only over the N rows m_y = 0..N-1 where c is non-zero. W1 stores each
+// sample's 2 w window values and its tap origins so that W3 reads them instead of evaluating
+// them again.
 
 #include <cuda_runtime.h>
 
@@ -47,13 +51,6 @@ struct PolyCoef {
     double c[kPolyMaxW][kPolyDeg + 1];   // c[l][k]: coefficient of x^k in p_l
 };
 
-__device__ __forceinline__ double poly_eval(const double* c, double x) {
-    double v = c[kPolyDeg];
-#pragma unroll
-    for (int k = kPolyDeg - 1; k >= 0; --k) v = fma(v, x, c[k]);
-    return v;
-}
-
 struct Origin64 {
     long long c;
     double d;
@@ -80,99 +77,169 @@ __device__ __forceinline__ int wrapi(long long c, int G) {
     return (int)(r < 0 ? r + G : r);
 }
 
-// W1: g_l += phi(u_x - l_x) phi(u_y - l_y) (real, unit strengths), one 16-lane group per sample:
-// lane l evaluates tap l of both axes once with its polynomial (and stores both values in the
-// sample's row of phi), the row factors are broadcast by shuffles, and lane l adds its column with
-// FP64 global atomics to the real grid (row stride ld).
-__global__ void __launch_bounds__(256)
+// W1: g_l += phi(u_x - l_x) phi(u_y - l_y) (real, unit strengths). The FP64 pipe bounds this
+// kernel, so every FP64 instruction is given 32 useful lanes. A warp takes 32 samples at a time:
+// lane i first computes sample i's tap origins and polynomial arguments (the origins are stored
+// for W3); then groups of 8 lanes take the samples four at a time. For one sample, the group's
+// lanes evaluate its 2 w tap polynomials (polynomial p is x-tap p for p < w and y-tap p - w
+// otherwise; lane l takes p = l, l + 8, ...), store the values in the sample's row of phi and in
+// shared memory, and add the w^2 products of the row-major footprint (tap t = l, l + 8, ...)
+// with FP64 global atomics to the real grid (row stride ld).
+constexpr int kW1Threads = 256;
+
+__global__ void __launch_bounds__(kW1Threads)
     k_w1_spread(const double* __restrict__ lam, int64_t M, double scale, int G, int64_t ld, int W,
                 const PolyCoef* __restrict__ pc, double* __restrict__ grid,
-                double* __restrict__ phi) {
-    const int l = threadIdx.x & 15;
-    const unsigned gmask = 0xffffu << ((threadIdx.x & 31) & 16);
-    double c[kPolyDeg + 1];                  // this lane's tap polynomial
-#pragma unroll
-    for (int k = 0; k <= kPolyDeg; ++k) c[k] = l < W ? pc->c[l][k] : 0.0;
+                double* __restrict__ phi, int2* __restrict__ org) {
+    __shared__ double s_c[kPolyMaxW][kPolyDeg + 1];
+    __shared__ double s_v[kW1Threads / 8][2 * kPolyMaxW];   // per group: its sample's values
+    for (int i = threadIdx.x; i < kPolyMaxW * (kPolyDeg + 1); i += kW1Threads)
+        s_c[i / (kPolyDeg + 1)][i % (kPolyDeg + 1)] = pc->c[i / (kPolyDeg + 1)][i % (kPolyDeg + 1)];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, l = lane & 7, gi = lane >> 3;
+    const unsigned gmask = 0xffu << (lane & 24);
+    double* v = s_v[threadIdx.x >> 3];
     const double s0 = 0.5 * W - 1.0;
-    const int64_t ngr = (int64_t)gridDim.x * (blockDim.x / 16);
-    const int64_t j0 = blockIdx.x * (int64_t)(blockDim.x / 16) + threadIdx.x / 16;
-    for (int64_t j = j0; j < M; j += ngr) {
-        Origin64 ox = origin64(lam[2 * j], scale, W);
-        Origin64 oy = origin64(lam[2 * j + 1], scale, W);
-        if (!ox.ok || !oy.ok) continue;                       // uniform within the group
-        const double fx = l < W ? poly_eval(c, 2.0 * (ox.d - s0) - 1.0) : 0.0;
-        const double fyl = l < W ? poly_eval(c, 2.0 * (oy.d - s0) - 1.0) : 0.0;
-        if (l < W) {
-            phi[j * 2 * W + l] = fx;
-            phi[j * 2 * W + W + l] = fyl;
+    const int np = 2 * W, nt = W * W;
+    const int r0 = l / W, c0 = l - r0 * W;               // this lane's first footprint tap
+    const int64_t step = (int64_t)gridDim.x * kW1Threads;
+    for (int64_t base = ((int64_t)blockIdx.x * kW1Threads + (threadIdx.x & ~31)); base < M;
+         base += step) {
+        const int64_t ji = base + lane;
+        double ax = 0.0, ay = 0.0;
+        int cx = 0, cy = 0, ok = 0;
+        if (ji < M) {
+            const Origin64 ox = origin64(lam[2 * ji], scale, W);
+            const Origin64 oy = origin64(lam[2 * ji + 1], scale, W);
+            ok = ox.ok && oy.ok;
+            if (ok) {
+                cx = wrapi(ox.c, G);
+                cy = wrapi(oy.c, G);
+                ax = 2.0 * (ox.d - s0) - 1.0;
+                ay = 2.0 * (oy.d - s0) - 1.0;
+            }
+            org[ji] = ok ? make_int2(cx, cy) : make_int2(-1, -1);
         }
-        const int col = wrapi(ox.c + l, G);
-        int row = wrapi(oy.c, G);
-        for (int r = 0; r < W; ++r) {
-            const double fy = __shfl_sync(gmask, fyl, r, 16);
-            if (l < W) atomicAdd(grid + (int64_t)row * ld + col, fx * fy);
-            if (++row == G) row = 0;
+        const int nb = (int)(M - base < 32 ? M - base : 32);
+        for (int q = 0; q < 8; ++q) {                     // samples 4 q + gi of the block
+            const int src = 4 * q + gi;
+            const double sx = __shfl_sync(0xffffffffu, ax, src);
+            const double sy = __shfl_sync(0xffffffffu, ay, src);
+            const int scx = __shfl_sync(0xffffffffu, cx, src);
+            const int scy = __shfl_sync(0xffffffffu, cy, src);
+            const int sok = __shfl_sync(0xffffffffu, ok, src);
+            if (src >= nb || !sok) continue;               // uniform within the group
+            const int64_t j = base + src;
+            for (int p = l; p < np; p += 8) {
+                const int tap = p < W ? p : p - W;
+                const double x = p < W ? sx : sy;
+                double acc = s_c[tap][kPolyDeg];
+#pragma unroll
+                for (int k = kPolyDeg - 1; k >= 0; --k) acc = fma(acc, x, s_c[tap][k]);
+                v[p] = acc;
+                phi[j * np + p] = acc;
+            }
+            __syncwarp(gmask);
+            int r = r0, c = c0;
+            for (int t = l; t < nt; t += 8) {
+                int row = scy + r, col = scx + c;
+                if (row >= G) row -= G;
+                if (col >= G) col -= G;
+                atomicAdd(grid + (int64_t)row * ld + col, v[c] * v[W + r]);
+                c += 8;
+                while (c >= W) {
+                    c -= W;
+                    ++r;
+                }
+            }
+            __syncwarp(gmask);
         }
     }
 }
 
-// W2: on the half spectrum of the real-to-complex transform (G rows x (G/2 + 1) columns) keep
-// q = m mod G for m in {-N..N-1}^2 and multiply by r(m_x) r(m_y) (adjoint window division) * c(m) *
-// r(m_x) r(m_y) (forward window division); zero every other cell. The columns q_x < N hold
-// m_x = q_x; m_x < 0 lies in the implicit conjugate half (q_x >= G - N > G / 2), and m_x = N
-// (q_x = N) has c = 0. r has 2N entries for m = -N..N-1.
-__global__ void k_w2_lag(double2* __restrict__ spec, int G, int N, const double* __restrict__ r) {
-    const int H = G / 2 + 1;
-    const int64_t total = (int64_t)G * H;
+// W2 on the column-first half spectrum B[q_y][q_x] (q_y in 0..G/2 along the rows of B, q_x in
+// 0..G-1, row width G): the first N rows hold m_y = q_y in 0..N-1; in them q_x < N holds
+// m_x = q_x and q_x >= G - N holds m_x = q_x - G. Those cells are multiplied by r(m_x) r(m_y)
+// (adjoint window division) * c(m) * r(m_x) r(m_y) (forward window division); every other cell of
+// the first N rows is zeroed (rows N..G/2, m_y >= N where c = 0, are zeroed by the caller). r has
+// 2N entries for m = -N..N-1.
+__global__ void k_w2_lag(double2* __restrict__ B, int G, int N, const double* __restrict__ r) {
+    const int64_t total = (int64_t)N * G;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int qy = (int)(i / H), qx = (int)(i - (int64_t)qy * H);
-        const int my = qy < N ? qy : (qy >= G - N ? qy - G : INT32_MIN);
-        double2 v = spec[i];
-        if (my == INT32_MIN || qx >= N) {
+        const int my = (int)(i / G), qx = (int)(i - (int64_t)my * G);
+        const int mx = qx < N ? qx : (qx >= G - N ? qx - G : INT32_MIN);
+        double2 v = B[i];
+        if (mx == INT32_MIN) {
             v.x = 0.0;
             v.y = 0.0;
         } else {
-            const int mx = qx;
             const double ry = r[my + N], rx = r[mx + N];
-            const double cx = (double)(N - mx) / ((double)N * N);
-            const double cy = (double)(N - (my < 0 ? -my : my)) / ((double)N * N);
+            const double cx = (double)(N - (mx < 0 ? -mx : mx)) / ((double)N * N);
+            const double cy = (double)(N - my) / ((double)N * N);
             const double f = rx * rx * ry * ry * cx * cy;
             v.x *= f;
             v.y *= f;
         }
-        spec[i] = v;
+        B[i] = v;
     }
 }
 
-// W3 + W4: S_k = sum_taps phi phi h_l at 2 lambda_k, with the window values W1 stored; alpha_k =
-// 1 / S_k.
+// The grid columns that some sample's footprint reaches (W3 reads only those): occ[x] = 1.
+__global__ void k_mark_cols(const int2* __restrict__ org, int64_t M, int G, int W,
+                            unsigned char* __restrict__ occ) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M * W;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / W;
+        const int t = (int)(i - j * W);
+        const int x0 = org[j].x;
+        if (x0 < 0) continue;
+        int x = x0 + t;
+        if (x >= G) x -= G;
+        occ[x] = 1;
+    }
+}
+
+// W3 + W4: S_k = sum_taps phi phi h_l at 2 lambda_k from the origins and window values W1
+// stored; alpha_k = 1 / S_k. Four lanes per sample (eight samples per warp, so every FP64
+// instruction has 32 useful lanes): lane q sums the columns q, q + 4, ... of the footprint over
+// all w rows, weights them with the column factors, and the four partial sums are added.
 __global__ void __launch_bounds__(256)
-    k_w3_interp(const double* __restrict__ lam, int64_t M, double scale, int G, int64_t ld, int W,
+    k_w3_interp(const int2* __restrict__ org, int64_t M, int G, int64_t ld, int W,
                 const double* __restrict__ grid, const double* __restrict__ phi,
                 double* __restrict__ alpha, unsigned* __restrict__ status) {
-    const int l = threadIdx.x & 15;
-    const unsigned gmask = 0xffffu << ((threadIdx.x & 31) & 16);
-    const int64_t ngr = (int64_t)gridDim.x * (blockDim.x / 16);
-    for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / 16) + threadIdx.x / 16; j < M; j += ngr) {
-        Origin64 ox = origin64(lam[2 * j], scale, W);
-        Origin64 oy = origin64(lam[2 * j + 1], scale, W);
-        const bool ok = ox.ok && oy.ok;                       // uniform within the group
+    const int q = threadIdx.x & 3;
+    const unsigned qmask = 0xfu << ((threadIdx.x & 31) & ~3);
+    const int64_t ngr = (int64_t)gridDim.x * (blockDim.x / 4);
+    for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / 4) + threadIdx.x / 4; j < M; j += ngr) {
+        const int2 o = org[j];
+        const bool ok = o.x >= 0;                             // uniform within the group
         double sr = 0.0;
         if (ok) {
-            const double fx = l < W ? phi[j * 2 * W + l] : 0.0;
-            const double fyl = l < W ? phi[j * 2 * W + W + l] : 0.0;
-            const int col = wrapi(ox.c + l, G);
-            int row = wrapi(oy.c, G);
+            const double* ph = phi + j * 2 * W;
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            int col[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                col[c] = o.x + q + 4 * c;
+                if (col[c] >= G) col[c] -= G;
+            }
+            int row = o.y;
             for (int r = 0; r < W; ++r) {
-                const double fy = __shfl_sync(gmask, fyl, r, 16);
-                if (l < W) sr += fy * grid[(int64_t)row * ld + col];
+                const double fy = ph[W + r];
+                const double* g = grid + (int64_t)row * ld;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (q + 4 * c < W) acc[c] = fma(fy, g[col[c]], acc[c]);
                 if (++row == G) row = 0;
             }
-            sr *= fx;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (q + 4 * c < W) sr = fma(ph[q + 4 * c], acc[c], sr);
         }
-        for (int o = 8; o > 0; o >>= 1) sr += __shfl_xor_sync(gmask, sr, o, 16);
-        if (l == 0) {
+        sr += __shfl_xor_sync(qmask, sr, 1, 4);
+        sr += __shfl_xor_sync(qmask, sr, 2, 4);
+        if (q == 0) {
             if (!ok) {
                 alpha[j] = 0.0;
             } else if (!(sr > 0.0) || !isfinite(sr)) {
@@ -196,47 +263,99 @@ int nblocks(int64_t n, int t) {
 
 namespace {
 
-// cuFFT plans of the lag grid, one pair per (device, G), created once and shared; they own no
-// workspace (each call passes its own), and their use is serialised by the mutex.
-struct LagFft {
-    cufftHandle d2z = 0, z2d = 0;
+// cuFFT plans of the lag transforms, created on first use and shared; they own no workspace
+// (each call passes its own) and their use is serialised by the mutex. Per device and grid side
+// G: column transforms along y of a batch of adjacent columns (D2Z from the real grid, row stride
+// G + 2, into B, row width G; Z2D back), batches being runs of kLagColBlock-column blocks, and
+// row transforms along x of the first N rows of B (Z2Z).
+constexpr int kLagColBlock = 128;
+enum LagKind { LAG_D2Z_Y = 0, LAG_Z2D_Y = 1, LAG_Z2Z_X = 2 };
+struct LagKey {
+    int dev, G, kind, batch;
+    bool operator<(const LagKey& o) const {
+        if (dev != o.dev) return dev < o.dev;
+        if (G != o.G) return G < o.G;
+        if (kind != o.kind) return kind < o.kind;
+        return batch < o.batch;
+    }
+};
+struct LagPlan {
+    cufftHandle h = 0;
     size_t ws = 0;
 };
 std::mutex g_lag_mu;
-std::map<std::pair<int, int>, LagFft> g_lag;
+std::map<LagKey, LagPlan> g_lag;
 
-ftcg_status_t lag_fft_locked(int G, LagFft* out) {
-    int dev = 0;
-    FTCG_CK(cudaGetDevice(&dev));
-    auto it = g_lag.find({dev, G});
+ftcg_status_t lag_plan_locked(int dev, int G, int kind, int batch, LagPlan* out) {
+    const LagKey key{dev, G, kind, batch};
+    auto it = g_lag.find(key);
     if (it == g_lag.end()) {
-        LagFft f;
-        size_t w1 = 0, w2 = 0;
-        FTCG_CKFFT(cufftCreate(&f.d2z));
-        FTCG_CKFFT(cufftSetAutoAllocation(f.d2z, 0));
-        FTCG_CKFFT(cufftMakePlan2d(f.d2z, G, G, CUFFT_D2Z, &w1));
-        FTCG_CKFFT(cufftCreate(&f.z2d));
-        FTCG_CKFFT(cufftSetAutoAllocation(f.z2d, 0));
-        FTCG_CKFFT(cufftMakePlan2d(f.z2d, G, G, CUFFT_Z2D, &w2));
-        f.ws = std::max(w1, w2);
-        it = g_lag.emplace(std::make_pair(dev, G), f).first;
+        LagPlan pl;
+        int n[1] = {G};
+        const int ld = G + 2, H = G / 2 + 1;
+        int inembed[1] = {G}, onembed[1] = {G};
+        FTCG_CKFFT(cufftCreate(&pl.h));
+        FTCG_CKFFT(cufftSetAutoAllocation(pl.h, 0));
+        cufftResult r;
+        if (kind == LAG_D2Z_Y) {
+            onembed[0] = H;
+            r = cufftMakePlanMany(pl.h, 1, n, inembed, ld, 1, onembed, G, 1, CUFFT_D2Z, batch,
+                                  &pl.ws);
+        } else if (kind == LAG_Z2D_Y) {
+            inembed[0] = H;
+            r = cufftMakePlanMany(pl.h, 1, n, inembed, G, 1, onembed, ld, 1, CUFFT_Z2D, batch,
+                                  &pl.ws);
+        } else {
+            r = cufftMakePlanMany(pl.h, 1, n, inembed, 1, G, onembed, 1, G, CUFFT_Z2Z, batch,
+                                  &pl.ws);
+        }
+        if (r != CUFFT_SUCCESS) {
+            cufftDestroy(pl.h);
+            set_error("cuFFT plan of the lag transforms failed (%d)", (int)r);
+            return FTCG_ERR_CUDA;
+        }
+        it = g_lag.emplace(key, pl).first;
     }
     *out = it->second;
     return FTCG_SUCCESS;
+}
+
+// Runs [x0, x0 + n) of kLagColBlock-column blocks (the last block may be shorter) holding an
+// occupied column.
+std::vector<std::pair<int, int>> lag_runs(const std::vector<unsigned char>& occ, int G) {
+    std::vector<std::pair<int, int>> runs;
+    const int nblk = (G + kLagColBlock - 1) / kLagColBlock;
+    int start = -1;
+    for (int b = 0; b <= nblk; ++b) {
+        bool any = false;
+        if (b < nblk)
+            for (int x = b * kLagColBlock; x < std::min(G, (b + 1) * kLagColBlock) && !any; ++x)
+                any = occ[x] != 0;
+        if (any && start < 0) start = b;
+        if (!any && start >= 0) {
+            const int x0 = start * kLagColBlock;
+            runs.push_back({x0, std::min(G, b * kLagColBlock) - x0});
+            start = -1;
+        }
+    }
+    return runs;
 }
 
 // Device buffers of one weight computation, released on every path.
 struct WeightBuffers {
     double* r2 = nullptr;
     double* grid = nullptr;
+    double2* spec = nullptr;
     double* phi = nullptr;
+    int2* org = nullptr;
+    unsigned char* occ = nullptr;
     void* work = nullptr;
     PolyCoef* coef = nullptr;
     double* alpha = nullptr;
     bool own_alpha = false;
     cudaStream_t s = nullptr;            // allocated from the pool on s, freed on s
     ~WeightBuffers() {
-        void* all[6] = {r2, grid, phi, work, coef, own_alpha ? alpha : nullptr};
+        void* all[9] = {r2, grid, spec, phi, org, occ, work, coef, own_alpha ? alpha : nullptr};
         for (void* q : all)
             if (q) pool_free(q, s);
     }
@@ -291,24 +410,30 @@ ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s) {
     const int Wa = p.opts.weight_width > 0 ? p.opts.weight_width : 12;
     const int N2 = 2 * p.N;
     const int G2 = 2 * p.G;                      // sigma * (2N)
-    const int64_t ld = G2 + 2;                   // real row stride of the in-place transforms
+    const int64_t ld = G2 + 2;                   // row stride of the real lag grid
+    const int H = G2 / 2 + 1;                    // rows of the column-first half spectrum
     const double scale = 2.0 * p.sigma;          // u = sigma * (2 lambda)
     Window wa{Wa, es_beta(Wa, p.sigma)};
 
     std::lock_guard<std::mutex> lk(g_lag_mu);
-    LagFft fft;
-    FTCG_TRY(lag_fft_locked(G2, &fft));
+    int dev = 0;
+    FTCG_CK(cudaGetDevice(&dev));
     WeightBuffers b;
     const size_t gbytes = (size_t)G2 * ld * sizeof(double);
+    const size_t sbytes = (size_t)H * G2 * sizeof(double2);
     const size_t pbytes = (size_t)p.M * 2 * Wa * sizeof(double);
     b.s = s;
     if (pool_malloc(&b.r2, N2 * sizeof(double), s) != cudaSuccess ||
-        pool_malloc(&b.grid, gbytes, s) != cudaSuccess || pool_malloc(&b.phi, pbytes, s) != cudaSuccess ||
-        pool_malloc(&b.coef, sizeof(PolyCoef), s) != cudaSuccess ||
-        (fft.ws > 0 && pool_malloc(&b.work, fft.ws, s) != cudaSuccess)) {
+        pool_malloc(&b.grid, gbytes, s) != cudaSuccess ||
+        pool_malloc(&b.spec, sbytes, s) != cudaSuccess ||
+        pool_malloc(&b.phi, pbytes, s) != cudaSuccess ||
+        pool_malloc(&b.org, (size_t)p.M * sizeof(int2), s) != cudaSuccess ||
+        pool_malloc(&b.occ, (size_t)G2, s) != cudaSuccess ||
+        pool_malloc(&b.coef, sizeof(PolyCoef), s) != cudaSuccess) {
         cudaGetLastError();
-        set_error("ftcg_weights: cannot allocate the FP64 lag grid (%zu bytes), the window table "
-                  "(%zu bytes) or the FFT workspace (%zu bytes)", gbytes, pbytes, fft.ws);
+        set_error("ftcg_weights: cannot allocate the FP64 lag grid (%zu bytes), its spectrum "
+                  "(%zu bytes), the window table (%zu bytes) or the tap origins", gbytes, sbytes,
+                  pbytes);
         return FTCG_ERR_OUT_OF_MEMORY;
     }
     b.alpha = d_alpha_out;
@@ -325,23 +450,58 @@ ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s) {
     FTCG_CK(cudaMemcpyAsync(b.coef, &hc, sizeof(PolyCoef), cudaMemcpyHostToDevice, s));
     FTCG_TRY(window_factors(b.r2, N2, G2, wa, s));
     FTCG_CK(cudaMemsetAsync(b.grid, 0, gbytes, s));
-    k_w1_spread<<<nblocks(p.M * 16, 256), 256, 0, s>>>(p.lambda, p.M, scale, G2, ld, Wa, b.coef,
-                                                        b.grid, b.phi);
+    FTCG_CK(cudaMemsetAsync(b.occ, 0, (size_t)G2, s));
+    k_w1_spread<<<nblocks(p.M, kW1Threads), kW1Threads, 0, s>>>(p.lambda, p.M, scale, G2, ld, Wa,
+                                                                b.coef, b.grid, b.phi, b.org);
+    k_mark_cols<<<nblocks(p.M * Wa, 256), 256, 0, s>>>(b.org, p.M, G2, Wa, b.occ);
     FTCG_CK(cudaGetLastError());
-    cufftDoubleComplex* spec = reinterpret_cast<cufftDoubleComplex*>(b.grid);
-    FTCG_CKFFT(cufftSetStream(fft.d2z, s));
-    FTCG_CKFFT(cufftSetWorkArea(fft.d2z, b.work));
-    FTCG_CKFFT(cufftExecD2Z(fft.d2z, b.grid, spec));
-    k_w2_lag<<<nblocks((int64_t)G2 * (G2 / 2 + 1), 256), 256, 0, s>>>(
-        reinterpret_cast<double2*>(b.grid), G2, p.N, b.r2);
+    // The lag transforms, column-first and pruned: along y only over the column blocks that
+    // footprints reach (W3 reads nothing else), keeping the half spectrum m_y >= 0; along x only
+    // over the N rows m_y = 0..N-1 that the lag weights keep.
+    std::vector<unsigned char> occ((size_t)G2);
+    FTCG_CK(cudaMemcpyAsync(occ.data(), b.occ, (size_t)G2, cudaMemcpyDeviceToHost, s));
+    FTCG_CK(cudaStreamSynchronize(s));
+    const std::vector<std::pair<int, int>> runs = lag_runs(occ, G2);
+    std::vector<LagPlan> fwd(runs.size()), inv(runs.size());
+    LagPlan rows;
+    size_t ws = 0;
+    for (size_t k = 0; k < runs.size(); ++k) {
+        FTCG_TRY(lag_plan_locked(dev, G2, LAG_D2Z_Y, runs[k].second, &fwd[k]));
+        FTCG_TRY(lag_plan_locked(dev, G2, LAG_Z2D_Y, runs[k].second, &inv[k]));
+        ws = std::max(ws, std::max(fwd[k].ws, inv[k].ws));
+    }
+    FTCG_TRY(lag_plan_locked(dev, G2, LAG_Z2Z_X, p.N, &rows));
+    ws = std::max(ws, rows.ws);
+    if (ws > 0 && pool_malloc(&b.work, ws, s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("ftcg_weights: cannot allocate the FFT workspace (%zu bytes)", ws);
+        return FTCG_ERR_OUT_OF_MEMORY;
+    }
+    cufftDoubleComplex* spec = reinterpret_cast<cufftDoubleComplex*>(b.spec);
+    FTCG_CK(cudaMemsetAsync(b.spec, 0, (size_t)p.N * G2 * sizeof(double2), s));
+    for (size_t k = 0; k < runs.size(); ++k) {
+        FTCG_CKFFT(cufftSetStream(fwd[k].h, s));
+        FTCG_CKFFT(cufftSetWorkArea(fwd[k].h, b.work));
+        FTCG_CKFFT(cufftExecD2Z(fwd[k].h, b.grid + runs[k].first, spec + runs[k].first));
+    }
+    // rows N..G/2 (m_y >= N, lag weight 0) are zero for the inverse
+    FTCG_CK(cudaMemsetAsync(b.spec + (size_t)p.N * G2, 0,
+                            (size_t)(H - p.N) * G2 * sizeof(double2), s));
+    FTCG_CKFFT(cufftSetStream(rows.h, s));
+    FTCG_CKFFT(cufftSetWorkArea(rows.h, b.work));
+    FTCG_CKFFT(cufftExecZ2Z(rows.h, spec, spec, CUFFT_FORWARD));
+    k_w2_lag<<<nblocks((int64_t)p.N * G2, 256), 256, 0, s>>>(b.spec, G2, p.N, b.r2);
     FTCG_CK(cudaGetLastError());
-    FTCG_CKFFT(cufftSetStream(fft.z2d, s));
-    FTCG_CKFFT(cufftSetWorkArea(fft.z2d, b.work));
-    FTCG_CKFFT(cufftExecZ2D(fft.z2d, spec, b.grid));
+    FTCG_CKFFT(cufftExecZ2Z(rows.h, spec, spec, CUFFT_INVERSE));
+    for (size_t k = 0; k < runs.size(); ++k) {
+        FTCG_CKFFT(cufftSetStream(inv[k].h, s));
+        FTCG_CKFFT(cufftSetWorkArea(inv[k].h, b.work));
+        FTCG_CKFFT(cufftExecZ2D(inv[k].h, spec + runs[k].first, b.grid + runs[k].first));
+    }
     unsigned before = 0;
     FTCG_CK(cudaMemcpyAsync(&before, p.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    k_w3_interp<<<nblocks(p.M * 16, 256), 256, 0, s>>>(p.lambda, p.M, scale, G2, ld, Wa, b.grid,
-                                                        b.phi, b.alpha, p.status);
+    k_w3_interp<<<nblocks(p.M * 4, 256), 256, 0, s>>>(b.org, p.M, G2, ld, Wa, b.grid, b.phi,
+                                                       b.alpha, p.status);
     FTCG_CK(cudaGetLastError());
     FTCG_TRY(launch_set_alpha(p, b.alpha, FTCG_WEIGHTS_F64, s));
     unsigned after = 0;
