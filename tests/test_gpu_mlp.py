@@ -2,10 +2,15 @@
 tensor-core forward and gradients, on-device training, checkpoint continuation, and the gain the
 trained network brings over gridding without weights.
 
-Bars: neighbour indices bit-exact; feature values within bfloat16 rounding (2^-8 relative);
-forward y and every gradient tensor within 3e-2 norm-relative of the FP64 oracle evaluated on the
-same bf16-rounded parameters and features (activations are rounded to bfloat16 between layers on
-the GPU, unit roundoff 2^-9, across three layers)."""
+Bars: neighbour indices bit-exact; feature values within bfloat16 rounding (2^-8 relative).
+Forward y, the loss and every gradient tensor are held to a bar derived per tensor from the
+device's arithmetic: the device rounds to bfloat16 (unit roundoff 2^-9) exactly at six points,
+the activations h1, h2, h3 and the back-propagated dz3, dz2, dz1, and computes everything else
+in FP32 on bf16-rounded parameters and features. `bf16_model` repeats the network in FP64 with
+those six roundings; its distance E from the FP64 oracle (no rounding) is the error the
+roundings alone cause for that tensor, and the device must lie within 4 E + 1e-5 of the oracle
+(the factor covers roundings that fall differently on FP32 inputs; 1e-5 the FP32 accumulation),
+and within 1e-3 of the model itself."""
 import numpy as np
 import pytest
 
@@ -36,6 +41,28 @@ def bf16(x):
 
 def nrel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def bf16_model(P, X, t):
+    """The network's forward pass, loss and gradients in FP64 with bfloat16 rounding where the
+    device rounds (h1, h2, h3 and dz3, dz2, dz1); P holds the bf16-rounded weights."""
+    r = bf16
+    z1 = X @ P["W1"] + P["b1"]
+    h1 = r(L.gelu(z1))
+    z2 = h1 @ P["W2"] + P["b2"]
+    h2 = r(L.gelu(z2))
+    z3 = h2 @ P["W3"] + P["b3"]
+    h3 = r(L.gelu(z3))
+    y = h3 @ P["w4"] + P["b4"][0]
+    dy = 2.0 * (y - t) / y.shape[0]
+    g = {"w4": h3.T @ dy, "b4": np.array([dy.sum()])}
+    dz3 = r(np.outer(dy, P["w4"]) * L.gelu_grad(z3))
+    g["W3"], g["b3"] = h2.T @ dz3, dz3.sum(0)
+    dz2 = r((dz3 @ P["W3"].T) * L.gelu_grad(z2))
+    g["W2"], g["b2"] = h1.T @ dz2, dz2.sum(0)
+    dz1 = r((dz2 @ P["W2"].T) * L.gelu_grad(z1))
+    g["W1"], g["b1"] = X.T @ dz1, dz1.sum(0)
+    return y, g, L.loss(y, t)
 
 
 def test_features_exact_neighbours(F):
@@ -132,13 +159,19 @@ def test_forward_and_grads_vs_oracle(F):
     for k in ("W1", "W2", "W3", "w4"):
         Pr[k] = bf16(Pr[k])
     y_ref, cache = L.forward(Pr, X)
-    assert nrel(np.log(alpha), y_ref) < 3e-2
-    g, loss = mlp.grads(Xt, dev(t))
     g_ref = L.backward(Pr, cache, y_ref, t)
-    assert abs(loss - L.loss(y_ref, t)) / L.loss(y_ref, t) < 3e-2
+    l_ref = L.loss(y_ref, t)
+    y_m, g_m, l_m = bf16_model(Pr, X, t)
+    y_dev = np.log(alpha)
+    assert nrel(y_dev, y_ref) <= 4 * nrel(y_m, y_ref) + 1e-5
+    assert nrel(y_dev, y_m) < 1e-3
+    g, loss = mlp.grads(Xt, dev(t))
+    assert abs(loss - l_ref) / l_ref <= 4 * abs(l_m - l_ref) / l_ref + 1e-5
     G = L.unpack(g)
     for k, _ in L.ORDER:
-        assert nrel(G[k], g_ref[k]) < 3e-2, k
+        bar = 4 * nrel(g_m[k], g_ref[k]) + 1e-5
+        assert nrel(G[k], g_ref[k]) <= bar, (k, nrel(G[k], g_ref[k]), bar)
+        assert nrel(G[k], g_m[k]) < 1e-3, k
     mlp.close()
 
 
