@@ -37,18 +37,20 @@ namespace ftcg {
 
 namespace {
 
-// The window on the weight path, in FP64, as one polynomial per tap: the first-tap offset d lies in
-// (w/2 - 1, w/2], so tap l's argument d - l covers one unit interval, and with s = d - (w/2 - 1)
-// in (0, 1] phi(d - l) = p_l(2 s - 1). p_l has degree kPolyDeg and interpolates phi at the
-// Chebyshev points of its interval (coefficients from window_poly on the host). The end
-// intervals hold the window's square-root branch point, where phi = exp(-beta); the interpolation
-// error there is about exp(-beta) / 2 of phi(0) (6e-13 at w = 12, sigma = 2; 1e-10 at w = 12,
-// sigma = 1.25) and far smaller inside, i.e. at the level of the window's own truncation.
-constexpr int kPolyDeg = 14;
+// The window on the weight path, in FP64, as two polynomials per tap: the first-tap offset d lies
+// in (w/2 - 1, w/2], so tap l's argument d - l covers one unit interval; with s = d - (w/2 - 1) in
+// (0, 1] and x = 2 s - 1, phi(d - l) = p_{l,h}(2 x + 1 - 2 h) on the half h = [x >= 0] of the
+// interval. Each p_{l,h} has degree kPolyDeg and interpolates phi at the Chebyshev points of its
+// half interval (coefficients from window_poly on the host); halving the interval brings degree
+// 9 to the accuracy that degree 14 gives on the whole interval. The end intervals hold the
+// window's square-root branch point, where phi = exp(-beta); the interpolation error there is
+// about exp(-beta) / 2 of phi(0) (6e-13 at w = 12, sigma = 2; 1.2e-10 at w = 12, sigma = 1.25)
+// and far smaller inside, i.e. at the level of the window's own truncation.
+constexpr int kPolyDeg = 9;
 constexpr int kPolyMaxW = 16;
 
 struct PolyCoef {
-    double c[kPolyMaxW][kPolyDeg + 1];   // c[l][k]: coefficient of x^k in p_l
+    double c[kPolyMaxW][2][kPolyDeg + 1];   // c[l][h][k]: coefficient of y^k in p_{l,h}
 };
 
 struct Origin64 {
@@ -91,10 +93,10 @@ __global__ void __launch_bounds__(kW1Threads)
     k_w1_spread(const double* __restrict__ lam, int64_t M, double scale, int G, int64_t ld, int W,
                 const PolyCoef* __restrict__ pc, double* __restrict__ grid,
                 double* __restrict__ phi, int2* __restrict__ org) {
-    __shared__ double s_c[kPolyMaxW][kPolyDeg + 1];
+    __shared__ double s_c[kPolyMaxW][2][kPolyDeg + 1];
     __shared__ double s_v[kW1Threads / 8][2 * kPolyMaxW];   // per group: its sample's values
-    for (int i = threadIdx.x; i < kPolyMaxW * (kPolyDeg + 1); i += kW1Threads)
-        s_c[i / (kPolyDeg + 1)][i % (kPolyDeg + 1)] = pc->c[i / (kPolyDeg + 1)][i % (kPolyDeg + 1)];
+    for (int i = threadIdx.x; i < kPolyMaxW * 2 * (kPolyDeg + 1); i += kW1Threads)
+        (&s_c[0][0][0])[i] = (&pc->c[0][0][0])[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, l = lane & 7, gi = lane >> 3;
     const unsigned gmask = 0xffu << (lane & 24);
@@ -133,9 +135,12 @@ __global__ void __launch_bounds__(kW1Threads)
             for (int p = l; p < np; p += 8) {
                 const int tap = p < W ? p : p - W;
                 const double x = p < W ? sx : sy;
-                double acc = s_c[tap][kPolyDeg];
+                const int h = x >= 0.0 ? 1 : 0;
+                const double y = fma(2.0, x, h ? -1.0 : 1.0);
+                const double* cf = s_c[tap][h];
+                double acc = cf[kPolyDeg];
 #pragma unroll
-                for (int k = kPolyDeg - 1; k >= 0; --k) acc = fma(acc, x, s_c[tap][k]);
+                for (int k = kPolyDeg - 1; k >= 0; --k) acc = fma(acc, y, cf[k]);
                 v[p] = acc;
                 phi[j * np + p] = acc;
             }
@@ -361,9 +366,10 @@ struct WeightBuffers {
     }
 };
 
-// p_l interpolates phi(s + w/2 - 1 - l), s = (x + 1) / 2, at the kPolyDeg + 1 Chebyshev points
-// x_i = cos(pi (i + 1/2) / n); the Chebyshev coefficients a_k = (2 - [k = 0]) / n sum_i f_i T_k(x_i)
-// are converted to powers of x with T_{k+1} = 2 x T_k - T_{k-1}.
+// p_{l,h} interpolates phi(s + w/2 - 1 - l), s = (x + 1) / 2, x = (y - 1) / 2 + h, at the
+// kPolyDeg + 1 Chebyshev points y_i = cos(pi (i + 1/2) / n); the Chebyshev coefficients
+// a_k = (2 - [k = 0]) / n sum_i f_i T_k(y_i) are converted to powers of y with
+// T_{k+1} = 2 y T_k - T_{k-1}.
 void window_poly(int W, double beta, PolyCoef* out) {
     const double pi = 3.14159265358979323846;
     const int n = kPolyDeg + 1;
@@ -373,30 +379,35 @@ void window_poly(int W, double beta, PolyCoef* out) {
         return q >= 0.0 ? std::exp(beta * (std::sqrt(q) - 1.0)) : 0.0;
     };
     for (int l = 0; l < kPolyMaxW; ++l)
-        for (int k = 0; k <= kPolyDeg; ++k) out->c[l][k] = 0.0;
+        for (int h = 0; h < 2; ++h)
+            for (int k = 0; k <= kPolyDeg; ++k) out->c[l][h][k] = 0.0;
     for (int l = 0; l < W; ++l) {
-        double f[kPolyDeg + 1], a[kPolyDeg + 1];
-        for (int i = 0; i < n; ++i) {
-            const double x = std::cos(pi * (i + 0.5) / n);
-            f[i] = phi_host(0.5 * (x + 1.0) + 0.5 * W - 1.0 - l);
-        }
-        for (int k = 0; k < n; ++k) {
-            double acc = 0.0;
-            for (int i = 0; i < n; ++i) acc += f[i] * std::cos(pi * k * (i + 0.5) / n);
-            a[k] = (k == 0 ? 1.0 : 2.0) * acc / n;
-        }
-        double tm[kPolyDeg + 1] = {0}, tc[kPolyDeg + 1] = {0}, tn[kPolyDeg + 1];
-        tm[0] = 1.0;                                 // T_0
-        tc[1] = 1.0;                                 // T_1
-        out->c[l][0] += a[0];
-        for (int k = 1; k < n; ++k) {
-            for (int j = 0; j <= kPolyDeg; ++j) out->c[l][j] += a[k] * tc[j];
-            if (k + 1 < n) {
-                for (int j = 0; j <= kPolyDeg; ++j)
-                    tn[j] = (j > 0 ? 2.0 * tc[j - 1] : 0.0) - tm[j];
-                for (int j = 0; j <= kPolyDeg; ++j) {
-                    tm[j] = tc[j];
-                    tc[j] = tn[j];
+        for (int h = 0; h < 2; ++h) {
+            double f[kPolyDeg + 1], a[kPolyDeg + 1];
+            for (int i = 0; i < n; ++i) {
+                const double y = std::cos(pi * (i + 0.5) / n);
+                const double x = 0.5 * (y - 1.0) + h;
+                f[i] = phi_host(0.5 * (x + 1.0) + 0.5 * W - 1.0 - l);
+            }
+            for (int k = 0; k < n; ++k) {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += f[i] * std::cos(pi * k * (i + 0.5) / n);
+                a[k] = (k == 0 ? 1.0 : 2.0) * acc / n;
+            }
+            double* c = out->c[l][h];
+            double tm[kPolyDeg + 1] = {0}, tc[kPolyDeg + 1] = {0}, tn[kPolyDeg + 1];
+            tm[0] = 1.0;                                 // T_0
+            tc[1] = 1.0;                                 // T_1
+            c[0] += a[0];
+            for (int k = 1; k < n; ++k) {
+                for (int j = 0; j <= kPolyDeg; ++j) c[j] += a[k] * tc[j];
+                if (k + 1 < n) {
+                    for (int j = 0; j <= kPolyDeg; ++j)
+                        tn[j] = (j > 0 ? 2.0 * tc[j - 1] : 0.0) - tm[j];
+                    for (int j = 0; j <= kPolyDeg; ++j) {
+                        tm[j] = tc[j];
+                        tc[j] = tn[j];
+                    }
                 }
             }
         }
