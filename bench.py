@@ -440,14 +440,16 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
     g.manual_seed(seed)
     vals = [torch.randn(p.M, dtype=torch.complex64, device=device, generator=g) for p in pings]
     M_tot = sum(p.M for p in pings)
-    # warm the kernels and the autotuner's choices for every ping class, single-ping and batched
-    # (both arms then time planning without trial launches)
-    with F.Plan(lams[0], pings[0].N, 2.0, 8) as pl:
-        pl.weights()
-        pl.adjoint(vals[0])
-    for lam, p in zip(lams, pings):
-        F.Plan(lam, p.N, 2.0, 8).close()
-    F.Batch(lams, [p.N for p in pings], 2.0, 8).close()
+    # warm the kernels, the autotuner's choices for every ping class (single-ping and batched) and
+    # the lag transforms' cuFFT plans of every ping's weights in both arms, so that neither arm
+    # times first-use work
+    for lam, p, v in zip(lams, pings, vals):
+        with F.Plan(lam, p.N, 2.0, 8) as pl:
+            pl.weights()
+            pl.adjoint(v)
+    with F.Batch(lams, [p.N for p in pings], 2.0, 8) as b:
+        b.weights()
+        b.weights()
     # plain: one ping after another
     torch.cuda.synchronize()
     t0 = time.perf_counter()
