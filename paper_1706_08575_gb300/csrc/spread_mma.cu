@@ -15,7 +15,9 @@
 // The plan regroups each tile's sorted entries into chunks of 8 samples of one column bin that
 // fit one window position (first-tap rows within yb .. yb + 8), padding the last chunk of a
 // window with flagged empty slots; consecutive windows of a bin move down by 8 rows, so that the
-// window's accumulator, held in the MMA's D fragments, only ever shifts by its lower half. Each
+// window's accumulator, held in the MMA's D fragments, only ever loses its lower half (that half
+// is flushed and cleared, and the two D halves swap roles: the A operands are routed to the
+// half that holds each window row, so no register moves). Each
 // warp of the tile's CTA takes a contiguous range of chunks; windows that are left or shifted
 // are added to the tile's shared accumulator with shared-memory atomics, and the tile is stored
 // once (coalesced) with its halo strips, exactly as the register-window kernel does.

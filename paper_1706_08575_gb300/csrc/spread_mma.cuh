@@ -26,10 +26,16 @@ constexpr int kBatchUnroll = FTCG_MMA_UNROLL ? 4 : 1;
 // padding chunks after the last one (a read past the end stays inside the array)
 constexpr int kPrefetchChunks = 1;
 
-// Dynamic shared memory of one tile: the two accumulator planes of the (T + 7)^2 block, then
-// each warp's staging buffers (32 slots of 16 bytes, 32 row offsets, 4 chunk headers).
+// Rows of the tile's accumulator planes: a window starts on a row of the tile (0..T-1) and its
+// upper half reaches row T + 14; rows past T + 6 only ever receive zeros, so flushes need no
+// bounds test.
+__host__ __device__ constexpr int acc_rows(int T) { return T + 2 * kMmaMaxW - 1; }
+
+// Dynamic shared memory of one tile: the two accumulator planes (acc_rows(T) rows of T + 8
+// floats), then each warp's staging buffers (32 slots of 16 bytes, 32 row offsets, 4 chunk
+// headers).
 __host__ __device__ constexpr size_t tile_smem_bytes(int T) {
-    return (size_t)2 * (T + kMmaMaxW - 1) * (T + kMmaMaxW) * sizeof(float) +
+    return (size_t)2 * acc_rows(T) * (T + kMmaMaxW) * sizeof(float) +
            (size_t)kWarps * (32 * (16 + sizeof(int)) + 4 * sizeof(uint32_t));
 }
 
@@ -98,10 +104,10 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                                             float2* __restrict__ grid, int G, int ntx, int W,
                                             const MmaPoly& poly, float2* __restrict__ halo_buf,
                                             int halo_cells, int tile, float* smem) {
-    constexpr int PT = T + kMmaMaxW - 1;     // accumulator side (tile + overflow strips)
-    constexpr int LD = PT + 1;
+    constexpr int PR = acc_rows(T);          // accumulator rows
+    constexpr int LD = T + kMmaMaxW;         // row pitch: the tile + overflow columns, + 1
     float* s_re = smem;
-    float* s_im = smem + PT * LD;
+    float* s_im = smem + PR * LD;
     const int c0 = tile_chunk[tile], c1 = tile_chunk[tile + 1];
     const int tyi = tile / ntx, txi = tile - tyi * ntx;
     const int X0 = txi * T, Y0 = tyi * T;
@@ -110,7 +116,7 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
         tile::store_zero_tile<kThreads>(grid, G, X0, Y0, Tw, Th);
         return;
     }
-    for (int i = threadIdx.x; i < 2 * PT * LD; i += kThreads) smem[i] = 0.0f;
+    for (int i = threadIdx.x; i < 2 * PR * LD; i += kThreads) smem[i] = 0.0f;
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -121,29 +127,44 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
     const int n = c1 - c0;
     const int ca = c0 + (int)((int64_t)n * warp / kWarps);
     const int cb = c0 + (int)((int64_t)n * (warp + 1) / kWarps);
-    // D fragments: real and imaginary plane, rows g (d[0], d[1]) and g + 8 (d[2], d[3]) of the
-    // window, columns 2t and 2t + 1
-    // the hi x hi products and the two cross products accumulate separately, so that the MMAs
-    // of a chunk do not wait on one another
+    // D fragments: real and imaginary plane, rows g (d[0], d[1]) and g + 8 (d[2], d[3]),
+    // columns 2t and 2t + 1; the hi x hi products and the two cross products accumulate
+    // separately, so that the MMAs of a chunk do not wait on one another. The window's lower
+    // half (rows yb .. yb + 7) lives in D half ph (0: rows g, 1: rows g + 8): a window that moves
+    // down by 8 rows flushes and clears that half and flips ph instead of moving registers.
     float dr[4] = {0.f, 0.f, 0.f, 0.f}, di[4] = {0.f, 0.f, 0.f, 0.f};
     float er[4] = {0.f, 0.f, 0.f, 0.f}, ei[4] = {0.f, 0.f, 0.f, 0.f};
-    int cur_cx = -1, cur_yb = 0;
-    auto flush_half = [&](int h) {             // window rows g + 8h into the tile accumulator
-        const int row = cur_yb + g + 8 * h;
-        if (row < PT) {
-            const int o = row * LD + cur_cx + 2 * t;   // cur_cx + 2t + 1 <= T + 6 < PT
-            atomicAdd(s_re + o, dr[2 * h] + er[2 * h]);
-            atomicAdd(s_re + o + 1, dr[2 * h + 1] + er[2 * h + 1]);
-            atomicAdd(s_im + o, di[2 * h] + ei[2 * h]);
-            atomicAdd(s_im + o + 1, di[2 * h + 1] + ei[2 * h + 1]);
+    int cur_cx = -1, cur_yb = 0, ph = 0;
+    auto flush_d0 = [&](int o) {               // D rows g into the accumulator at offset o
+        atomicAdd(s_re + o, dr[0] + er[0]);
+        atomicAdd(s_re + o + 1, dr[1] + er[1]);
+        atomicAdd(s_im + o, di[0] + ei[0]);
+        atomicAdd(s_im + o + 1, di[1] + ei[1]);
+        dr[0] = dr[1] = di[0] = di[1] = er[0] = er[1] = ei[0] = ei[1] = 0.f;
+    };
+    auto flush_d1 = [&](int o) {               // D rows g + 8
+        atomicAdd(s_re + o, dr[2] + er[2]);
+        atomicAdd(s_re + o + 1, dr[3] + er[3]);
+        atomicAdd(s_im + o, di[2] + ei[2]);
+        atomicAdd(s_im + o + 1, di[3] + ei[3]);
+        dr[2] = dr[3] = di[2] = di[3] = er[2] = er[3] = ei[2] = ei[3] = 0.f;
+    };
+    auto flush_window = [&]() {                // both halves (window rows cur_yb + g, + 8)
+        const int o = (cur_yb + g) * LD + cur_cx + 2 * t;
+        if (ph) {
+            flush_d1(o);
+            flush_d0(o + 8 * LD);
+        } else {
+            flush_d0(o);
+            flush_d1(o + 8 * LD);
         }
     };
 
     // per-warp staging buffers after the accumulator planes
-    StagedSlot* st_slot = reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) + warp * kStageSlots;
-    int* st_off = reinterpret_cast<int*>(reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) +
+    StagedSlot* st_slot = reinterpret_cast<StagedSlot*>(smem + 2 * PR * LD) + warp * kStageSlots;
+    int* st_off = reinterpret_cast<int*>(reinterpret_cast<StagedSlot*>(smem + 2 * PR * LD) +
                                          kWarps * kStageSlots) + warp * kStageSlots;
-    uint32_t* st_hdr = reinterpret_cast<uint32_t*>(reinterpret_cast<StagedSlot*>(smem + 2 * PT * LD) +
+    uint32_t* st_hdr = reinterpret_cast<uint32_t*>(reinterpret_cast<StagedSlot*>(smem + 2 * PR * LD) +
                                                    kWarps * kStageSlots) +
                        kWarps * kStageSlots + warp * kStageChunks;
     if (ca < cb) {
@@ -175,25 +196,15 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                 const uint32_t h = st_hdr[k];
                 const int cx = (int)(h & 0xffu), yb = (int)((h >> 8) & 0xffu);
                 if (cx != cur_cx || (yb != cur_yb && yb != cur_yb + 8)) {   // a new window
-                    if (cur_cx >= 0) {
-                        flush_half(0);
-                        flush_half(1);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) dr[i] = di[i] = er[i] = ei[i] = 0.f;
+                    if (cur_cx >= 0) flush_window();
                     cur_cx = cx;
                     cur_yb = yb;
+                    ph = 0;
                 } else if (yb != cur_yb) {         // the window moves down by 8 rows
-                    flush_half(0);
-                    dr[0] = dr[2];
-                    dr[1] = dr[3];
-                    di[0] = di[2];
-                    di[1] = di[3];
-                    er[0] = er[2];
-                    er[1] = er[3];
-                    ei[0] = ei[2];
-                    ei[1] = ei[3];
-                    dr[2] = dr[3] = di[2] = di[3] = er[2] = er[3] = ei[2] = ei[3] = 0.f;
+                    const int o = (cur_yb + g) * LD + cur_cx + 2 * t;
+                    if (ph) flush_d1(o);
+                    else flush_d0(o);
+                    ph ^= 1;
                     cur_yb = yb;
                 }
                 const StagedSlot e1 = st_slot[k * kMmaChunk + t];
@@ -207,7 +218,8 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                 // samples)
                 const float a1 = __shfl_sync(0xffffffffu, fy1, (((g - off1) & 7) << 2) | t);
                 const float a2 = __shfl_sync(0xffffffffu, fy2, (((g - off2) & 7) << 2) | t);
-                const bool low1 = g >= off1, low2 = g >= off2;
+                // window row g (lower half) or g + 8, mapped to the D half that holds it
+                const bool low1 = (g >= off1) != (ph != 0), low2 = (g >= off2) != (ph != 0);
                 uint32_t a1h, a1l, a2h, a2l;
                 split_tf32(a1, a1h, a1l);
                 split_tf32(a2, a2h, a2l);
@@ -228,8 +240,7 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                 mma_tf32(ei, al0, al1, al2, al3, b1ih, b2ih);
             }
         }
-        flush_half(0);
-        flush_half(1);
+        flush_window();
     }
     __syncthreads();
     tile::store_tile<true, kThreads>(s_re, s_im, LD, grid, G, X0, Y0, Tw, Th, T, W,
