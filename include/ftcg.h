@@ -77,8 +77,14 @@ enum { FTCG_LAYOUT_AUTO = 0, FTCG_LAYOUT_DUPLICATE = 1, FTCG_LAYOUT_HALO = 2 };
  *            sigma >= 1.25, w = 6 at sigma = 2); NOT_SUPPORTED elsewhere. */
 enum { FTCG_SPREAD_AUTO = 0, FTCG_SPREAD_WINDOW = 1, FTCG_SPREAD_TENSOR = 2 };
 
+/* Gridding window (Sec. III-A leaves the choice open; the exact weights' internal lag route
+ * always uses ES): exponential of semicircle exp(beta (sqrt(1 - z^2) - 1)), Kaiser-Bessel
+ * I0(beta sqrt(1 - z^2)) / I0(beta) and truncated Gaussian exp(-beta z^2), z = 2 t / w, zero for
+ * |z| > 1; beta from w and sigma as ftcg_plan_info reports. */
+enum { FTCG_WINDOW_ES = 0, FTCG_WINDOW_KB = 1, FTCG_WINDOW_GAUSS = 2 };
+
 typedef struct {
-    int32_t kernel;        /* 0 = ES (the only window of this build)                            */
+    int32_t kernel;        /* FTCG_WINDOW_ES (default), _KB or _GAUSS                          */
     int32_t precision;     /* FTCG_PREC_FP32 (default) or FTCG_PREC_BF16 weight storage        */
     int32_t tile;          /* fine-grid tile side of the spreading kernel: 0 = auto, 32 or 64 */
     int32_t weight_width;  /* window width of the FP64 weight construction: 0 = 12, else 4..16 */

@@ -84,7 +84,7 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
                            p->opts.layout == FTCG_LAYOUT_HALO, p->status, p->samp, s, &bytes));
     if (p->bin.halo && p->opts.spread_kernel != FTCG_SPREAD_WINDOW && p->w <= kMmaMaxW) {
         double err = 0;
-        if (mma_window_poly(p->w, p->win.beta, &p->bin.poly, &err))
+        if (mma_window_poly(p->w, p->win.beta, p->win.kind, &p->bin.poly, &err))
             FTCG_TRY(build_chunks(p->bin, s, &bytes));
     }
     if (own_grid) {
@@ -123,20 +123,24 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
         return invalid("ftcg_plan: opts.layout must be 0, 1 or 2");
     if (o.spread_kernel < FTCG_SPREAD_AUTO || o.spread_kernel > FTCG_SPREAD_TENSOR)
         return invalid("ftcg_plan: opts.spread_kernel must be 0, 1 or 2");
+    if (o.kernel < FTCG_WINDOW_ES || o.kernel > FTCG_WINDOW_GAUSS)
+        return invalid("ftcg_plan: opts.kernel must be 0 (ES), 1 (Kaiser-Bessel) or 2 (Gaussian)");
+    const double beta = kernel_beta(w, sigma, o.kernel);
+    if (!std::isfinite(beta)) {
+        set_error("ftcg_plan: no Kaiser-Bessel shape parameter for w = %d, sigma = %g "
+                  "((w / sigma)^2 (sigma - 1/2)^2 <= 0.8)", w, sigma);
+        return FTCG_ERR_NOT_SUPPORTED;
+    }
     if (o.spread_kernel == FTCG_SPREAD_TENSOR) {
         MmaPoly poly;
         double err = 0;
         if (o.layout == FTCG_LAYOUT_DUPLICATE || w > kMmaMaxW ||
-            !mma_window_poly(w, es_beta(w, sigma), &poly, &err)) {
+            !mma_window_poly(w, beta, o.kernel, &poly, &err)) {
             set_error("ftcg_plan: the tensor-core spreading kernel needs the halo layout, w <= 8 "
                       "and a window within 1e-6 of its tap polynomials (w = %d, sigma = %g: %.1e)",
                       w, sigma, err);
             return FTCG_ERR_NOT_SUPPORTED;
         }
-    }
-    if (o.kernel != 0) {
-        set_error("ftcg_plan: only the ES window (kernel 0) is built");
-        return FTCG_ERR_NOT_SUPPORTED;
     }
     if (o.precision != FTCG_PREC_FP32 && o.precision != FTCG_PREC_BF16)
         return invalid("ftcg_plan: opts.precision must be 0 (FP32) or 1 (BF16)");
@@ -263,7 +267,7 @@ ftcg_status_t ftcg_plan(ftcg_plan_t* out, const double* d_lambda, int64_t M, int
     p->w = w;
     p->sigma = sigma;
     p->opts = o;
-    p->win = Window{w, es_beta(w, sigma)};
+    p->win = Window{w, kernel_beta(w, sigma, o.kernel), o.kernel};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->last_stream = s;
     if (o.tile == 0 || o.layout == FTCG_LAYOUT_AUTO) {

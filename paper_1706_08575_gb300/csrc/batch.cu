@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
 template <int GW, int WT, bool VBF, bool ABF, int CPL>
 __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
     k_spread_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items, int nitems,
-                   int* __restrict__ counter, int Wrt, float beta, float inv_hw) {
+                   int* __restrict__ counter, int Wrt, Win32 win) {
     extern __shared__ float smem[];
     __shared__ int s_item;
     for (;;) {
@@ -93,20 +93,20 @@ __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
         if (d.halo) {
             if (d.T == 64)
                 tile::spread_tile<GW, WT, 64, VBF, ABF, true, CPL>(d.ent, d.colptr, d.vals, d.grid, d.G,
-                                                              d.ntx, Wrt, beta, inv_hw, pt.y, smem,
+                                                              d.ntx, Wrt, win, pt.y, smem,
                                                               d.halo_buf, d.halo_cells);
             else
                 tile::spread_tile<GW, WT, 32, VBF, ABF, true, CPL>(d.ent, d.colptr, d.vals, d.grid, d.G,
-                                                              d.ntx, Wrt, beta, inv_hw, pt.y, smem,
+                                                              d.ntx, Wrt, win, pt.y, smem,
                                                               d.halo_buf, d.halo_cells);
         } else {
             if (d.T == 64)
                 tile::spread_tile<GW, WT, 64, VBF, ABF, false, CPL>(d.ent, d.colptr, d.vals, d.grid,
-                                                               d.G, d.ntx, Wrt, beta, inv_hw, pt.y,
+                                                               d.G, d.ntx, Wrt, win, pt.y,
                                                                smem, nullptr, 0);
             else
                 tile::spread_tile<GW, WT, 32, VBF, ABF, false, CPL>(d.ent, d.colptr, d.vals, d.grid,
-                                                               d.G, d.ntx, Wrt, beta, inv_hw, pt.y,
+                                                               d.G, d.ntx, Wrt, win, pt.y,
                                                                smem, nullptr, 0);
         }
     }
@@ -162,6 +162,7 @@ struct TuneKey {
     int G, w, prec, bucket, tile, layout;   // tile / layout: the caller's fixed choices (0 = free)
     int skern;                              // the caller's spreading-kernel choice
     int batch;                              // 1: chosen for pings of a batch (timed batched)
+    int win;                                // the gridding window (FTCG_WINDOW_*)
     bool operator<(const TuneKey& o) const {
         if (G != o.G) return G < o.G;
         if (w != o.w) return w < o.w;
@@ -170,7 +171,8 @@ struct TuneKey {
         if (tile != o.tile) return tile < o.tile;
         if (layout != o.layout) return layout < o.layout;
         if (skern != o.skern) return skern < o.skern;
-        return batch < o.batch;
+        if (batch != o.batch) return batch < o.batch;
+        return win < o.win;
     }
 };
 // the tuner's choice for a key: tile side, layout and spreading kernel
@@ -244,7 +246,8 @@ std::vector<TuneVal> tune_candidates(int w, double sigma, const ftcg_opts_t& opt
     else layouts = {FTCG_LAYOUT_DUPLICATE, FTCG_LAYOUT_HALO};
     MmaPoly poly;
     double perr = 0;
-    const bool tensor_ok = w <= kMmaMaxW && mma_window_poly(w, es_beta(w, sigma), &poly, &perr);
+    const bool tensor_ok = w <= kMmaMaxW && mma_window_poly(w, kernel_beta(w, sigma, opts.kernel),
+                                                            opts.kernel, &poly, &perr);
     std::vector<TuneVal> out;
     for (int T : tiles)
         for (int layout : layouts) {
@@ -265,7 +268,7 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
                         int* skern_out) {
     const int G = (int)std::llround(sigma * N);
     const TuneKey key{G, w, opts.precision, density_bucket(M, G), opts.tile, opts.layout,
-                      opts.spread_kernel, 0};
+                      opts.spread_kernel, 0, opts.kernel};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -302,7 +305,7 @@ ftcg_status_t tune_tile(const double* d_lambda, int64_t M, int N, double sigma, 
         p->opts.tile = c.T;
         p->opts.layout = c.layout;
         p->opts.spread_kernel = c.skern;
-        p->win = Window{w, es_beta(w, sigma)};
+        p->win = Window{w, kernel_beta(w, sigma, opts.kernel), opts.kernel};
         ftcg_status_t st = make_plan(p, d_lambda, s, false);
         float ms = 1e30f;
         if (st == FTCG_SUCCESS || st == FTCG_ERR_NUMERIC) st = time_spread(*p, zeros, grid, s, &ms);
@@ -403,10 +406,10 @@ ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
                                                               smem));
         b.persistent_ctas = std::max(1, sms * std::max(1, per));
     }
-    const float beta = (float)es_beta(b.w, b.sigma);
-    const float inv_hw = (float)(2.0 / b.w);
+    const Win32 win = win32_of(Window{b.w, kernel_beta(b.w, b.sigma, b.opts.kernel),
+                                      b.opts.kernel});
     kern<<<b.persistent_ctas, tile::kSpreadThreads, smem, s>>>(
-        b.d_desc, b.d_items + b.n_mma, b.nitems - b.n_mma, b.d_counter + 1, b.w, beta, inv_hw);
+        b.d_desc, b.d_items + b.n_mma, b.nitems - b.n_mma, b.d_counter + 1, b.w, win);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
 }
@@ -609,7 +612,7 @@ ftcg_status_t make_plans_parallel(const std::vector<Plan*>& pings, const double*
 // The tuner key of a ping of batch b (batch = 1: chosen by timing batched launches).
 TuneKey batch_key(const Batch& b, int64_t M, int G) {
     return TuneKey{G, b.w, b.opts.precision, density_bucket(M, G), b.opts.tile, b.opts.layout,
-                   b.opts.spread_kernel, 1};
+                   b.opts.spread_kernel, 1, b.opts.kernel};
 }
 
 ftcg_status_t tune_batch(const Batch& b, const double* const* d_lambda, const int64_t* M,
@@ -653,7 +656,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         p->opts.tile = T;
         p->opts.layout = layout;
         p->opts.spread_kernel = skern;
-        p->win = Window{b.w, es_beta(b.w, b.sigma)};
+        p->win = Window{b.w, kernel_beta(b.w, b.sigma, b.opts.kernel), b.opts.kernel};
         b.pings.push_back(p);
     }
     std::vector<ftcg_status_t> sts(b.n, FTCG_SUCCESS);
@@ -1270,10 +1273,11 @@ ftcg_status_t ftcg_tuner_save(const char* path) {
         std::fprintf(f,
                      "{\"G\": %d, \"w\": %d, \"precision\": %d, \"bucket\": %d, "
                      "\"tile_req\": %d, \"layout_req\": %d, \"spread_req\": %d, "
-                     "\"batch\": %d, \"tile\": %d, \"layout\": %d, \"spread\": %d}%s\n",
+                     "\"batch\": %d, \"window\": %d, \"tile\": %d, \"layout\": %d, "
+                     "\"spread\": %d}%s\n",
                      e.first.G, e.first.w, e.first.prec, e.first.bucket, e.first.tile,
-                     e.first.layout, e.first.skern, e.first.batch, e.second.T, e.second.layout,
-                     e.second.skern, ++k < snap.size() ? "," : "");
+                     e.first.layout, e.first.skern, e.first.batch, e.first.win, e.second.T,
+                     e.second.layout, e.second.skern, ++k < snap.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
     if (std::fclose(f) != 0) {
@@ -1312,6 +1316,7 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
         if (!json_int(line, "spread_req", &k.skern)) k.skern = FTCG_SPREAD_AUTO;   // older files
         if (!json_int(line, "spread", &spread)) spread = FTCG_SPREAD_AUTO;
         if (!json_int(line, "batch", &k.batch)) k.batch = 0;
+        if (!json_int(line, "window", &k.win)) k.win = FTCG_WINDOW_ES;
         const bool ok = json_int(line, "G", &k.G) && json_int(line, "w", &k.w) &&
                         json_int(line, "precision", &k.prec) &&
                         json_int(line, "bucket", &k.bucket) &&
@@ -1328,6 +1333,7 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
                            (spread != FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
                            (k.skern == FTCG_SPREAD_AUTO || spread == k.skern) &&
                            (k.batch == 0 || k.batch == 1) &&
+                           (k.win >= FTCG_WINDOW_ES && k.win <= FTCG_WINDOW_GAUSS) &&
                            (tile == 32 || tile == 64) &&
                            (layout == FTCG_LAYOUT_DUPLICATE || layout == FTCG_LAYOUT_HALO) &&
                            (k.tile == 0 || k.tile == tile) && (k.layout == 0 || k.layout == layout);

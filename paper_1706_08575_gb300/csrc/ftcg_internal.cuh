@@ -115,6 +115,14 @@ struct MmaPoly {
 struct Window {
     int w;
     double beta;
+    int kind = FTCG_WINDOW_ES;             // FTCG_WINDOW_ES, _KB or _GAUSS
+};
+
+// The gridding window in FP32 on the device (one of three families, shape parameter beta, with
+// inv_hw = 2 / w and norm = 1 / I0(beta) for Kaiser-Bessel).
+struct Win32 {
+    float beta, inv_hw, norm;
+    int kind;
 };
 
 // Launch with programmatic dependent launch: the kernel may be scheduled while the previous
@@ -253,7 +261,7 @@ ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2*
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s);
 // spread_mma.cu: the tensor-core spreading path (halo layout, w <= 8)
 // fit the per-tap window polynomials; returns false if their error exceeds the path's bound
-bool mma_window_poly(int W, double beta, MmaPoly* out, double* max_err);
+bool mma_window_poly(int W, double beta, int kind, MmaPoly* out, double* max_err);
 ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes);
 void free_chunks(Binning& b);
 ftcg_status_t launch_spread_mma(const Plan& p, const void* vals, bool vbf, float2* grid,
@@ -357,6 +365,9 @@ ftcg_status_t forward_device(Plan* p, const void* img, void* vals, cudaStream_t 
 // window.cu
 ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cudaStream_t s);
 double es_beta(int w, double sigma);
+double kernel_beta(int w, double sigma, int kind);
+double window64(double t, int w, double beta, int kind);   // the window in FP64 on the host
+Win32 win32_of(const Window& win);
 // weights.cu
 ftcg_status_t compute_weights(Plan& p, double* d_alpha_out, cudaStream_t s);
 // judge.cu: exact Fejer sums at K samples, the verdict, and its installation

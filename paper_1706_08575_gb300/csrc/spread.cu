@@ -22,19 +22,19 @@ namespace ftcg {
 namespace {
 
 using tile::kSpreadThreads;
-using tile::es32;
+using tile::win32;
 
 template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL>
 __global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
     k_spread(const Entry* __restrict__ ent, const int* __restrict__ colptr,
              const int* __restrict__ tile_order, const void* __restrict__ vals,
-             float2* __restrict__ grid, int G, int ntx, int Wrt, float beta, float inv_hw,
+             float2* __restrict__ grid, int G, int ntx, int Wrt, Win32 win,
              float2* __restrict__ halo_buf, int halo_cells) {
     extern __shared__ float smem[];
     pdl_allow_next();                          // the fix-up may be scheduled during the tail
     const int t = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
-    tile::spread_tile<GW, WT, T, VBF, ABF, HALO, CPL>(ent, colptr, vals, grid, G, ntx, Wrt, beta,
-                                                      inv_hw, t, smem, halo_buf, halo_cells);
+    tile::spread_tile<GW, WT, T, VBF, ABF, HALO, CPL>(ent, colptr, vals, grid, G, ntx, Wrt, win,
+                                                      t, smem, halo_buf, halo_cells);
 }
 
 // one CTA per non-empty tile (the first n_nonempty of the heaviest-first order)
@@ -57,10 +57,8 @@ ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStre
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
-    const float beta = (float)p.win.beta;
-    const float inv_hw = (float)(2.0 / p.win.w);
     kern<<<nt, kSpreadThreads, smem, s>>>(b.ent, b.colptr, b.tile_order, vals, grid, b.G,
-                                                b.ntx, b.W, beta, inv_hw, b.halo_buf,
+                                                b.ntx, b.W, win32_of(p.win), b.halo_buf,
                                                 b.halo_cells);
     FTCG_CK(cudaGetLastError());
     if (HALO) return launch_halo_add(p, grid, s);
@@ -118,7 +116,7 @@ __global__ void k_pad_apod(const float2* __restrict__ img, float2* __restrict__ 
 template <int GW>
 __global__ void __launch_bounds__(256)
     k_interp(const int4* __restrict__ samp, int64_t M, const float2* __restrict__ grid,
-             float2* __restrict__ out, int G, int W, float beta, float inv_hw) {
+             float2* __restrict__ out, int G, int W, Win32 win) {
     const int l = threadIdx.x % GW;
     const unsigned gmask = ((1u << GW) - 1u) << ((threadIdx.x & 31) & ~(GW - 1));
     const int64_t groups_total = (int64_t)gridDim.x * (blockDim.x / GW);
@@ -129,8 +127,8 @@ __global__ void __launch_bounds__(256)
         if (sm.x >= 0) {
             const float dx = __int_as_float(sm.z), dy = __int_as_float(sm.w);
             const bool lane_tap = l < W;
-            const float fx = lane_tap ? es32(dx - (float)l, inv_hw, beta) : 0.0f;
-            const float fy = lane_tap ? es32(dy - (float)l, inv_hw, beta) : 0.0f;
+            const float fx = lane_tap ? win32(dx - (float)l, win) : 0.0f;
+            const float fy = lane_tap ? win32(dy - (float)l, win) : 0.0f;
             int col = sm.x + l;
             if (col >= G) col -= G;
             for (int r = 0; r < W; ++r) {
@@ -232,14 +230,13 @@ ftcg_status_t launch_pad_apod(const Plan& p, const float2* img, float2* grid, cu
 
 ftcg_status_t launch_interp(const Plan& p, const float2* grid, float2* vals, cudaStream_t s) {
     if (p.M == 0) return FTCG_SUCCESS;
-    const float beta = (float)p.win.beta;
-    const float inv_hw = (float)(2.0 / p.win.w);
+    const Win32 win = win32_of(p.win);
     if (p.w <= 8) {
         k_interp<8><<<blocks_for(p.M * 8, 256), 256, 0, s>>>(p.samp, p.M, grid, vals, p.G, p.w,
-                                                             beta, inv_hw);
+                                                             win);
     } else {
         k_interp<16><<<blocks_for(p.M * 16, 256), 256, 0, s>>>(p.samp, p.M, grid, vals, p.G, p.w,
-                                                               beta, inv_hw);
+                                                               win);
     }
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;

@@ -39,18 +39,12 @@ namespace {
 
 constexpr double kMmaPolyBound = 1e-6;
 
-// The ES window in FP64 (the definition every path shares; see window.cu for its transform).
-double es64(double t, int W, double beta) {
-    const double z = 2.0 * t / W;
-    if (std::fabs(z) > 1.0) return 0.0;
-    return std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
-}
-
 }  // namespace
 
 // Chebyshev interpolation of phi(s + w/2 - 1/2 - l) on s in [-1/2, 1/2] at the 8 Chebyshev
-// points, converted to monomial coefficients in s. The error is measured on 257 points per tap.
-bool mma_window_poly(int W, double beta, MmaPoly* out, double* max_err) {
+// points (phi the plan's window, in FP64), converted to monomial coefficients in s. The error is
+// measured on 257 points per tap.
+bool mma_window_poly(int W, double beta, int kind, MmaPoly* out, double* max_err) {
     std::memset(out, 0, sizeof(*out));
     *max_err = 0.0;
     if (W > kMmaMaxW || W < 2) {
@@ -64,7 +58,7 @@ bool mma_window_poly(int W, double beta, MmaPoly* out, double* max_err) {
         double f[n], y[n];
         for (int k = 0; k < n; ++k) {
             y[k] = std::cos(M_PI * (k + 0.5) / n);     // in [-1, 1], s = y / 2
-            f[k] = es64(0.5 * y[k] + shift, W, beta);
+            f[k] = window64(0.5 * y[k] + shift, W, beta, kind);
         }
         // Chebyshev coefficients in y
         double cheb[n];
@@ -101,7 +95,7 @@ bool mma_window_poly(int W, double beta, MmaPoly* out, double* max_err) {
             const double s = -0.5 + i / 256.0;
             double p = c[n - 1];
             for (int k = n - 2; k >= 0; --k) p = p * s + c[k];
-            worst = std::max(worst, std::fabs(p - es64(s + shift, W, beta)));
+            worst = std::max(worst, std::fabs(p - window64(s + shift, W, beta, kind)));
         }
     }
     *max_err = worst;

@@ -32,13 +32,19 @@ constexpr int kSpreadThreads = FTCG_SPREAD_THREADS;
 constexpr int kCpl8 = FTCG_SPREAD_CPL8, kCpl16 = FTCG_SPREAD_CPL16;
 constexpr int kSpreadUnroll = FTCG_SPREAD_UNROLL;
 
-// ES window in FP32: exp(beta (sqrt(1 - z^2) - 1)) written as exp(-beta z^2 / (1 + sqrt(1 - z^2)))
-// so that no cancellation occurs near the centre (sqrt(1 - z^2) - 1 loses all its digits there).
-__device__ __forceinline__ float es32(float t, float inv_hw, float beta) {
-    const float z = t * inv_hw;
+// The gridding window in FP32 at offset t (cells), zero outside |t| <= w/2. ES:
+// exp(beta (sqrt(1 - z^2) - 1)) written as exp(-beta z^2 / (1 + sqrt(1 - z^2))) so that no
+// cancellation occurs near the centre (sqrt(1 - z^2) - 1 loses all its digits there); Kaiser-
+// Bessel: I0(beta sqrt(1 - z^2)) / I0(beta); truncated Gaussian: exp(-beta z^2). The family is
+// uniform across a launch, so the branch costs no divergence.
+__device__ __forceinline__ float win32(float t, const Win32& w) {
+    const float z = t * w.inv_hw;
     const float z2 = z * z;
     const float q = 1.0f - z2;
-    return q >= 0.0f ? __expf(__fdividef(-beta * z2, 1.0f + sqrtf(q))) : 0.0f;
+    if (!(q >= 0.0f)) return 0.0f;
+    if (w.kind == FTCG_WINDOW_KB) return cyl_bessel_i0f(w.beta * sqrtf(q)) * w.norm;
+    if (w.kind == FTCG_WINDOW_GAUSS) return __expf(-w.beta * z2);
+    return __expf(__fdividef(-w.beta * z2, 1.0f + sqrtf(q)));
 }
 
 // A BF16-stored weight is a float32 whose low 16 bits are zero (the bfloat16 rounding of the
@@ -125,7 +131,7 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
                                             const int* __restrict__ colptr,
                                             const void* __restrict__ vals,
                                             float2* __restrict__ grid, int G, int ntx, int Wrt,
-                                            float beta, float inv_hw, int tile, float* smem,
+                                            Win32 win, int tile, float* smem,
                                             float2* __restrict__ halo_buf, int halo_cells) {
     constexpr int WMAX = WT > 0 ? WT : GW * CPL;
     static_assert(WMAX <= GW * CPL, "a group must cover the kernel width");
@@ -213,8 +219,8 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
         float xr[CPL], xi[CPL], fy[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-            const float fx = tap[c] ? es32(e.dx - (float)(l + c * GW), inv_hw, beta) : 0.0f;
-            fy[c] = tap[c] ? es32(e.dy - (float)(l + c * GW), inv_hw, beta) : 0.0f;
+            const float fx = tap[c] ? win32(e.dx - (float)(l + c * GW), win) : 0.0f;
+            fy[c] = tap[c] ? win32(e.dy - (float)(l + c * GW), win) : 0.0f;
             const float ax = al * fx;
             xr[c] = v.x * ax;
             xi[c] = v.y * ax;

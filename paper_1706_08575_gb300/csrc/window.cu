@@ -4,7 +4,8 @@
 // grid, division by phi^(p / G) (the m = 0 term of the Poisson sum of Eq. twodcg):
 //     phi^(xi) = int phi(t) exp(-2 pi i xi t) dt = 2 int_0^{pi/2} phi(w/2 sin th) cos(pi w xi sin th)
 //                (w/2) cos th dth,
-// the substitution t = (w/2) sin th removing the square-root edge of the ES window. The integral
+// the substitution t = (w/2) sin th removing the square-root edge of the ES and Kaiser-Bessel
+// windows (the truncated Gaussian is smooth inside its support). The integral
 // is taken by Gauss-Legendre quadrature whose nodes are computed here by Newton iteration on the
 // Legendre polynomial P_n (three-term recurrence), then the N reciprocals are evaluated in FP64.
 
@@ -64,7 +65,7 @@ struct Quad {
 };
 
 __global__ void k_window_factors(double* __restrict__ out, int N, int G, int W, double beta,
-                                 Quad q) {
+                                 int kind, Quad q) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double pi = 3.14159265358979323846;
@@ -74,7 +75,11 @@ __global__ void k_window_factors(double* __restrict__ out, int N, int G, int W, 
     for (int k = 0; k < kQuadNodes; ++k) {
         double sn, cs;
         sincos(q.th[k], &sn, &cs);
-        double ph = exp(beta * (cs - 1.0));           // ES at t = (w/2) sin th
+        // the window at t = (w/2) sin th, where sqrt(1 - (2t/w)^2) = cos th
+        double ph;
+        if (kind == FTCG_WINDOW_KB) ph = cyl_bessel_i0(beta * cs) / cyl_bessel_i0(beta);
+        else if (kind == FTCG_WINDOW_GAUSS) ph = exp(-beta * sn * sn);
+        else ph = exp(beta * (cs - 1.0));
         s += q.wt[k] * ph * cos(2.0 * pi * xi * half * sn) * half * cs;
     }
     out[i] = 1.0 / (2.0 * s);
@@ -87,18 +92,51 @@ double es_beta(int w, double sigma) {
     return 0.97 * pi * (1.0 - 0.5 / sigma) * w;
 }
 
+// Shape parameter of each window family for width w and oversampling sigma: ES as es_beta
+// (Barnett, Magland, af Klinteberg 2019); Kaiser-Bessel beta = pi sqrt((w/sigma)^2 (sigma - 1/2)^2
+// - 0.8) (Beatty, Nishimura, Pauly 2005; NaN where the root is not real); truncated Gaussian
+// exp(-beta z^2) with beta = (pi w / 2) (1 - 1/(2 sigma)).
+double kernel_beta(int w, double sigma, int kind) {
+    const double pi = 3.14159265358979323846;
+    if (kind == FTCG_WINDOW_KB) {
+        const double a = (w / sigma) * (w / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8;
+        return a > 0.0 ? pi * std::sqrt(a) : std::nan("");
+    }
+    if (kind == FTCG_WINDOW_GAUSS) return 0.5 * pi * w * (1.0 - 0.5 / sigma);
+    return es_beta(w, sigma);
+}
+
+Win32 win32_of(const Window& win) {
+    Win32 r;
+    r.beta = (float)win.beta;
+    r.inv_hw = (float)(2.0 / win.w);
+    r.norm = win.kind == FTCG_WINDOW_KB ? (float)(1.0 / std::cyl_bessel_i(0.0, win.beta)) : 1.0f;
+    r.kind = win.kind;
+    return r;
+}
+
+double window64(double t, int w, double beta, int kind) {
+    const double z = 2.0 * t / w;
+    if (std::fabs(z) > 1.0) return 0.0;
+    if (kind == FTCG_WINDOW_KB) return std::cyl_bessel_i(0.0, beta * std::sqrt(1.0 - z * z)) /
+                                       std::cyl_bessel_i(0.0, beta);
+    if (kind == FTCG_WINDOW_GAUSS) return std::exp(-beta * z * z);
+    return std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
+}
+
 namespace {
 
 // Factors already computed, per (device, N, G, w, beta): plans of the same shape (ping after
 // ping) copy them instead of repeating the FP64 quadrature. Held until the process exits.
 struct FactorKey {
-    int dev, N, G, w;
+    int dev, N, G, w, kind;
     uint64_t beta_bits;
     bool operator<(const FactorKey& o) const {
         if (dev != o.dev) return dev < o.dev;
         if (N != o.N) return N < o.N;
         if (G != o.G) return G < o.G;
         if (w != o.w) return w < o.w;
+        if (kind != o.kind) return kind < o.kind;
         return beta_bits < o.beta_bits;
     }
 };
@@ -109,7 +147,7 @@ std::map<FactorKey, double*> g_factors;
 
 ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cudaStream_t s) {
     if (N <= 0) return FTCG_SUCCESS;
-    FactorKey key{0, N, G, win.w, 0};
+    FactorKey key{0, N, G, win.w, win.kind, 0};
     FTCG_CK(cudaGetDevice(&key.dev));
     std::memcpy(&key.beta_bits, &win.beta, sizeof(double));
     std::lock_guard<std::mutex> lk(g_factor_mu);
@@ -125,7 +163,7 @@ ftcg_status_t window_factors(double* d_out, int N, int G, const Window& win, cud
         }
         double* d = nullptr;
         FTCG_CK(cudaMalloc(&d, (size_t)N * sizeof(double)));
-        k_window_factors<<<(N + 127) / 128, 128, 0, s>>>(d, N, G, win.w, win.beta, q);
+        k_window_factors<<<(N + 127) / 128, 128, 0, s>>>(d, N, G, win.w, win.beta, win.kind, q);
         FTCG_CK(cudaGetLastError());
         FTCG_CK(cudaStreamSynchronize(s));       // complete before another stream reads it
         it = g_factors.emplace(key, d).first;

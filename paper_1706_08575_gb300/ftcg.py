@@ -31,6 +31,7 @@ class FtcgError(RuntimeError):
 
 LAYOUT_AUTO, LAYOUT_DUPLICATE, LAYOUT_HALO = 0, 1, 2
 SPREAD_AUTO, SPREAD_WINDOW, SPREAD_TENSOR = 0, 1, 2
+WINDOW_ES, WINDOW_KB, WINDOW_GAUSS = 0, 1, 2  # gridding window families
 
 
 class Opts(ctypes.Structure):
@@ -147,14 +148,15 @@ class Plan:
     """A binned geometry: ftcg_plan on lam (torch float64, M x 2, CUDA)."""
 
     def __init__(self, lam, N, sigma=2.0, w=8, tile=0, precision=PREC_FP32, weight_width=0,
-                 stream=None, allow_numeric=False, layout=LAYOUT_AUTO, spread_kernel=SPREAD_AUTO):
+                 stream=None, allow_numeric=False, layout=LAYOUT_AUTO, spread_kernel=SPREAD_AUTO,
+                 window=WINDOW_ES):
         import torch
         if lam.dtype != torch.float64 or lam.dim() != 2 or lam.shape[1] != 2 or not lam.is_cuda:
             raise TypeError("lam must be a CUDA float64 tensor of shape (M, 2)")
         lam = lam.contiguous()
         self.M, self.N, self.sigma, self.w = int(lam.shape[0]), int(N), float(sigma), int(w)
         self.device = lam.device
-        opts = Opts(0, precision, tile, weight_width, layout, spread_kernel)
+        opts = Opts(window, precision, tile, weight_width, layout, spread_kernel)
         h = ctypes.c_void_p()
         st = lib().ftcg_plan(ctypes.byref(h), _ptr(lam), self.M, self.N, self.sigma, self.w,
                              ctypes.byref(opts), _stream(stream))
@@ -320,7 +322,7 @@ class Batch:
     """Many pings gridded together: ftcg_plan_batch on a list of (M_i, 2) float64 CUDA tensors."""
 
     def __init__(self, lams, Ns, sigma=2.0, w=8, tile=0, precision=PREC_FP32, stream=None,
-                 layout=LAYOUT_AUTO, spread_kernel=SPREAD_AUTO):
+                 layout=LAYOUT_AUTO, spread_kernel=SPREAD_AUTO, window=WINDOW_ES):
         import torch
         self.n = len(lams)
         self.lams = [l.contiguous() for l in lams]
@@ -332,7 +334,7 @@ class Batch:
         self.device = self.lams[0].device
         M_arr = (ctypes.c_int64 * self.n)(*self.Ms)
         N_arr = (ctypes.c_int32 * self.n)(*self.Ns)
-        opts = Opts(0, precision, tile, 0, layout, spread_kernel)
+        opts = Opts(window, precision, tile, 0, layout, spread_kernel)
         h = ctypes.c_void_p()
         st = lib().ftcg_plan_batch(ctypes.byref(h), self.n, _ptr_array(self.lams), M_arr, N_arr,
                                    float(sigma), int(w), ctypes.byref(opts), _stream(stream))

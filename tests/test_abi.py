@@ -66,7 +66,7 @@ def test_plan_rejects(L, kw, status):
 
 def test_plan_rejects_opts(L):
     from paper_1706_08575_gb300 import ftcg
-    assert _plan(L, opts=ftcg.Opts(1, 0, 0, 0)) == 4                 # only the ES window
+    assert _plan(L, opts=ftcg.Opts(3, 0, 0, 0)) == 1                 # window family
     assert _plan(L, opts=ftcg.Opts(0, 2, 0, 0)) == 1                 # precision
     assert _plan(L, opts=ftcg.Opts(0, 0, 48, 0)) == 1                # tile
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 3)) == 1                 # weight width
@@ -143,6 +143,7 @@ def test_tuner_file_round_trip(L, tmp_path):
     assert saved["ftcg_tuner"] == 1
     for e in entries:               # files written before the spreading-kernel choice load as 0
         assert dict(e, spread_req=e.get("spread_req", 0), batch=e.get("batch", 0),
+                    window=e.get("window", 0),
                     spread=e.get("spread", e.get("spread_req", 0))) in saved["entries"]
     bad = tmp_path / "bad.json"
     bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[0], G=1000, tile=48))
@@ -153,6 +154,9 @@ def test_tuner_file_round_trip(L, tmp_path):
                    + "\n]}\n")          # the tensor-core kernel needs the halo layout
     assert L.ftcg_tuner_load(str(bad).encode()) == 1
     bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[4], batch=2))
+                   + "\n]}\n")
+    assert L.ftcg_tuner_load(str(bad).encode()) == 1
+    bad.write_text('{"ftcg_tuner": 1, "entries": [\n' + json.dumps(dict(entries[4], window=3))
                    + "\n]}\n")
     assert L.ftcg_tuner_load(str(bad).encode()) == 1
     other = tmp_path / "other.json"
