@@ -179,6 +179,19 @@ ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t 
                                 void* h_image, ftcg_stream_t stream);
 
 /*
+ * ftcg_adjoint_host_async -- ftcg_adjoint_host without the final synchronisation, for streams of
+ * pings through one plan: the upload of h_values runs on a copy stream of the plan into one of
+ * two device buffers (alternating), and the adjoint on `stream` waits for it, so the upload of
+ * the next call overlaps the adjoint of this one (and its image write-back into a page-locked
+ * h_image). Returns once the work is enqueued. h_values must stay unchanged, and h_image is not
+ * complete, until `stream` has reached this call's work (synchronise it, or record an event
+ * after the call). Calls in flight need distinct h_image buffers; a plan takes one such stream
+ * of calls at a time.
+ */
+ftcg_status_t ftcg_adjoint_host_async(ftcg_plan_t plan, const void* h_values, int32_t vdtype,
+                                      void* h_image, ftcg_stream_t stream);
+
+/*
  * ftcg_forward -- the gridded transpose of ftcg_adjoint without weights (the data frame of
  * Eq. twoddataframe applied to an image): f_k ~= sum_p I_p exp(-2 pi i lambda_k . p / N).
  * d_image: N x N complex64; d_values: M complex64 out, acquisition order. Asynchronous.

@@ -53,6 +53,12 @@ void release_plan(Plan* p) {
     if (p->alpha_cur) cudaFree(p->alpha_cur);
     release_band(p);
     if (p->stage_img) cudaFree(p->stage_img);
+    for (int k = 0; k < 2; ++k) {
+        if (p->pipe_vals[k]) cudaFree(p->pipe_vals[k]);
+        if (p->pipe_up[k]) cudaEventDestroy(p->pipe_up[k]);
+        if (p->pipe_used[k]) cudaEventDestroy(p->pipe_used[k]);
+    }
+    if (p->pipe_copy) cudaStreamDestroy(p->pipe_copy);
     if (p->fft_ok) cufftDestroy(p->fft);
     release_pruned_fft(p);
     if (p->prof_ev) {
@@ -396,6 +402,56 @@ ftcg_status_t ftcg_adjoint_host(ftcg_plan_t plan, const void* h_values, int32_t 
         FTCG_CK(cudaMemcpyAsync(h_image, p->stage_img, ibytes, cudaMemcpyDeviceToHost, s));
     }
     FTCG_CK(cudaStreamSynchronize(s));
+    return FTCG_SUCCESS;
+    FTCG_API_END
+}
+
+ftcg_status_t ftcg_adjoint_host_async(ftcg_plan_t plan, const void* h_values, int32_t vdtype,
+                                      void* h_image, ftcg_stream_t stream) {
+    FTCG_API_BEGIN
+    clear_error();
+    if (!plan) return invalid("ftcg_adjoint_host_async: plan is NULL");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    FTCG_TRY(check_values(p, h_values, vdtype, "ftcg_adjoint_host_async"));
+    if (!h_image) return invalid("ftcg_adjoint_host_async: image pointer is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    p->last_stream = s;
+    const size_t vbytes = (size_t)p->M * (vdtype == FTCG_VALUES_C64 ? 8 : 4);
+    const size_t ibytes = (size_t)p->N * p->N * sizeof(float2);
+    if (!p->pipe_copy) {
+        FTCG_CK(cudaStreamCreateWithFlags(&p->pipe_copy, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            FTCG_CK(cudaEventCreateWithFlags(&p->pipe_up[k], cudaEventDisableTiming));
+            FTCG_CK(cudaEventCreateWithFlags(&p->pipe_used[k], cudaEventDisableTiming));
+            if (p->M > 0) FTCG_CK(cudaMalloc(&p->pipe_vals[k], (size_t)p->M * 8));
+        }
+    }
+    void* img_dev = nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h_image) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer) {
+        img_dev = at.devicePointer;
+    } else {
+        cudaGetLastError();
+        if (!p->stage_img) FTCG_CK(pool_malloc(&p->stage_img, ibytes, s));
+    }
+    const int k = p->pipe_next;
+    p->pipe_next ^= 1;
+    // upload into buffer k on the copy stream once the adjoint that last read it is done; the
+    // adjoint on `stream` waits for the upload only, so the next call's upload overlaps it
+    FTCG_CK(cudaStreamWaitEvent(p->pipe_copy, p->pipe_used[k], 0));
+    if (vbytes)
+        FTCG_CK(cudaMemcpyAsync(p->pipe_vals[k], h_values, vbytes, cudaMemcpyHostToDevice,
+                                p->pipe_copy));
+    FTCG_CK(cudaEventRecord(p->pipe_up[k], p->pipe_copy));
+    FTCG_CK(cudaStreamWaitEvent(s, p->pipe_up[k], 0));
+    if (img_dev) {
+        FTCG_TRY(adjoint_device(p, p->pipe_vals[k], vdtype, img_dev, s));
+    } else {
+        FTCG_TRY(adjoint_device(p, p->pipe_vals[k], vdtype, p->stage_img, s));
+        FTCG_CK(cudaMemcpyAsync(h_image, p->stage_img, ibytes, cudaMemcpyDeviceToHost, s));
+    }
+    FTCG_CK(cudaEventRecord(p->pipe_used[k], s));
     return FTCG_SUCCESS;
     FTCG_API_END
 }

@@ -225,6 +225,12 @@ struct Plan {
                                         // nullptr while alpha = 1)
     void* stage_vals = nullptr;         // ftcg_adjoint_host staging (device)
     void* stage_img = nullptr;
+    // ftcg_adjoint_host_async: two value staging buffers, a copy stream, and per buffer an event
+    // when its upload is done and one when the adjoint that read it is done
+    void* pipe_vals[2] = {nullptr, nullptr};
+    cudaStream_t pipe_copy = nullptr;
+    cudaEvent_t pipe_up[2] = {nullptr, nullptr}, pipe_used[2] = {nullptr, nullptr};
+    int pipe_next = 0;
     cudaStream_t last_stream = nullptr;
     int64_t device_bytes = 0;
     // stage profiling: 4 events per recorded adjoint call

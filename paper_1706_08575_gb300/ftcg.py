@@ -61,6 +61,7 @@ SIGNATURES = [
     ("ftcg_spread", _I32, [_VP, _VP, _I32, _VP, _VP]),
     ("ftcg_adjoint", _I32, [_VP, _VP, _I32, _VP, _VP]),
     ("ftcg_adjoint_host", _I32, [_VP, _VP, _I32, _VP, _VP]),
+    ("ftcg_adjoint_host_async", _I32, [_VP, _VP, _I32, _VP, _VP]),
     ("ftcg_forward", _I32, [_VP, _VP, _VP, _VP]),
     ("ftcg_check", _I32, [_VP]),
     ("ftcg_plan_entries", _I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -236,6 +237,14 @@ class Plan:
         vd = _values_dtype(values_host)
         _check(lib().ftcg_adjoint_host(self._h, _ptr(values_host), vd, _ptr(image_host),
                                        _stream(stream)))
+        return image_host
+
+    def adjoint_host_async(self, values_host, image_host, stream=None):
+        """Enqueue ftcg_adjoint_host_async (no synchronisation): the upload overlaps the previous
+        call's adjoint. Keep both tensors alive and unchanged until the stream has run it."""
+        vd = _values_dtype(values_host)
+        _check(lib().ftcg_adjoint_host_async(self._h, _ptr(values_host), vd, _ptr(image_host),
+                                             _stream(stream)))
         return image_host
 
     def forward(self, image, out=None, stream=None):

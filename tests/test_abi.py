@@ -164,7 +164,12 @@ def test_tuner_file_round_trip(L, tmp_path):
     assert L.ftcg_tuner_load(str(other).encode()) == 1
     assert L.ftcg_tuner_load(str(tmp_path / "absent.json").encode()) == 1
     ftcg.tuner_save(out)
-    assert all(e["G"] != 1000 and e["G"] != 4096 for e in json.loads(out.read_text())["entries"])
+    # neither the refused entry nor the foreign file's entry was added (other entries of this
+    # process, from plans built earlier, may be present)
+    after = json.loads(out.read_text())["entries"]
+    assert all(e["G"] != 1000 for e in after)
+    assert not any(e["G"] == 4096 and e["bucket"] == entries[0]["bucket"] and e["w"] == 8 and
+                   e["tile_req"] == 0 and e["layout_req"] == 0 and e["tile"] == 32 for e in after)
 
 
 def test_library_carries_its_source_hash():

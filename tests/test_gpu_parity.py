@@ -319,3 +319,30 @@ def test_adjoint_host_matches_device(F, N, pinned):
         p.adjoint_host(hv, himg)
         p.adjoint_host(hv, himg)                       # twice: the result does not accumulate
     assert O.rel_l2(himg.numpy(), a.numpy()) < 1e-6   # same kernels; atomics order may differ
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_adjoint_host_async_pipeline(F, pinned):
+    """ftcg_adjoint_host_async: a stream of calls with different values and two alternating
+    images, enqueued back to back (each upload overlapping the previous adjoint); after one
+    synchronisation every image equals the device adjoint of its own values."""
+    import torch
+    N = 64
+    lam, _ = sasgen.random_case(52, 3000, N, spread=N)
+    rng = np.random.default_rng(53)
+    vs = [c64(rng.standard_normal(3000) + 1j * rng.standard_normal(3000)) for _ in range(5)]
+    with F.Plan(dev(lam), N, 2.0, 8) as p:
+        refs = [p.adjoint(dev(v)).cpu().numpy() for v in vs]
+        hvs = [torch.from_numpy(v) for v in vs]
+        imgs = [[torch.full((N, N), 7.0 + 0j, dtype=torch.complex64) for _ in range(2)]
+                for _ in vs]
+        if pinned:
+            hvs = [h.pin_memory() for h in hvs]
+            imgs = [[i.pin_memory() for i in pair] for pair in imgs]
+        s = torch.cuda.Stream()
+        outs = []
+        for k, hv in enumerate(hvs):
+            outs.append(p.adjoint_host_async(hv, imgs[k][k % 2], stream=s))
+        s.synchronize()
+    for got, ref in zip(outs, refs):
+        assert O.rel_l2(got.numpy(), ref) < 1e-6
