@@ -24,7 +24,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # fast single-precision exp/sqrt; FP64 code (weights, window transform, planning) is unaffected.
 EXTRA = {
     "spread.cu": ["--use_fast_math"],
+    "spread_any.cu": ["--use_fast_math"],
     "batch.cu": ["--use_fast_math"],
+    "batch_window.cu": ["--use_fast_math"],
+    "batch_window_any.cu": ["--use_fast_math"],
 }
 
 

@@ -27,29 +27,13 @@
 
 #include "fft_smem.cuh"
 #include "spread_mma.cuh"
+#include "batch_desc.cuh"
 #include "spread_tile.cuh"
 
 namespace ftcg {
 
 namespace {
 
-struct PingDesc {
-    const Entry* ent;
-    const int* colptr;
-    const void* vals;
-    float2* grid;
-    float2* img;
-    const float2* deapod2;
-    float2* halo_buf;
-    const unsigned* col_mask;    // shared-memory FFT: column blocks that taps reach
-    int G, ntx, T, N;
-    int halo, halo_cells, ncb, W;
-    int fused;                   // 1: the row pass writes the image (no k_deapod_batch)
-    // tensor-core spreading (halo layout, w <= 8): the ping's chunks
-    const MmaEntry* cent;
-    const uint32_t* chdr;
-    const int* tile_chunk;
-};
 
 // The persistent tensor-core spreading launch: CTAs take (ping, tile) items of pings planned
 // for the tensor-core kernel from an atomic counter, heaviest first.
@@ -73,42 +57,6 @@ __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
         else
             mma::spread_tile<32, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
                                            d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
-    }
-}
-
-template <int GW, int WT, bool VBF, bool ABF, int CPL>
-__global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
-    k_spread_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items, int nitems,
-                   int* __restrict__ counter, int Wrt, Win32 win) {
-    extern __shared__ float smem[];
-    __shared__ int s_item;
-    for (;;) {
-        __syncthreads();   // the previous item's tile is stored and s_item consumed
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= nitems) return;
-        const int2 pt = items[it];
-        const PingDesc d = desc[pt.x];
-        if (d.halo) {
-            if (d.T == 64)
-                tile::spread_tile<GW, WT, 64, VBF, ABF, true, CPL>(d.ent, d.colptr, d.vals, d.grid, d.G,
-                                                              d.ntx, Wrt, win, pt.y, smem,
-                                                              d.halo_buf, d.halo_cells);
-            else
-                tile::spread_tile<GW, WT, 32, VBF, ABF, true, CPL>(d.ent, d.colptr, d.vals, d.grid, d.G,
-                                                              d.ntx, Wrt, win, pt.y, smem,
-                                                              d.halo_buf, d.halo_cells);
-        } else {
-            if (d.T == 64)
-                tile::spread_tile<GW, WT, 64, VBF, ABF, false, CPL>(d.ent, d.colptr, d.vals, d.grid,
-                                                               d.G, d.ntx, Wrt, win, pt.y,
-                                                               smem, nullptr, 0);
-            else
-                tile::spread_tile<GW, WT, 32, VBF, ABF, false, CPL>(d.ent, d.colptr, d.vals, d.grid,
-                                                               d.G, d.ntx, Wrt, win, pt.y,
-                                                               smem, nullptr, 0);
-        }
     }
 }
 
@@ -150,12 +98,6 @@ __global__ void __launch_bounds__(sfft::row_threads(L))
     sfft::rows_body<L>(d.grid, d.col_mask, tw, d.deapod2, d.N, d.img, blockIdx.x, sm);
 }
 
-template <int WMAX>
-size_t spread_smem() {
-    return std::max(std::max(tile::tile_smem_bytes<64, WMAX, true>(),
-                             tile::tile_smem_bytes<64, WMAX, false>()),
-                    tile::tile_smem_bytes<32, WMAX, true>());
-}
 
 // ---- autotuner ----------------------------------------------------------------------------
 struct TuneKey {
@@ -391,29 +333,6 @@ void release_batch(Batch* b) {
     delete b;
 }
 
-template <int GW, int WT, bool VBF, bool ABF, int CPL = 1>
-ftcg_status_t launch_batch_spread_t(Batch& b, cudaStream_t s) {
-    auto kern = k_spread_batch<GW, WT, VBF, ABF, CPL>;
-    const size_t smem = spread_smem<(WT > 0 ? WT : GW * CPL)>();
-    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared));
-    if (b.persistent_ctas == 0) {
-        int dev = 0, sms = 0, per = 0;
-        FTCG_CK(cudaGetDevice(&dev));
-        FTCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        FTCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, tile::kSpreadThreads,
-                                                              smem));
-        b.persistent_ctas = std::max(1, sms * std::max(1, per));
-    }
-    const Win32 win = win32_of(Window{b.w, kernel_beta(b.w, b.sigma, b.opts.kernel),
-                                      b.opts.kernel});
-    kern<<<b.persistent_ctas, tile::kSpreadThreads, smem, s>>>(
-        b.d_desc, b.d_items + b.n_mma, b.nitems - b.n_mma, b.d_counter + 1, b.w, win);
-    FTCG_CK(cudaGetLastError());
-    return FTCG_SUCCESS;
-}
-
 template <bool VBF, bool ABF>
 ftcg_status_t launch_batch_spread_mma(Batch& b, cudaStream_t s) {
     auto kern = k_spread_batch_mma<VBF, ABF>;
@@ -432,20 +351,6 @@ ftcg_status_t launch_batch_spread_mma(Batch& b, cudaStream_t s) {
                                                             b.d_counter, b.poly);
     FTCG_CK(cudaGetLastError());
     return FTCG_SUCCESS;
-}
-
-template <bool VBF, bool ABF>
-ftcg_status_t launch_batch_spread_w(Batch& b, cudaStream_t s) {
-    using tile::kCpl8;
-    using tile::kCpl16;
-    switch (b.w) {
-        case 6: return launch_batch_spread_t<8 / kCpl8, 6, VBF, ABF, kCpl8>(b, s);
-        case 8: return launch_batch_spread_t<8 / kCpl8, 8, VBF, ABF, kCpl8>(b, s);
-        default:
-            if (b.w <= 4) return launch_batch_spread_t<4, 0, VBF, ABF>(b, s);
-            if (b.w <= 8) return launch_batch_spread_t<8 / kCpl8, 0, VBF, ABF, kCpl8>(b, s);
-            return launch_batch_spread_t<16 / kCpl16, 0, VBF, ABF, kCpl16>(b, s);
-    }
 }
 
 template <int L>
@@ -501,12 +406,10 @@ ftcg_status_t batch_spread(Batch& b, bool vbf, cudaStream_t s) {
         else if (abf) FTCG_TRY((launch_batch_spread_mma<false, true>(b, s)));
         else FTCG_TRY((launch_batch_spread_mma<false, false>(b, s)));
     }
-    if (b.nitems > b.n_mma) {
-        if (vbf && abf) FTCG_TRY((launch_batch_spread_w<true, true>(b, s)));
-        else if (vbf) FTCG_TRY((launch_batch_spread_w<true, false>(b, s)));
-        else if (abf) FTCG_TRY((launch_batch_spread_w<false, true>(b, s)));
-        else FTCG_TRY((launch_batch_spread_w<false, false>(b, s)));
-    }
+    if (b.nitems > b.n_mma)
+        FTCG_TRY(launch_batch_window(b.d_desc, b.d_items + b.n_mma, b.nitems - b.n_mma,
+                                     b.d_counter + 1, b.w, b.sigma, b.opts.kernel, vbf, abf,
+                                     &b.persistent_ctas, s));
     if (b.nitems > 0 && b.any_halo) {
         k_halo_add_batch<<<b.nitems, 256, 0, s>>>(b.d_desc, b.d_items);
         FTCG_CK(cudaGetLastError());

@@ -15,7 +15,7 @@
 // grid cell is written exactly once, with no zero-fill. In the halo layout the accumulator also
 // holds the w - 1 overflow rows and columns, which k_halo_add adds to the neighbouring tiles.
 
-#include "spread_tile.cuh"
+#include "spread_window.cuh"
 
 namespace ftcg {
 
@@ -23,19 +23,6 @@ namespace {
 
 using tile::kSpreadThreads;
 using tile::win32;
-
-template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL>
-__global__ void __launch_bounds__(tile::kSpreadThreads, FTCG_SPREAD_MINB)
-    k_spread(const Entry* __restrict__ ent, const int* __restrict__ colptr,
-             const int* __restrict__ tile_order, const void* __restrict__ vals,
-             float2* __restrict__ grid, int G, int ntx, int Wrt, Win32 win,
-             float2* __restrict__ halo_buf, int halo_cells) {
-    extern __shared__ float smem[];
-    pdl_allow_next();                          // the fix-up may be scheduled during the tail
-    const int t = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
-    tile::spread_tile<GW, WT, T, VBF, ABF, HALO, CPL>(ent, colptr, vals, grid, G, ntx, Wrt, win,
-                                                      t, smem, halo_buf, halo_cells);
-}
 
 // one CTA per non-empty tile (the first n_nonempty of the heaviest-first order)
 __global__ void __launch_bounds__(256)
@@ -46,47 +33,6 @@ __global__ void __launch_bounds__(256)
     pdl_allow_next();
     tile::halo_add_tile(halo_buf, halo_cells, colptr, ncb, grid, G, T, W, ntx,
                         tile_order[blockIdx.x]);
-}
-
-template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL = 1>
-ftcg_status_t run_spread(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
-    const Binning& b = p.bin;
-    constexpr int WMAX = WT > 0 ? WT : GW * CPL;
-    const size_t smem = tile::tile_smem_bytes<T, WMAX, HALO>();
-    auto kern = k_spread<GW, WT, T, VBF, ABF, HALO, CPL>;
-    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared));
-    kern<<<nt, kSpreadThreads, smem, s>>>(b.ent, b.colptr, b.tile_order, vals, grid, b.G,
-                                                b.ntx, b.W, win32_of(p.win), b.halo_buf,
-                                                b.halo_cells);
-    FTCG_CK(cudaGetLastError());
-    if (HALO) return launch_halo_add(p, grid, s);
-    return FTCG_SUCCESS;
-}
-
-template <int T, bool VBF, bool ABF, bool HALO>
-ftcg_status_t dispatch_w(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
-    using tile::kCpl8;
-    using tile::kCpl16;
-    switch (p.w) {
-        case 6: return run_spread<8 / kCpl8, 6, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s, nt);
-        case 8: return run_spread<8 / kCpl8, 8, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s, nt);
-        default:
-            if (p.w <= 4) return run_spread<4, 0, T, VBF, ABF, HALO>(p, vals, grid, s, nt);
-            if (p.w <= 8) return run_spread<8 / kCpl8, 0, T, VBF, ABF, HALO, kCpl8>(p, vals, grid, s, nt);
-            return run_spread<16 / kCpl16, 0, T, VBF, ABF, HALO, kCpl16>(p, vals, grid, s, nt);
-    }
-}
-
-template <bool VBF, bool ABF>
-ftcg_status_t dispatch_t(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
-    if (p.bin.halo) {
-        if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, true>(p, vals, grid, s, nt);
-        return dispatch_w<64, VBF, ABF, true>(p, vals, grid, s, nt);
-    }
-    if (p.bin.T == 32) return dispatch_w<32, VBF, ABF, false>(p, vals, grid, s, nt);
-    return dispatch_w<64, VBF, ABF, false>(p, vals, grid, s, nt);
 }
 
 // ---- deapodisation and crop (the body is deapod_crop_block) -------------------------------------
@@ -204,11 +150,8 @@ ftcg_status_t launch_spread(const Plan& p, const void* vals, int vdtype, float2*
     const int nt = pruned && p.bin.n_read > 0 ? p.bin.n_read : p.bin.ntiles;
     const bool vbf = vdtype == FTCG_VALUES_BF16X2;
     if (p.bin.mma) return launch_spread_mma(p, vals, vbf, grid, s, nt);
-    const bool abf = p.opts.precision == FTCG_PREC_BF16;
-    if (vbf && abf) return dispatch_t<true, true>(p, vals, grid, s, nt);
-    if (vbf) return dispatch_t<true, false>(p, vals, grid, s, nt);
-    if (abf) return dispatch_t<false, true>(p, vals, grid, s, nt);
-    return dispatch_t<false, false>(p, vals, grid, s, nt);
+    if (p.win.kind == FTCG_WINDOW_ES) return swin::launch_window_spread<true>(p, vals, vbf, grid, s, nt);
+    return swin::launch_window_spread_any(p, vals, vbf, grid, s, nt);
 }
 
 ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img, cudaStream_t s) {

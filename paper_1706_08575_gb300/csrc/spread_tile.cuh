@@ -36,7 +36,15 @@ constexpr int kSpreadUnroll = FTCG_SPREAD_UNROLL;
 // exp(beta (sqrt(1 - z^2) - 1)) written as exp(-beta z^2 / (1 + sqrt(1 - z^2))) so that no
 // cancellation occurs near the centre (sqrt(1 - z^2) - 1 loses all its digits there); Kaiser-
 // Bessel: I0(beta sqrt(1 - z^2)) / I0(beta); truncated Gaussian: exp(-beta z^2). The family is
-// uniform across a launch, so the branch costs no divergence.
+// uniform across a launch, so the branch costs no divergence; es32 is the ES branch alone (the
+// kernels instantiate it separately, which saves the family test in their inner loops).
+__device__ __forceinline__ float es32(float t, const Win32& w) {
+    const float z = t * w.inv_hw;
+    const float z2 = z * z;
+    const float q = 1.0f - z2;
+    return q >= 0.0f ? __expf(__fdividef(-w.beta * z2, 1.0f + sqrtf(q))) : 0.0f;
+}
+
 __device__ __forceinline__ float win32(float t, const Win32& w) {
     const float z = t * w.inv_hw;
     const float z2 = z * z;
@@ -126,7 +134,8 @@ __device__ __forceinline__ void store_zero_tile(float2* __restrict__ grid, int G
 // w <= GW * CPL). HALO: the tile's entries are the samples whose first tap lies in it; the
 // accumulator covers the tile plus w - 1 cells to the right and below, the tile's own cells go to
 // the grid and the overflow strips to halo_buf (added to the neighbours by k_halo_add).
-template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL>
+// ES: the window is the exponential of semicircle (es32), otherwise any family (win32).
+template <int GW, int WT, int T, bool VBF, bool ABF, bool HALO, int CPL, bool ES = true>
 __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
                                             const int* __restrict__ colptr,
                                             const void* __restrict__ vals,
@@ -219,8 +228,9 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
         float xr[CPL], xi[CPL], fy[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-            const float fx = tap[c] ? win32(e.dx - (float)(l + c * GW), win) : 0.0f;
-            fy[c] = tap[c] ? win32(e.dy - (float)(l + c * GW), win) : 0.0f;
+            const float tx = e.dx - (float)(l + c * GW), ty = e.dy - (float)(l + c * GW);
+            const float fx = tap[c] ? (ES ? es32(tx, win) : win32(tx, win)) : 0.0f;
+            fy[c] = tap[c] ? (ES ? es32(ty, win) : win32(ty, win)) : 0.0f;
             const float ax = al * fx;
             xr[c] = v.x * ax;
             xi[c] = v.y * ax;
