@@ -74,8 +74,11 @@ enum { FTCG_LAYOUT_AUTO = 0, FTCG_LAYOUT_DUPLICATE = 1, FTCG_LAYOUT_HALO = 2 };
  *   TENSOR:  the tensor-core kernel (per column bin, 8 samples x a 16-row window per
  *            mma.sync.m16n8k8 in split TF32); it applies in the halo layout with w <= 8 and a
  *            window whose per-tap degree-7 polynomials are within 1e-6 of it (w >= 7 for any
- *            sigma >= 1.25, w = 6 at sigma = 2); NOT_SUPPORTED elsewhere. */
-enum { FTCG_SPREAD_AUTO = 0, FTCG_SPREAD_WINDOW = 1, FTCG_SPREAD_TENSOR = 2 };
+ *            sigma >= 1.25, w = 6 at sigma = 2); NOT_SUPPORTED elsewhere.
+ *   BLOCK:   the tensor-core kernel on 8 x 8-cell blocks (chunks of 8 samples whose first taps
+ *            share a block, a 16 x 16-cell window per block, 12 split-TF32 MMAs per chunk);
+ *            same conditions as TENSOR. */
+enum { FTCG_SPREAD_AUTO = 0, FTCG_SPREAD_WINDOW = 1, FTCG_SPREAD_TENSOR = 2, FTCG_SPREAD_BLOCK = 3 };
 
 /* Gridding window (Sec. III-A leaves the choice open; the exact weights' internal lag route
  * always uses ES): exponential of semicircle exp(beta (sqrt(1 - z^2) - 1)), Kaiser-Bessel
@@ -89,7 +92,7 @@ typedef struct {
     int32_t tile;          /* fine-grid tile side of the spreading kernel: 0 = auto, 32 or 64 */
     int32_t weight_width;  /* window width of the FP64 weight construction: 0 = 12, else 4..16 */
     int32_t layout;        /* FTCG_LAYOUT_AUTO (default), _DUPLICATE or _HALO                  */
-    int32_t spread_kernel; /* FTCG_SPREAD_AUTO (default), _WINDOW or _TENSOR                    */
+    int32_t spread_kernel; /* FTCG_SPREAD_AUTO (default), _WINDOW, _TENSOR or _BLOCK            */
     int32_t reserved[2];   /* must be zero                                                      */
 } ftcg_opts_t;
 
@@ -101,7 +104,7 @@ typedef struct {
     int64_t entries;       /* sorted (tile, sample) entries                                     */
     double beta;           /* window shape parameter                                            */
     int64_t device_bytes;  /* device memory the plan holds                                      */
-    int32_t spread_kernel; /* FTCG_SPREAD_WINDOW or FTCG_SPREAD_TENSOR: the kernel the plan uses */
+    int32_t spread_kernel; /* FTCG_SPREAD_WINDOW, _TENSOR or _BLOCK: the kernel the plan uses   */
     int32_t pad0;
     int64_t chunks;        /* tensor-core chunks of 8 sample slots (0 for the other kernel)     */
 } ftcg_plan_info_t;

@@ -91,7 +91,8 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
     if (p->bin.halo && p->opts.spread_kernel != FTCG_SPREAD_WINDOW && p->w <= kMmaMaxW) {
         double err = 0;
         if (mma_window_poly(p->w, p->win.beta, p->win.kind, &p->bin.poly, &err))
-            FTCG_TRY(build_chunks(p->bin, s, &bytes));
+            FTCG_TRY(build_chunks(p->bin, s, &bytes,
+                                  p->opts.spread_kernel == FTCG_SPREAD_BLOCK));
     }
     if (own_grid) {
         FTCG_CK(pool_malloc(&p->grid, (size_t)p->G * p->G * sizeof(float2), s));
@@ -127,8 +128,8 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
         if (o.reserved[i] != 0) return invalid("ftcg_plan: opts.reserved must be zero");
     if (o.layout < FTCG_LAYOUT_AUTO || o.layout > FTCG_LAYOUT_HALO)
         return invalid("ftcg_plan: opts.layout must be 0, 1 or 2");
-    if (o.spread_kernel < FTCG_SPREAD_AUTO || o.spread_kernel > FTCG_SPREAD_TENSOR)
-        return invalid("ftcg_plan: opts.spread_kernel must be 0, 1 or 2");
+    if (o.spread_kernel < FTCG_SPREAD_AUTO || o.spread_kernel > FTCG_SPREAD_BLOCK)
+        return invalid("ftcg_plan: opts.spread_kernel must be 0, 1, 2 or 3");
     if (o.kernel < FTCG_WINDOW_ES || o.kernel > FTCG_WINDOW_GAUSS)
         return invalid("ftcg_plan: opts.kernel must be 0 (ES), 1 (Kaiser-Bessel) or 2 (Gaussian)");
     const double beta = kernel_beta(w, sigma, o.kernel);
@@ -137,7 +138,7 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
                   "((w / sigma)^2 (sigma - 1/2)^2 <= 0.8)", w, sigma);
         return FTCG_ERR_NOT_SUPPORTED;
     }
-    if (o.spread_kernel == FTCG_SPREAD_TENSOR) {
+    if (o.spread_kernel == FTCG_SPREAD_TENSOR || o.spread_kernel == FTCG_SPREAD_BLOCK) {
         MmaPoly poly;
         double err = 0;
         if (o.layout == FTCG_LAYOUT_DUPLICATE || w > kMmaMaxW ||
@@ -310,7 +311,9 @@ ftcg_status_t ftcg_plan_info(ftcg_plan_t plan, ftcg_plan_info_t* info) {
     info->entries = p->bin.n_entries;
     info->beta = p->win.beta;
     info->device_bytes = p->device_bytes;
-    info->spread_kernel = p->bin.mma ? FTCG_SPREAD_TENSOR : FTCG_SPREAD_WINDOW;
+    info->spread_kernel = !p->bin.mma ? FTCG_SPREAD_WINDOW
+                          : p->bin.blk ? FTCG_SPREAD_BLOCK
+                                       : FTCG_SPREAD_TENSOR;
     info->pad0 = 0;
     info->chunks = p->bin.n_chunks;
     return FTCG_SUCCESS;

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "fft_smem.cuh"
+#include "spread_blk.cuh"
 #include "spread_mma.cuh"
 #include "batch_desc.cuh"
 #include "spread_tile.cuh"
@@ -51,12 +52,22 @@ __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
         if (it >= nitems) return;
         const int2 pt = items[it];
         const PingDesc d = desc[pt.x];
-        if (d.T == 64)
+        if (d.blk) {
+            if (d.T == 64)
+                blk::spread_tile<64, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
+                                               d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y,
+                                               smem);
+            else
+                blk::spread_tile<32, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
+                                               d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y,
+                                               smem);
+        } else if (d.T == 64) {
             mma::spread_tile<64, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
                                            d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
-        else
+        } else {
             mma::spread_tile<32, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
                                            d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
+        }
     }
 }
 
@@ -184,7 +195,8 @@ std::vector<TuneVal> tune_candidates(int w, double sigma, const ftcg_opts_t& opt
     std::vector<int> tiles, layouts;
     if (opts.tile) tiles.push_back(opts.tile); else tiles = {32, 64};
     if (opts.layout) layouts.push_back(opts.layout);
-    else if (opts.spread_kernel == FTCG_SPREAD_TENSOR) layouts.push_back(FTCG_LAYOUT_HALO);
+    else if (opts.spread_kernel == FTCG_SPREAD_TENSOR || opts.spread_kernel == FTCG_SPREAD_BLOCK)
+        layouts.push_back(FTCG_LAYOUT_HALO);
     else layouts = {FTCG_LAYOUT_DUPLICATE, FTCG_LAYOUT_HALO};
     MmaPoly poly;
     double perr = 0;
@@ -195,9 +207,11 @@ std::vector<TuneVal> tune_candidates(int w, double sigma, const ftcg_opts_t& opt
         for (int layout : layouts) {
             if (layout == FTCG_LAYOUT_HALO && tensor_ok && opts.spread_kernel == FTCG_SPREAD_AUTO) {
                 out.push_back({T, layout, FTCG_SPREAD_TENSOR});
+                out.push_back({T, layout, FTCG_SPREAD_BLOCK});
                 out.push_back({T, layout, FTCG_SPREAD_WINDOW});
-            } else if (layout == FTCG_LAYOUT_HALO && opts.spread_kernel == FTCG_SPREAD_TENSOR) {
-                out.push_back({T, layout, FTCG_SPREAD_TENSOR});
+            } else if (layout == FTCG_LAYOUT_HALO && (opts.spread_kernel == FTCG_SPREAD_TENSOR ||
+                                                     opts.spread_kernel == FTCG_SPREAD_BLOCK)) {
+                out.push_back({T, layout, opts.spread_kernel});
             } else {
                 out.push_back({T, layout, FTCG_SPREAD_WINDOW});
             }
@@ -638,6 +652,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         d.cent = bn.cent;
         d.chdr = bn.chdr;
         d.tile_chunk = bn.tile_chunk;
+        d.blk = bn.blk ? 1 : 0;
         if (bn.mma) b.poly = bn.poly;
         b.any_halo = b.any_halo || bn.halo;
         std::vector<Item>& list = bn.mma ? items_mma : items;
@@ -1230,10 +1245,10 @@ ftcg_status_t ftcg_tuner_load(const char* path) {
                            (k.prec == FTCG_PREC_FP32 || k.prec == FTCG_PREC_BF16) &&
                            (k.tile == 0 || k.tile == 32 || k.tile == 64) &&
                            (k.layout >= FTCG_LAYOUT_AUTO && k.layout <= FTCG_LAYOUT_HALO) &&
-                           (k.skern >= FTCG_SPREAD_AUTO && k.skern <= FTCG_SPREAD_TENSOR) &&
-                           (k.skern != FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
-                           (spread >= FTCG_SPREAD_AUTO && spread <= FTCG_SPREAD_TENSOR) &&
-                           (spread != FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
+                           (k.skern >= FTCG_SPREAD_AUTO && k.skern <= FTCG_SPREAD_BLOCK) &&
+                           (k.skern < FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
+                           (spread >= FTCG_SPREAD_AUTO && spread <= FTCG_SPREAD_BLOCK) &&
+                           (spread < FTCG_SPREAD_TENSOR || layout == FTCG_LAYOUT_HALO) &&
                            (k.skern == FTCG_SPREAD_AUTO || spread == k.skern) &&
                            (k.batch == 0 || k.batch == 1) &&
                            (k.win >= FTCG_WINDOW_ES && k.win <= FTCG_WINDOW_GAUSS) &&

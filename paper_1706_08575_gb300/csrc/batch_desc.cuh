@@ -23,6 +23,7 @@ struct PingDesc {
     const MmaEntry* cent;
     const uint32_t* chdr;
     const int* tile_chunk;
+    int blk;                     // 1: the chunks are 8 x 8-cell blocks (spread_blk.cuh)
 };
 
 // Dynamic shared memory of the register-window tile body for any tile side and layout a batch

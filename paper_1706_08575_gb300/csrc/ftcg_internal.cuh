@@ -180,6 +180,7 @@ struct Binning {
     // Tensor-core spreading (halo layout, w <= 8): each tile's entries regrouped into chunks of 8
     // samples of one column bin whose first-tap rows fit one 16-row window (spread_mma.cu).
     bool mma = false;
+    bool blk = false;                   // the chunks are 8 x 8-cell blocks (spread_blk.cuh)
     int64_t n_chunks = 0;
     MmaEntry* cent = nullptr;           // n_chunks * 8 slots, tile by tile (padding slots flagged)
     uint32_t* chdr = nullptr;           // per chunk: first-tap column | window row << 8
@@ -268,7 +269,7 @@ ftcg_status_t launch_deapod_crop(const Plan& p, const float2* grid, float2* img,
 // spread_mma.cu: the tensor-core spreading path (halo layout, w <= 8)
 // fit the per-tap window polynomials; returns false if their error exceeds the path's bound
 bool mma_window_poly(int W, double beta, int kind, MmaPoly* out, double* max_err);
-ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes);
+ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes, bool block = false);
 void free_chunks(Binning& b);
 ftcg_status_t launch_spread_mma(const Plan& p, const void* vals, bool vbf, float2* grid,
                                 cudaStream_t s, int nt);

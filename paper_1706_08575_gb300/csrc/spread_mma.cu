@@ -31,6 +31,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "spread_blk.cuh"
 #include "spread_mma.cuh"
 
 namespace ftcg {
@@ -246,6 +247,98 @@ ftcg_status_t dispatch_mma_t(const Plan& p, const void* vals, float2* grid, cuda
     return run_mma<64, VBF, ABF>(p, vals, grid, s, nt);
 }
 
+// ---- block chunks (plan time): one thread per (tile, 8 x 8 block of first-tap cells) ----------
+// The block's entries are those of its 8 column bins (halo layout: bin = first-tap column + w - 1)
+// whose first-tap row lies in the block's 8 rows, taken bin by bin in row order (deterministic).
+__device__ __forceinline__ int blk_row(const Entry& e, int W) {
+    return (int)(e.packed >> kSampleBits) - (W - 1);
+}
+
+__global__ void k_blk_count(const Entry* __restrict__ ent, const int* __restrict__ colptr,
+                            int ntiles, int ncb, int T, int W, int* __restrict__ cnt) {
+    const int nbs = T / 8, nb = nbs * nbs;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)ntiles * nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tile = i / nb;
+        const int b = (int)(i - tile * nb), bxi = b % nbs, byi = b / nbs;
+        int c = 0;
+        for (int bin = 8 * bxi + W - 1; bin < 8 * bxi + 8 + W - 1 && bin < ncb; ++bin) {
+            const int a0 = colptr[tile * ncb + bin], a1 = colptr[tile * ncb + bin + 1];
+            for (int e = a0; e < a1; ++e) c += (blk_row(ent[e], W) >> 3) == byi;
+        }
+        cnt[i] = (c + kMmaChunk - 1) / kMmaChunk;
+    }
+}
+
+__global__ void k_blk_emit(const Entry* __restrict__ ent, const int* __restrict__ colptr,
+                           const int* __restrict__ off, int ntiles, int ncb, int T, int W,
+                           MmaEntry* __restrict__ cent, uint32_t* __restrict__ chdr) {
+    const int nbs = T / 8, nb = nbs * nbs;
+    const float c0 = 0.5f * W - 0.5f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)ntiles * nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tile = i / nb;
+        const int b = (int)(i - tile * nb), bxi = b % nbs, byi = b / nbs;
+        const int64_t first = off[i];
+        int64_t k = 0;
+        for (int bin = 8 * bxi + W - 1; bin < 8 * bxi + 8 + W - 1 && bin < ncb; ++bin) {
+            const int a0 = colptr[tile * ncb + bin], a1 = colptr[tile * ncb + bin + 1];
+            const int ox = bin - (W - 1) - 8 * bxi;              // first-tap column in the block
+            for (int e = a0; e < a1; ++e) {
+                const Entry en = ent[e];
+                const int r = blk_row(en, W);
+                if ((r >> 3) != byi) continue;
+                MmaEntry m;
+                m.sx = en.dx - c0;                              // as the column chunks
+                m.sy = en.dy - c0;
+                m.alpha = en.alpha;
+                m.packed = (en.packed & kSampleMask) | ((uint32_t)ox << blk::kOffXShift) |
+                           ((uint32_t)(r - 8 * byi) << blk::kOffYShift);
+                cent[first * kMmaChunk + k] = m;
+                ++k;
+            }
+        }
+        const int64_t nch = (k + kMmaChunk - 1) / kMmaChunk;
+        for (; k < nch * kMmaChunk; ++k) cent[first * kMmaChunk + k] = MmaEntry{0.f, 0.f, 0u, kMmaPad};
+        for (int64_t c = 0; c < nch; ++c)
+            chdr[first + c] = (uint32_t)(8 * bxi) | ((uint32_t)(8 * byi) << 8);
+    }
+}
+
+template <int T, bool VBF, bool ABF>
+__global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
+    k_spread_blk(const MmaEntry* __restrict__ cent, const uint32_t* __restrict__ chdr,
+                 const int* __restrict__ tile_chunk, const int* __restrict__ tile_order,
+                 const void* __restrict__ vals, float2* __restrict__ grid, int G, int ntx, int W,
+                 const __grid_constant__ MmaPoly poly, float2* __restrict__ halo_buf,
+                 int halo_cells) {
+    extern __shared__ float smem[];
+    pdl_allow_next();                          // the fix-up may be scheduled during the tail
+    blk::spread_tile<T, VBF, ABF>(cent, chdr, tile_chunk, vals, grid, G, ntx, W, poly, halo_buf,
+                                  halo_cells, tile_order[blockIdx.x], smem);
+}
+
+template <int T, bool VBF, bool ABF>
+ftcg_status_t run_blk(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
+    const Binning& b = p.bin;
+    const size_t smem = mma::tile_smem_bytes(T);
+    auto kern = k_spread_blk<T, VBF, ABF>;
+    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
+    kern<<<nt, mma::kThreads, smem, s>>>(b.cent, b.chdr, b.tile_chunk, b.tile_order, vals, grid,
+                                       b.G, b.ntx, b.W, b.poly, b.halo_buf, b.halo_cells);
+    FTCG_CK(cudaGetLastError());
+    return launch_halo_add(p, grid, s);
+}
+
+template <bool VBF, bool ABF>
+ftcg_status_t dispatch_blk_t(const Plan& p, const void* vals, float2* grid, cudaStream_t s,
+                             int nt) {
+    if (p.bin.T == 32) return run_blk<32, VBF, ABF>(p, vals, grid, s, nt);
+    return run_blk<64, VBF, ABF>(p, vals, grid, s, nt);
+}
+
 }  // namespace
 
 void free_chunks(Binning& b) {
@@ -257,14 +350,18 @@ void free_chunks(Binning& b) {
     b.tile_chunk = nullptr;
     b.n_chunks = 0;
     b.mma = false;
+    b.blk = false;
 }
 
-ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes) {
+ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes, bool block) {
     if (!b.halo || b.W > kMmaMaxW || (b.T != 32 && b.T != 64)) {
         set_error("build_chunks: the tensor-core path needs the halo layout, w <= 8, T = 32 or 64");
         return FTCG_ERR_NOT_SUPPORTED;
     }
-    const int64_t nseg = (int64_t)b.ntiles * b.ncb;
+    b.blk = block;
+    // segments: (tile, column bin) for column chunks, (tile, 8 x 8 block) for block chunks
+    const int per_tile = block ? (b.T / 8) * (b.T / 8) : b.ncb;
+    const int64_t nseg = (int64_t)b.ntiles * per_tile;
     FTCG_CK(pool_malloc(&b.tile_chunk, (b.ntiles + 1) * sizeof(int), s));
     *bytes += (b.ntiles + 1) * sizeof(int);
     if (b.n_entries == 0) {
@@ -277,7 +374,11 @@ ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes) {
     int* off = nullptr;
     FTCG_CK(pool_malloc(&cnt, nseg * sizeof(int), s));
     FTCG_CK(pool_malloc(&off, nseg * sizeof(int), s));
-    k_chunk_count<<<blocks_for(nseg, 256), 256, 0, s>>>(b.ent, b.colptr, nseg, b.W, cnt);
+    if (block)
+        k_blk_count<<<blocks_for(nseg, 256), 256, 0, s>>>(b.ent, b.colptr, b.ntiles, b.ncb, b.T,
+                                                          b.W, cnt);
+    else
+        k_chunk_count<<<blocks_for(nseg, 256), 256, 0, s>>>(b.ent, b.colptr, nseg, b.W, cnt);
     FTCG_CK(cudaGetLastError());
     FTCG_TRY(exclusive_scan_i32(cnt, off, nseg, s));
     int last_off = 0, last_cnt = 0;
@@ -296,10 +397,14 @@ ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes) {
                                                 kPad * kMmaChunk);
     FTCG_CK(cudaGetLastError());
     FTCG_CK(cudaMemsetAsync(b.chdr + total, 0, kPad * sizeof(uint32_t), s));
-    k_chunk_emit<<<blocks_for(nseg, 256), 256, 0, s>>>(b.ent, b.colptr, off, nseg, b.ncb, b.W,
-                                                       b.cent, b.chdr);
+    if (block)
+        k_blk_emit<<<blocks_for(nseg, 256), 256, 0, s>>>(b.ent, b.colptr, off, b.ntiles, b.ncb,
+                                                         b.T, b.W, b.cent, b.chdr);
+    else
+        k_chunk_emit<<<blocks_for(nseg, 256), 256, 0, s>>>(b.ent, b.colptr, off, nseg, b.ncb, b.W,
+                                                           b.cent, b.chdr);
     FTCG_CK(cudaGetLastError());
-    k_tile_chunk<<<blocks_for(b.ntiles + 1, 256), 256, 0, s>>>(off, b.ntiles, b.ncb, total,
+    k_tile_chunk<<<blocks_for(b.ntiles + 1, 256), 256, 0, s>>>(off, b.ntiles, per_tile, total,
                                                                b.tile_chunk);
     FTCG_CK(cudaGetLastError());
     FTCG_CK(pool_free(cnt, s));
@@ -311,6 +416,12 @@ ftcg_status_t build_chunks(Binning& b, cudaStream_t s, int64_t* bytes) {
 ftcg_status_t launch_spread_mma(const Plan& p, const void* vals, bool vbf, float2* grid,
                                 cudaStream_t s, int nt) {
     const bool abf = p.opts.precision == FTCG_PREC_BF16;
+    if (p.bin.blk) {
+        if (vbf && abf) return dispatch_blk_t<true, true>(p, vals, grid, s, nt);
+        if (vbf) return dispatch_blk_t<true, false>(p, vals, grid, s, nt);
+        if (abf) return dispatch_blk_t<false, true>(p, vals, grid, s, nt);
+        return dispatch_blk_t<false, false>(p, vals, grid, s, nt);
+    }
     if (vbf && abf) return dispatch_mma_t<true, true>(p, vals, grid, s, nt);
     if (vbf) return dispatch_mma_t<true, false>(p, vals, grid, s, nt);
     if (abf) return dispatch_mma_t<false, true>(p, vals, grid, s, nt);

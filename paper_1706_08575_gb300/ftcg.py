@@ -30,7 +30,7 @@ class FtcgError(RuntimeError):
 
 
 LAYOUT_AUTO, LAYOUT_DUPLICATE, LAYOUT_HALO = 0, 1, 2
-SPREAD_AUTO, SPREAD_WINDOW, SPREAD_TENSOR = 0, 1, 2
+SPREAD_AUTO, SPREAD_WINDOW, SPREAD_TENSOR, SPREAD_BLOCK = 0, 1, 2, 3
 WINDOW_ES, WINDOW_KB, WINDOW_GAUSS = 0, 1, 2  # gridding window families
 
 

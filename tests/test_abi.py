@@ -71,7 +71,7 @@ def test_plan_rejects_opts(L):
     assert _plan(L, opts=ftcg.Opts(0, 0, 48, 0)) == 1                # tile
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 3)) == 1                 # weight width
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 3)) == 1              # layout
-    assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 0, 3)) == 1           # spreading kernel
+    assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 0, 4)) == 1           # spreading kernel
     o = ftcg.Opts(0, 0, 0, 0)
     o.reserved[1] = 1
     assert _plan(L, opts=o) == 1

@@ -58,7 +58,7 @@ def test_batch_vs_oracle_and_single(F, layout):
         assert O.rel_l2(img, single) < 1e-6
 
 
-@pytest.mark.parametrize("kernel", [1, 2], ids=["window", "tensor"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["window", "tensor", "block"])
 def test_batch_each_spread_kernel(F, kernel):
     """The persistent batched launch with each spreading kernel forced (halo layout), over pings
     of both FFT paths (cuFFT below G = 256, shared-memory passes from 256) and an empty ping,

@@ -166,3 +166,33 @@ def test_batch_pings_whole_images(F):
     for q, x, a, img in zip(picks, vals, alphas, imgs):
         ref = O.adjoint(q.lam, a.astype(np.float32) * x.astype(np.complex128), q.N, 2.0, 8)
         assert O.rel_l2(img, ref) < TOL, q.N
+
+
+def test_largest_grid_cufft_path_sampled(F):
+    """The largest image of the test set, N = 4096 (G = 8192: beyond the shared-memory transforms,
+    the pruned cuFFT path): 400,000 samples over a jittered polar wedge spanning the band, with
+    random weights; 96 pixels (random, the centre row and column ends, the corners) against the
+    oracle's pixel-by-pixel gridding, and the bright target's pixel."""
+    N = 4096
+    rng = np.random.default_rng(4096)
+    kx, ky = sasgen.polar_raster(rng, 800, 500, 20.0, theta_jitter_deg=0.02)
+    span = max(kx.max() - kx.min(), ky.max() - ky.min())
+    lam = sasgen.baseband(kx, ky, 0.9 * 2 * np.pi * N / span)
+    M = lam.shape[0]
+    tgt = np.array([0.123, -0.231])                 # a point target (fraction of the FOV)
+    v = np.exp(-2j * np.pi * lam @ tgt) + 0.1 * (rng.standard_normal(M) +
+                                                  1j * rng.standard_normal(M))
+    alpha = rng.uniform(0.5, 1.5, M)
+    with F.Plan(dev(lam), N, 2.0, 8) as p:
+        p.set_weights(dev(alpha))
+        img = p.adjoint(dev(v.astype(np.complex64))).cpu().numpy()
+    pix = np.concatenate([rng.integers(-N // 2, N // 2, (88, 2)),
+                          [[-N // 2, 0], [N // 2 - 1, 0], [0, -N // 2], [0, N // 2 - 1],
+                           [-N // 2, -N // 2], [N // 2 - 1, N // 2 - 1],
+                           [int(round(tgt[0] * N)), int(round(tgt[1] * N))], [0, 0]]])
+    c = alpha.astype(np.float32) * v.astype(np.complex64).astype(np.complex128)
+    ref = O.adjoint_pixels(lam, c, N, 2.0, 8, pix)
+    got = img[pix[:, 1] + N // 2, pix[:, 0] + N // 2]
+    assert O.rel_l2(got, ref) < TOL
+    peak = np.unravel_index(np.argmax(np.abs(img)), img.shape)
+    assert (peak[1] - N // 2, peak[0] - N // 2) == (int(round(tgt[0] * N)), int(round(tgt[1] * N)))

@@ -1,12 +1,14 @@
-"""The two spreading kernels against the FP64 oracle, element by element, through the C ABI.
+"""The spreading kernels against the FP64 oracle, element by element, through the C ABI.
 
-The register-window kernel (FTCG_SPREAD_WINDOW) and the tensor-core kernel (FTCG_SPREAD_TENSOR:
-per column bin, chunks of 8 samples x a 16-row window per split-TF32 mma.sync.m16n8k8) must give
-the same grid and image within the FP32 bar (rel-L2 <= 1e-5 against the oracle on the same
-inputs). The cases stress what the tensor-core plan adds: ragged edge tiles, every sample in a
-handful of cells (many chunks and window restarts per column bin), first-tap rows spread so that
-windows move down by 8 rows and restart, wrap-around of the periodic grid, w from 6 to 8, both
-tile sides, BF16 storage, and the degenerate plans (no sample, one sample).
+The register-window kernel (FTCG_SPREAD_WINDOW), the tensor-core kernel on column bins
+(FTCG_SPREAD_TENSOR: chunks of 8 samples of one column bin x a 16-row window per split-TF32
+mma.sync.m16n8k8) and the tensor-core kernel on 8 x 8-cell blocks (FTCG_SPREAD_BLOCK: chunks of
+8 samples of one block x a 16 x 16 window, two column halves) must give the same grid and image
+within the FP32 bar (rel-L2 <= 1e-5 against the oracle on the same inputs). The cases stress what
+the chunked plans add: ragged edge tiles, every sample in a handful of cells (many chunks per
+column bin or block), first-tap rows spread so that column windows move down by 8 rows and
+restart, wrap-around of the periodic grid, w from 6 to 8, both tile sides, BF16 storage, and the
+degenerate plans (no sample, one sample).
 """
 import numpy as np
 import pytest
@@ -87,7 +89,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", [1, 2], ids=["window", "tensor"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["window", "tensor", "block"])
 @pytest.mark.parametrize("name,build,N,sigma,w,T", CASES, ids=[c[0] for c in CASES])
 def test_kernel_vs_oracle(F, name, build, N, sigma, w, T, kernel):
     lam, v = build()
@@ -100,7 +102,7 @@ def test_kernel_vs_oracle(F, name, build, N, sigma, w, T, kernel):
     assert O.rel_l2(img, O.adjoint(lam, cw, N, sigma, w)) < TOL
 
 
-@pytest.mark.parametrize("kernel", [1, 2], ids=["window", "tensor"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["window", "tensor", "block"])
 def test_kernel_bf16_storage(F, kernel):
     """BF16 values and weights: parity against the oracle on the same bf16-rounded inputs."""
     import torch
@@ -126,24 +128,28 @@ def test_kernels_agree_on_a_polar_ping(F):
     alpha = rng.uniform(0.5, 1.5, p.M)
     a, _ = run(F, p.lam, v, p.N, 2.0, 8, alpha, 32, 1)
     b, _ = run(F, p.lam, v, p.N, 2.0, 8, alpha, 32, 2)
+    c, _ = run(F, p.lam, v, p.N, 2.0, 8, alpha, 64, 3)
     ref = O.adjoint(p.lam, alpha.astype(np.float32) * c64(v).astype(np.complex128), p.N, 2.0, 8)
-    assert O.rel_l2(a, ref) < TOL
-    assert O.rel_l2(b, ref) < TOL
+    for img in (a, b, c):
+        assert O.rel_l2(img, ref) < TOL
     assert O.rel_l2(b, a) < 2e-6
+    assert O.rel_l2(c, a) < 2e-6
 
 
-def test_tensor_kernel_empty_plan(F):
+@pytest.mark.parametrize("kernel", [2, 3], ids=["tensor", "block"])
+def test_tensor_kernel_empty_plan(F, kernel):
     lam = np.zeros((0, 2))
     with F.Plan(dev(lam.reshape(0, 2)), 32, 2.0, 8, tile=32, layout=F.LAYOUT_HALO,
-                spread_kernel=F.SPREAD_TENSOR) as p:
+                spread_kernel=kernel) as p:
         import torch
         img = p.adjoint(torch.zeros(0, dtype=torch.complex64, device="cuda")).cpu().numpy()
     assert np.all(img == 0)
 
 
+@pytest.mark.parametrize("kernel", [2, 3], ids=["tensor", "block"])
 @pytest.mark.parametrize("kw", [dict(w=10), dict(w=4), dict(w=6, sigma=1.25),
                                 dict(layout=1)], ids=["w10", "w4", "w6-sigma1.25", "duplicate"])
-def test_tensor_kernel_refuses(F, kw):
+def test_tensor_kernel_refuses(F, kw, kernel):
     """Where the tensor-core kernel does not apply, asking for it is NOT_SUPPORTED (status 4)."""
     lam, _ = sasgen.random_case(50, 500, 32, 2.0, 8, 32)
     args = dict(w=8, sigma=2.0, layout=F.LAYOUT_HALO)
@@ -151,5 +157,5 @@ def test_tensor_kernel_refuses(F, kw):
     N = 32 if args["sigma"] == 2.0 else 64
     with pytest.raises(F.FtcgError) as ei:
         F.Plan(dev(lam), N, args["sigma"], args["w"], tile=32, layout=args["layout"],
-               spread_kernel=F.SPREAD_TENSOR)
+               spread_kernel=kernel)
     assert ei.value.status == 4
