@@ -547,7 +547,13 @@ def learned_vs_plain(device, large=None, n_pings=64, train_geos=60, train_steps=
 SPREAD_SOURCES = ["paper_1706_08575_gb300/csrc/spread_tile.cuh",
                   "paper_1706_08575_gb300/csrc/spread.cu", "paper_1706_08575_gb300/csrc/plan.cu",
                   "paper_1706_08575_gb300/csrc/spread_mma.cuh",
-                  "paper_1706_08575_gb300/csrc/spread_mma.cu"]
+                  "paper_1706_08575_gb300/csrc/spread_mma.cu",
+                  "paper_1706_08575_gb300/csrc/spread_blk.cuh"]
+
+# the spreading kernel of each FTCG_SPREAD_* value, and how the headline line describes it
+SPREAD_KERNELS = {1: ("k_spread", "register-window (k_spread)"),
+                  2: ("k_spread_mma", "tensor-core, column-bin chunks (k_spread_mma)"),
+                  3: ("k_spread_blk", "tensor-core, 8x8-block chunks (k_spread_blk)")}
 
 
 def spread_source_hash():
@@ -559,13 +565,23 @@ def spread_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_issue(tile):
-    """Instruction issue of the recorded k_spread capture (warp instructions per SM per cycle,
-    at most 4 on this GPU), or None if the spreading sources changed since."""
+def recorded_capture(tile, kernel):
+    """The committed ncu summary of the spreading kernel on this workload, or None if it is of
+    another tile side or kernel, or the spreading sources changed since that capture."""
+    with open(os.path.join(ROOT, "profiles", "k_spread_traffic.json")) as f:
+        d = json.load(f)
+    if (d.get("source_sha") != spread_source_hash() or int(d.get("tile", -1)) != int(tile) or
+            not str(d.get("kernel", "")).startswith(kernel + "<")):
+        return None
+    return d
+
+
+def recorded_issue(tile, kernel):
+    """Instruction issue of the recorded spreading capture (warp instructions per SM per cycle,
+    at most 4 on this GPU), or None if it does not apply."""
     try:
-        with open(os.path.join(ROOT, "profiles", "k_spread_traffic.json")) as f:
-            d = json.load(f)
-        if d.get("source_sha") != spread_source_hash() or int(d.get("tile", -1)) != int(tile):
+        d = recorded_capture(tile, kernel)
+        if d is None:
             return None
         ipc = float(d["warp_inst_per_sm_cycle"])
         return {"bound": "issue", "achieved": ipc, "peak": 4.0,
@@ -576,13 +592,12 @@ def recorded_issue(tile):
         return None
 
 
-def recorded_traffic(tile):
-    """DRAM bytes (read + write) of one k_spread launch on this workload from the committed ncu
-    summary, or None if the spreading sources changed since that capture."""
+def recorded_traffic(tile, kernel):
+    """DRAM bytes (read + write) of one spreading launch on this workload from the committed ncu
+    summary, or None if it does not apply."""
     try:
-        with open(os.path.join(ROOT, "profiles", "k_spread_traffic.json")) as f:
-            d = json.load(f)
-        if d.get("source_sha") != spread_source_hash() or int(d.get("tile", -1)) != int(tile):
+        d = recorded_capture(tile, kernel)
+        if d is None:
             return None
         return float(d["dram_bytes_per_launch"])
     except Exception:
@@ -1000,7 +1015,7 @@ def run_ours(args):
 
     info = plan.info
     G = info.G
-    tensor = plan.tensor_core()
+    kname, kdesc = SPREAD_KERNELS[info.spread_kernel]
     smem_fft = 256 <= G <= 4096 and (G & (G - 1)) == 0
     alg_bytes = 20 * p.M + 8 * G * G              # spreading: 20 B per sample + the grid write
     peak, peak_kind = load_peaks()
@@ -1040,18 +1055,17 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": headline_config(world),
             "plan": {"tile": info.tile, "layout": info.layout, "entries": info.entries,
-                     "spread_kernel": "tensor-core (k_spread_mma)" if tensor else
-                                      "register-window (k_spread)",
+                     "spread_kernel": kdesc,
                      "l2_flush_mib": flush_bytes / 2**20},
             "stages_ms": {"spread": sp_ms, "fft": fft_ms, "deapod_crop": dp_ms, "calls": ncalls,
                           "note": ("fft = column pass; deapod_crop = row pass fused with the "
                                    "window division and crop") if smem_fft else "cuFFT + k_deapod_crop"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(info.tile),
-                         "kernel": ("k_spread_mma" if tensor else "k_spread") +
+                         "frac": achieved / peak, "traffic": recorded_traffic(info.tile, kname),
+                         "kernel": kname +
                                    " + k_halo_add (the spreading stage)",
                          "peak_kind": peak_kind,
-                         "issue": recorded_issue(info.tile),
+                         "issue": recorded_issue(info.tile, kname),
                          "alg_bytes_per_launch": alg_bytes},
             "rel_l2_vs_fp64_oracle": rel,
             "per_ping": {"value": p.M / sum(pp), "unit": UNIT,

@@ -234,10 +234,11 @@ ftcg_status_t ftcg_stage_times(ftcg_plan_t plan, float* ms, int32_t* calls);
  * ftcg_plan_batch -- plan n pings. d_lambda, M, N: host arrays of n entries (d_lambda[i] a device
  * M[i] x 2 float64 array, read during the call); sigma, w, opts shared, with the checks of
  * ftcg_plan per ping. opts->tile = 0 or opts->layout = 0 lets the built-in autotuner pick the
- * tile side, layout and spreading kernel of each ping: the pings are grouped by (grid side, w,
- * precision, half-octave bucket of samples per grid cell), and for every group not decided yet
- * each candidate is timed as the batched spreading launch over up to 16 of the group's pings;
- * the fastest is kept for the life of the process. After the tuning (on `stream`), the pings'
+ * tile side, layout and spreading kernel of each ping: a ping's choice is keyed by (grid side, w,
+ * precision, half-octave bucket of samples per grid cell); for the keys not decided yet, each
+ * candidate is timed as the batched spreading launch over up to 16 of their pings (spread over
+ * the batch's range of sizes), and the fastest is kept for all of those keys for the life of the
+ * process. After the tuning (on `stream`), the pings'
  * plans are built by up to four host threads, each on its own stream that waits for `stream`
  * first. A ping whose coordinates are not all finite drops those samples (as ftcg_plan does) and
  * the batch is still built. Synchronises.

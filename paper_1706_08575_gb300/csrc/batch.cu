@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <set>
 #include <mutex>
 #include <new>
 #include <string>
@@ -350,7 +351,7 @@ void release_batch(Batch* b) {
 template <bool VBF, bool ABF>
 ftcg_status_t launch_batch_spread_mma(Batch& b, cudaStream_t s) {
     auto kern = k_spread_batch_mma<VBF, ABF>;
-    const size_t smem = mma::tile_smem_bytes(64);
+    const size_t smem = blk::tile_smem_bytes(64);     // the larger of the two kernels' layouts
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
@@ -804,59 +805,62 @@ ftcg_status_t time_batch_candidate(const Batch& parent, const TuneVal& c,
     return st;
 }
 
-// The batch tuner: the pings are grouped by tuner key (grid side, w, precision, half-octave
-// density bucket and the caller's fixed choices); for every key not decided yet, each candidate
-// (tile side, layout, kernel) is timed as the persistent spreading launch over up to
-// kTuneBatchPings pings of the group, planned for that candidate. Batched timings count what a
-// batch pays per item (per-tile and per-column-bin work) rather than how one small ping's launch
-// fills the GPU, which decides the single-ping tuner. Pings without samples take the first
-// candidate.
+// The batch tuner: one (tile side, layout, kernel) for all pings whose tuner key (grid side, w,
+// precision, half-octave density bucket, the caller's fixed choices) is not decided yet. Each
+// candidate is timed as the persistent spreading launch over a sample of up to kTuneBatchPings of
+// those pings (evenly spaced in the order of decreasing sample count, so that the sample has the
+// batch's mix of sizes), planned for that candidate; the fastest is recorded for every undecided
+// key. Timing the mix, not each key's pings alone, matters: most keys of a batch hold one or two
+// pings, and a launch over so few measures how one small ping fills the GPU rather than what it
+// costs inside the whole batch's launch. Batches without samples take the first candidate.
 constexpr int kTuneBatchPings = 16;
 
 ftcg_status_t tune_batch(const Batch& b, const double* const* d_lambda, const int64_t* M,
                          const int32_t* N, cudaStream_t s) {
-    std::map<TuneKey, std::vector<int>> groups;
-    for (int i = 0; i < b.n; ++i) {
-        const int G = (int)std::llround(b.sigma * N[i]);
-        groups[batch_key(b, M[i], G)].push_back(i);
-    }
-    const std::vector<TuneVal> cand = tune_candidates(b.w, b.sigma, b.opts);
-    for (const auto& g : groups) {
-        {
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            if (g_tune.count(g.first)) continue;
-        }
-        TuneVal best = cand[0];
-        if (cand.size() > 1 && M[g.second[0]] > 0) {
-            const int size = (int)g.second.size();
-            const int k = std::min(size, kTuneBatchPings);
-            std::vector<const double*> L(k);
-            std::vector<int64_t> m(k);
-            std::vector<int32_t> n(k);
-            int64_t max_m = 1;
-            for (int j = 0; j < k; ++j) {
-                const int i = g.second[(int64_t)j * size / k];
-                L[j] = d_lambda[i];
-                m[j] = M[i];
-                n[j] = N[i];
-                max_m = std::max(max_m, M[i]);
-            }
-            DevBuf zbuf;
-            FTCG_CK(cudaMalloc(&zbuf.p, (size_t)max_m * sizeof(float2)));
-            FTCG_CK(cudaMemsetAsync(zbuf.p, 0, (size_t)max_m * sizeof(float2), s));
-            float best_ms = 1e30f;
-            for (const TuneVal& c : cand) {
-                float ms = 1e30f;
-                FTCG_TRY(time_batch_candidate(b, c, L, m, n, zbuf.p, s, &ms));
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = c;
-                }
-            }
-        }
+    std::set<TuneKey> keys;
+    std::vector<int> todo;
+    {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[g.first] = best;
+        for (int i = 0; i < b.n; ++i) {
+            const TuneKey k = batch_key(b, M[i], (int)std::llround(b.sigma * N[i]));
+            if (g_tune.count(k)) continue;
+            keys.insert(k);
+            if (M[i] > 0) todo.push_back(i);
+        }
     }
+    if (keys.empty()) return FTCG_SUCCESS;
+    const std::vector<TuneVal> cand = tune_candidates(b.w, b.sigma, b.opts);
+    TuneVal best = cand[0];
+    if (cand.size() > 1 && !todo.empty()) {
+        std::stable_sort(todo.begin(), todo.end(), [&](int x, int y) { return M[x] > M[y]; });
+        const int size = (int)todo.size();
+        const int k = std::min(size, kTuneBatchPings);
+        std::vector<const double*> L(k);
+        std::vector<int64_t> m(k);
+        std::vector<int32_t> n(k);
+        int64_t max_m = 1;
+        for (int j = 0; j < k; ++j) {
+            const int i = todo[(int64_t)j * size / k];
+            L[j] = d_lambda[i];
+            m[j] = M[i];
+            n[j] = N[i];
+            max_m = std::max(max_m, M[i]);
+        }
+        DevBuf zbuf;
+        FTCG_CK(cudaMalloc(&zbuf.p, (size_t)max_m * sizeof(float2)));
+        FTCG_CK(cudaMemsetAsync(zbuf.p, 0, (size_t)max_m * sizeof(float2), s));
+        float best_ms = 1e30f;
+        for (const TuneVal& c : cand) {
+            float ms = 1e30f;
+            FTCG_TRY(time_batch_candidate(b, c, L, m, n, zbuf.p, s, &ms));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneKey& k : keys) g_tune.emplace(k, best);
     return FTCG_SUCCESS;
 }
 

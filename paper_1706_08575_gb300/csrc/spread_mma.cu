@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
 template <int T, bool VBF, bool ABF>
 ftcg_status_t run_blk(const Plan& p, const void* vals, float2* grid, cudaStream_t s, int nt) {
     const Binning& b = p.bin;
-    const size_t smem = mma::tile_smem_bytes(T);
+    const size_t smem = blk::tile_smem_bytes(T);
     auto kern = k_spread_blk<T, VBF, ABF>;
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -176,8 +176,8 @@ class Plan:
         return info
 
     def tensor_core(self):
-        """True when the plan spreads with the tensor-core kernel."""
-        return self.info.spread_kernel == SPREAD_TENSOR
+        """True when the plan spreads with one of the tensor-core kernels (column or block)."""
+        return self.info.spread_kernel in (SPREAD_TENSOR, SPREAD_BLOCK)
 
     def close(self):
         if getattr(self, "_h", None):

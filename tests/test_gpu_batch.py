@@ -220,3 +220,27 @@ def test_batch_ping_with_nonfinite_coordinate(F):
             keep[5] = False
         ref = O.adjoint(lam[keep], v[keep].astype(np.complex128), N, 2.0, 8)
         assert O.rel_l2(img, ref) < TOL, k
+
+
+def test_batch_tuner_one_choice_for_the_mix(F, tmp_path):
+    """The batch tuner times its candidates on the batch's mix of pings and records one choice
+    for every key it decides (w = 7 here, a width no other test of this process tunes); the
+    batch built with that choice still matches the oracle."""
+    import json
+    rng = np.random.default_rng(77)
+    cases = []
+    for i, (N, M) in enumerate([(32, 300), (64, 9000), (48, 2500), (96, 30000), (40, 80),
+                                (64, 600), (128, 50000)]):
+        lam, v = sasgen.random_case(7700 + i, M, N, 2.0, 7, spread=1.5 * N)
+        cases.append((lam, v.astype(np.complex64), rng.uniform(0.3, 1.7, M), N))
+    with F.Batch([dev(c[0]) for c in cases], [c[3] for c in cases], 2.0, 7) as b:
+        b.set_weights([dev(c[2]) for c in cases])
+        imgs = [x.cpu().numpy() for x in b.adjoint([dev(c[1]) for c in cases])]
+    path = tmp_path / "tuner.json"
+    F.ftcg.tuner_save(path)
+    ent = [e for e in json.loads(path.read_text())["entries"] if e["batch"] == 1 and e["w"] == 7]
+    assert len({e["bucket"] for e in ent}) >= 3          # several keys, decided together
+    assert len({(e["tile"], e["layout"], e["spread"]) for e in ent}) == 1
+    for (lam, v, a, N), img in zip(cases, imgs):
+        ref = O.adjoint(lam, a.astype(np.float32) * v.astype(np.complex128), N, 2.0, 7)
+        assert O.rel_l2(img, ref) < TOL
