@@ -1,8 +1,9 @@
 // Batched pings: many independent geometries, sample counts and image sides gridded together.
 //
-// Each ping keeps its own binning (plan.cu) and window factors. One persistent spreading launch
-// covers every (ping, tile) work item: CTAs (one per resident slot of the GPU) take items from an
-// atomic counter, heaviest items first, and run the same tile body as the single-ping kernel.
+// Each ping keeps its own binning (plan.cu) and window factors. Persistent spreading launches
+// cover the (ping, tile) work items, one per spreading kernel and tile side present (normally
+// one): CTAs (one per resident slot of the GPU) take items from an atomic counter, heaviest
+// items first, and run the same tile body as the single-ping kernel.
 // The fine grids of pings with the same side G are contiguous, so one batched cuFFT per distinct
 // G follows, then one window-division + crop launch for all pings. The whole sequence is
 // stream-ordered with no host synchronisation and can be captured once in a CUDA graph.
@@ -36,13 +37,16 @@ namespace ftcg {
 
 namespace {
 
+constexpr int kTcGroups = 4;   // tensor-core batch groups: {column, block} x {T = 32, T = 64}
 
-// The persistent tensor-core spreading launch: CTAs take (ping, tile) items of pings planned
-// for the tensor-core kernel from an atomic counter, heaviest first.
-template <bool VBF, bool ABF>
+
+// The persistent tensor-core spreading launches, one per (kernel, tile side) group of pings: CTAs
+// take the group's (ping, tile) items from an atomic counter, heaviest first. BLK selects the
+// block kernel (else the column-bin kernel).
+template <bool BLK, int T, bool VBF, bool ABF>
 __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
-    k_spread_batch_mma(const PingDesc* __restrict__ desc, const int2* __restrict__ items,
-                       int nitems, int* __restrict__ counter, const __grid_constant__ MmaPoly poly) {
+    k_spread_batch_tc(const PingDesc* __restrict__ desc, const int2* __restrict__ items,
+                      int nitems, int* __restrict__ counter, const __grid_constant__ MmaPoly poly) {
     extern __shared__ float smem[];
     __shared__ int s_item;
     for (;;) {
@@ -52,23 +56,13 @@ __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
         const int it = s_item;
         if (it >= nitems) return;
         const int2 pt = items[it];
-        const PingDesc d = desc[pt.x];
-        if (d.blk) {
-            if (d.T == 64)
-                blk::spread_tile<64, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
-                                               d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y,
-                                               smem);
-            else
-                blk::spread_tile<32, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
-                                               d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y,
-                                               smem);
-        } else if (d.T == 64) {
-            mma::spread_tile<64, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
-                                           d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
-        } else {
-            mma::spread_tile<32, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G,
-                                           d.ntx, d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
-        }
+        const PingDesc& d = desc[pt.x];
+        if constexpr (BLK)
+            blk::spread_tile<T, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G, d.ntx,
+                                          d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
+        else
+            mma::spread_tile<T, VBF, ABF>(d.cent, d.chdr, d.tile_chunk, d.vals, d.grid, d.G, d.ntx,
+                                          d.W, poly, d.halo_buf, d.halo_cells, pt.y, smem);
     }
 }
 
@@ -307,12 +301,14 @@ struct Batch {
     std::vector<int> cls_of, slot_of;
     PingDesc* h_desc = nullptr;   // pinned
     PingDesc* d_desc = nullptr;
-    // (ping, tile) work items: the n_mma items of tensor-core pings first, then the others
+    // (ping, tile) work items: the n_mma items of tensor-core pings first, grouped by kernel and
+    // tile side (group k = 2 blk + (T == 64): items [tc_off[k], tc_off[k + 1])), then the others
     int2* d_items = nullptr;
     int nitems = 0, n_mma = 0;
-    int* d_counter = nullptr;     // two counters: tensor-core items, register-window items
+    int tc_off[kTcGroups + 1] = {};
+    int* d_counter = nullptr;     // kTcGroups + 1 counters: the groups', the register-window one
     MmaPoly poly{};               // the window polynomials (every ping has the same w, sigma)
-    int persistent_ctas_mma = 0;
+    int persistent_ctas_tc[kTcGroups] = {};
     unsigned* d_masks = nullptr;  // shared-memory FFT column-block masks of all pings
     int max_N = 0;
     bool any_halo = false;
@@ -348,23 +344,38 @@ void release_batch(Batch* b) {
     delete b;
 }
 
-template <bool VBF, bool ABF>
-ftcg_status_t launch_batch_spread_mma(Batch& b, cudaStream_t s) {
-    auto kern = k_spread_batch_mma<VBF, ABF>;
-    const size_t smem = blk::tile_smem_bytes(64);     // the larger of the two kernels' layouts
+template <bool BLK, int T, bool VBF, bool ABF>
+ftcg_status_t launch_batch_tc_group(Batch& b, int k, cudaStream_t s) {
+    auto kern = k_spread_batch_tc<BLK, T, VBF, ABF>;
+    const size_t smem = BLK ? blk::tile_smem_bytes(T) : mma::tile_smem_bytes(T);
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
-    if (b.persistent_ctas_mma == 0) {
+    if (b.persistent_ctas_tc[k] == 0) {
         int dev = 0, sms = 0, per = 0;
         FTCG_CK(cudaGetDevice(&dev));
         FTCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         FTCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, mma::kThreads, smem));
-        b.persistent_ctas_mma = std::max(1, sms * std::max(1, per));
+        b.persistent_ctas_tc[k] = std::max(1, sms * std::max(1, per));
     }
-    kern<<<b.persistent_ctas_mma, mma::kThreads, smem, s>>>(b.d_desc, b.d_items, b.n_mma,
-                                                            b.d_counter, b.poly);
+    const int n = b.tc_off[k + 1] - b.tc_off[k];
+    kern<<<std::min(b.persistent_ctas_tc[k], n), mma::kThreads, smem, s>>>(
+        b.d_desc, b.d_items + b.tc_off[k], n, b.d_counter + k, b.poly);
     FTCG_CK(cudaGetLastError());
+    return FTCG_SUCCESS;
+}
+
+template <bool VBF, bool ABF>
+ftcg_status_t launch_batch_spread_mma(Batch& b, cudaStream_t s) {
+    for (int k = 0; k < kTcGroups; ++k) {
+        if (b.tc_off[k + 1] == b.tc_off[k]) continue;
+        switch (k) {
+            case 0: FTCG_TRY((launch_batch_tc_group<false, 32, VBF, ABF>(b, k, s))); break;
+            case 1: FTCG_TRY((launch_batch_tc_group<false, 64, VBF, ABF>(b, k, s))); break;
+            case 2: FTCG_TRY((launch_batch_tc_group<true, 32, VBF, ABF>(b, k, s))); break;
+            default: FTCG_TRY((launch_batch_tc_group<true, 64, VBF, ABF>(b, k, s))); break;
+        }
+    }
     return FTCG_SUCCESS;
 }
 
@@ -413,7 +424,7 @@ std::vector<float2> class_twiddles(int G) {
 // The spreading stage of a batch whose descriptors (values included) are on the device: the
 // persistent tensor-core and register-window launches, then the halo fix-up.
 ftcg_status_t batch_spread(Batch& b, bool vbf, cudaStream_t s) {
-    FTCG_CK(cudaMemsetAsync(b.d_counter, 0, 2 * sizeof(int), s));
+    FTCG_CK(cudaMemsetAsync(b.d_counter, 0, (kTcGroups + 1) * sizeof(int), s));
     const bool abf = b.opts.precision == FTCG_PREC_BF16;
     if (b.n_mma > 0) {
         if (vbf && abf) FTCG_TRY((launch_batch_spread_mma<true, true>(b, s)));
@@ -423,7 +434,7 @@ ftcg_status_t batch_spread(Batch& b, bool vbf, cudaStream_t s) {
     }
     if (b.nitems > b.n_mma)
         FTCG_TRY(launch_batch_window(b.d_desc, b.d_items + b.n_mma, b.nitems - b.n_mma,
-                                     b.d_counter + 1, b.w, b.sigma, b.opts.kernel, vbf, abf,
+                                     b.d_counter + kTcGroups, b.w, b.sigma, b.opts.kernel, vbf, abf,
                                      &b.persistent_ctas, s));
     if (b.nitems > 0 && b.any_halo) {
         k_halo_add_batch<<<b.nitems, 256, 0, s>>>(b.d_desc, b.d_items);
@@ -625,7 +636,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
     FTCG_CK(cudaMallocHost(&b.h_desc, b.n * sizeof(PingDesc)));
     FTCG_CK(cudaMalloc(&b.d_desc, b.n * sizeof(PingDesc)));
     struct Item {
-        int cnt, ping, tile;
+        int cnt, ping, tile, grp;   // grp: the tensor-core group (2 blk + (T == 64))
     };
     std::vector<Item> items, items_mma;
     for (int i = 0; i < b.n; ++i) {
@@ -657,22 +668,23 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         if (bn.mma) b.poly = bn.poly;
         b.any_halo = b.any_halo || bn.halo;
         std::vector<Item>& list = bn.mma ? items_mma : items;
+        const int grp = bn.mma ? 2 * (bn.blk ? 1 : 0) + (bn.T == 64 ? 1 : 0) : 0;
         if (c.smem && bn.n_read > 0 && (int)bn.tile_cnt.size() == bn.ntiles &&
             (int)bn.h_order.size() == bn.ntiles) {
             // the shared-memory transforms read only the column blocks that taps reach: the
             // tiles of the pruned launch order (non-empty ones, then empty ones in those columns)
             for (int k = 0; k < bn.n_read; ++k) {
                 const int t = bn.h_order[k];
-                list.push_back({bn.tile_cnt[t], i, t});
+                list.push_back({bn.tile_cnt[t], i, t, grp});
             }
         } else if ((int)bn.tile_cnt.size() == bn.ntiles) {
-            for (int t = 0; t < bn.ntiles; ++t) list.push_back({bn.tile_cnt[t], i, t});
+            for (int t = 0; t < bn.ntiles; ++t) list.push_back({bn.tile_cnt[t], i, t, grp});
         } else {
             std::vector<int> cp((size_t)bn.ntiles * bn.ncb + 1);
             FTCG_CK(cudaMemcpy(cp.data(), bn.colptr, cp.size() * sizeof(int),
                                cudaMemcpyDeviceToHost));
             for (int t = 0; t < bn.ntiles; ++t)
-                list.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t});
+                list.push_back({cp[(size_t)(t + 1) * bn.ncb] - cp[(size_t)t * bn.ncb], i, t, grp});
         }
     }
     // shared-memory FFT classes: per ping the column blocks that taps reach (items of the column
@@ -729,8 +741,13 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
     }
     auto heavy_first = [](const Item& x, const Item& y) { return x.cnt > y.cnt; };
     std::stable_sort(items.begin(), items.end(), heavy_first);
-    std::stable_sort(items_mma.begin(), items_mma.end(), heavy_first);
+    std::stable_sort(items_mma.begin(), items_mma.end(), [](const Item& x, const Item& y) {
+        return x.grp != y.grp ? x.grp < y.grp : x.cnt > y.cnt;
+    });
     b.n_mma = (int)items_mma.size();
+    for (int k = 0; k <= kTcGroups; ++k) b.tc_off[k] = 0;
+    for (const Item& x : items_mma) ++b.tc_off[x.grp + 1];
+    for (int k = 0; k < kTcGroups; ++k) b.tc_off[k + 1] += b.tc_off[k];
     b.nitems = (int)(items_mma.size() + items.size());
     std::vector<int2> it2;
     it2.reserve(b.nitems);
@@ -739,7 +756,7 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
     FTCG_CK(cudaMalloc(&b.d_items, std::max<size_t>(1, it2.size()) * sizeof(int2)));
     if (!it2.empty())
         FTCG_CK(cudaMemcpy(b.d_items, it2.data(), it2.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    FTCG_CK(cudaMalloc(&b.d_counter, 2 * sizeof(int)));
+    FTCG_CK(cudaMalloc(&b.d_counter, (kTcGroups + 1) * sizeof(int)));
     b.device_bytes += (int64_t)(it2.size() * sizeof(int2) + b.n * sizeof(PingDesc));
     return FTCG_SUCCESS;
 }

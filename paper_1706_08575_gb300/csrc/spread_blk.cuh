@@ -32,10 +32,37 @@ using mma::StagedSlot;
 using mma::kStageChunks;
 using mma::kStageSlots;
 
+// Raw chunk slots in flight per warp: two batches of kStageSlots entries (16 bytes) and of
+// kStageChunks headers, filled by cp.async one batch ahead of their staging.
+constexpr int kRawStages = 2;
+
 // Dynamic shared memory of one tile: the column kernel's (accumulator planes, staging buffers),
-// then the tap polynomials (8 x 8 floats).
+// then the tap polynomials (8 x 8 floats), then each warp's raw entries and headers.
 __host__ __device__ constexpr size_t tile_smem_bytes(int T) {
-    return mma::tile_smem_bytes(T) + (size_t)kMmaMaxW * (kMmaDeg + 1) * sizeof(float);
+    return mma::tile_smem_bytes(T) + (size_t)kMmaMaxW * (kMmaDeg + 1) * sizeof(float) +
+           (size_t)kWarps * kRawStages * (kStageSlots * sizeof(MmaEntry) +
+                                          kStageChunks * sizeof(uint32_t));
+}
+
+// Asynchronous global -> shared copies (cp.async): 16 bytes, of which the first n come from src
+// and the rest are zero (n = 0 reads nothing); 4 bytes; commit; wait for all of this thread's.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t n) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src)), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Bits of a block chunk slot's packed word: sample index (kSampleBits), then the first tap's
@@ -43,23 +70,20 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int T) {
 constexpr int kOffXShift = kSampleBits;
 constexpr int kOffYShift = kSampleBits + 3;
 
-// Load slot i of the chunk array (a padding slot, or an index past the warp's range, gives
-// c = 0): its offsets, weighted value, and its first tap's place in the block as
-// q = 4 offx | (4 offy) << 16, so that (lane + 32) * 0x10001 - q holds lane - 4 offx + 32 in its
-// low half and lane - 4 offy + 32 in its high half, both in 4..63 (no borrow between the halves).
-template <bool VBF, bool ABF>
-__device__ __forceinline__ void load_block_slot(const MmaEntry* __restrict__ cent,
-                                                const void* __restrict__ vals, int64_t i,
-                                                int64_t end, StagedSlot& out, uint32_t& q) {
-    const bool live = i < end;
-    const MmaEntry e = cent[live ? i : end - 1];
-    const float2 v = tile::load_value<VBF>(vals, e.packed & kSampleMask);
-    float al = ABF ? tile::bf16_bits_to_float(e.alpha) : __uint_as_float(e.alpha);
-    al = (live && !(e.packed & kMmaPad)) ? al : 0.0f;
+// The staged form of raw slot e with its value v (index i of the chunk array, end = one past
+// the warp's last slot): its offsets, c = alpha v (zero for a padding slot or past the end), and
+// its first tap's place in the block as q = 4 offx | (4 offy) << 16, so that
+// (lane + 32) * 0x10001 - q holds lane - 4 offx + 32 in its low half and lane - 4 offy + 32 in
+// its high half, both in 4..63 (no borrow between the halves).
+template <bool ABF>
+__device__ __forceinline__ void stage_block_slot(const MmaEntry& e, float2 v, int64_t i,
+                                                 int64_t end, StagedSlot& out, uint32_t& q) {
+    const float al = ABF ? tile::bf16_bits_to_float(e.alpha) : __uint_as_float(e.alpha);
+    const bool live = i < end && !(e.packed & kMmaPad);
     out.sx = e.sx;
     out.sy = e.sy;
-    out.cr = al * v.x;
-    out.ci = al * v.y;
+    out.cr = live ? al * v.x : 0.0f;
+    out.ci = live ? al * v.y : 0.0f;
     q = (((e.packed >> kOffXShift) & 7u) << 2) | (((e.packed >> kOffYShift) & 7u) << 18);
 }
 
@@ -136,28 +160,53 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
     uint32_t* st_hdr = reinterpret_cast<uint32_t*>(reinterpret_cast<StagedSlot*>(smem + 2 * PR * LD) +
                                                    kWarps * kStageSlots) +
                        kWarps * kStageSlots + warp * kStageChunks;
+    // then, after the tap polynomials, each warp's raw slots and headers (kRawStages batches)
+    MmaEntry* raw_all = reinterpret_cast<MmaEntry*>(s_cf + kMmaMaxW * (kMmaDeg + 1));
+    MmaEntry* raw = raw_all + warp * kRawStages * kStageSlots;
+    uint32_t* raw_hdr = reinterpret_cast<uint32_t*>(raw_all + kWarps * kRawStages * kStageSlots) +
+                        warp * kRawStages * kStageChunks;
     if (ca < cb) {
-        // each lane loads one slot of the next kStageChunks chunks; the registers hold the next
-        // batch while the current one is computed from shared memory
+        // batch j: chunks ca + 4j .. ca + 4j + 3, one slot per lane. Its raw slots and headers
+        // are copied by cp.async two batches ahead; the value gather of batch j + 1 is issued
+        // before batch j is computed and staged after it, so that after the first batch neither
+        // load is waited for.
         const int64_t send = (int64_t)cb * kMmaChunk;
-        StagedSlot nxt;
-        uint32_t npos;
-        uint32_t nhdr = 0;
-        load_block_slot<VBF, ABF>(cent, vals, (int64_t)ca * kMmaChunk + lane, send, nxt, npos);
-        if (lane < kStageChunks) nhdr = chdr[min(ca + lane, cb - 1)];
-        for (int cbase = ca; cbase < cb; cbase += kStageChunks) {
-            __syncwarp();
-            st_slot[lane] = nxt;
-            st_pos[lane] = npos;
-            if (lane < kStageChunks) st_hdr[lane] = nhdr;
-            __syncwarp();
-            if (cbase + kStageChunks < cb) {
-                load_block_slot<VBF, ABF>(cent, vals,
-                                    (int64_t)(cbase + kStageChunks) * kMmaChunk + lane, send, nxt,
-                                    npos);
-                if (lane < kStageChunks) nhdr = chdr[min(cbase + kStageChunks + lane, cb - 1)];
+        const int nb = (cb - ca + kStageChunks - 1) / kStageChunks;
+        auto issue = [&](int j) {                // batch j's copies into ring stage j & 1
+            const int64_t i = ((int64_t)ca + kStageChunks * j) * kMmaChunk + lane;
+            cp_async16(raw + (j & 1) * kStageSlots + lane, cent + min(i, send - 1),
+                       i < send ? 16u : 0u);
+            if (lane < kStageChunks)
+                cp_async4(raw_hdr + (j & 1) * kStageChunks + lane,
+                          chdr + min(ca + kStageChunks * j + lane, cb - 1));
+            cp_async_commit();
+        };
+        auto stage = [&](int j, float2 v) {      // batch j from its ring stage, with values v
+            const MmaEntry e = raw[(j & 1) * kStageSlots + lane];
+            StagedSlot sl;
+            uint32_t q;
+            stage_block_slot<ABF>(e, v, ((int64_t)ca + kStageChunks * j) * kMmaChunk + lane, send,
+                                  sl, q);
+            st_slot[lane] = sl;
+            st_pos[lane] = q;
+            if (lane < kStageChunks) st_hdr[lane] = raw_hdr[(j & 1) * kStageChunks + lane];
+        };
+        issue(0);
+        if (nb > 1) issue(1);
+        cp_async_wait_all();
+        __syncwarp();
+        stage(0, tile::load_value<VBF>(vals, raw[lane].packed & kSampleMask));
+        __syncwarp();
+        for (int j = 0; j < nb; ++j) {
+            const bool more = j + 1 < nb;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (more) {
+                cp_async_wait_all();               // batch j + 1's raw slots (this lane's)
+                v = tile::load_value<VBF>(
+                    vals, raw[((j + 1) & 1) * kStageSlots + lane].packed & kSampleMask);
+                if (j + 2 < nb) issue(j + 2);      // into batch j's stage, staged already
             }
-            const int nk = min(kStageChunks, cb - cbase);
+            const int nk = min(kStageChunks, cb - (ca + kStageChunks * j));
 #pragma unroll mma::kBatchUnroll
             for (int k = 0; k < kStageChunks; ++k) {
                 if (k >= nk) break;
@@ -211,6 +260,11 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                 mma::mma_tf32(i0, al0, a1l, al2, a2l, j1h & m1, j2h & m2);
                 mma::mma_tf32(r1, al0, a1l, al2, a2l, r1h, r2h);
                 mma::mma_tf32(i1, al0, a1l, al2, a2l, j1h, j2h);
+            }
+            if (more) {
+                __syncwarp();                      // every lane is done with batch j's slots
+                stage(j + 1, v);
+                __syncwarp();
             }
         }
         flush();
