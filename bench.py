@@ -900,6 +900,8 @@ def run_ours(args):
     barrier(device)
     import paper_1706_08575_gb300 as F
     import sasgen
+    if args.tuner_load and os.path.exists(args.tuner_load):
+        F.ftcg.tuner_load(args.tuner_load)      # the autotuner's choices of an earlier process
 
     p = rank_ping(rank)
     v_np = sasgen.values_for(p, device=device).astype(np.complex64)
@@ -1143,6 +1145,11 @@ def main(argv=None):
                     default=None,
                     help="run one part alone for profiling (prints its own line, not the headline)")
     ap.add_argument("--batch-pings", type=int, default=512)
+    ap.add_argument("--tuner-load", default=None,
+                    help="load the autotuner's choices from this file first (ftcg_tuner_load), "
+                         "e.g. to profile the launches an unprofiled run chose")
+    ap.add_argument("--tuner-save", default=None,
+                    help="write the autotuner's choices to this file at the end (ftcg_tuner_save)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
@@ -1152,6 +1159,9 @@ def main(argv=None):
         import torch
         import __graft_entry__ as ge
         ge.build()
+        if args.tuner_load and os.path.exists(args.tuner_load):
+            import paper_1706_08575_gb300 as F
+            F.ftcg.tuner_load(args.tuner_load)
         print(json.dumps({"batch": batch_full_extra(torch.device("cuda", 0),
                                                     n_pings=args.batch_pings,
                                                     reps=args.steps)}), flush=True)
@@ -1167,6 +1177,9 @@ def main(argv=None):
         run_reference(args)
     else:
         run_ours(args)
+    if args.tuner_save and args.impl == "ours" and dist_env()[0] == 0:
+        import paper_1706_08575_gb300 as F
+        F.ftcg.tuner_save(args.tuner_save)
 
 
 if __name__ == "__main__":
