@@ -22,6 +22,12 @@
 // are added to the tile's shared accumulator with shared-memory atomics, and the tile is stored
 // once (coalesced) with its halo strips, exactly as the register-window kernel does.
 //
+// The block kernel (FTCG_SPREAD_BLOCK; tile body in spread_blk.cuh) groups the samples by the
+// 8 x 8 block of cells their first taps lie in instead of by column bin: a chunk of up to 8 of
+// them spreads into the 16 x 16 cells from the block's origin, two column halves of 16 x 8, and
+// the window stays put for all of the block's chunks (no shifts, one flush per block and warp).
+// Its chunks are built here as well (k_blk_count, k_blk_emit).
+//
 // The window values are evaluated as per-tap degree-7 polynomials in s (the sample's offset
 // within the tap's unit interval), fitted on the host by Chebyshev interpolation of the FP64
 // window; the fit error is checked when the plan is built (the path is used only when it is
