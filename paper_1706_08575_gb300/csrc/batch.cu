@@ -69,10 +69,9 @@ __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
 // the overflow strips of every halo-layout (ping, tile) item, after the spreading launch
 __global__ void __launch_bounds__(256)
     k_halo_add_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items) {
-    const int2 pt = items[blockIdx.x];
+    const int2 pt = items[blockIdx.x];        // a non-empty tile of a halo-layout ping
     const PingDesc d = desc[pt.x];
-    if (!d.halo) return;
-    tile::halo_add_tile(d.halo_buf, d.halo_cells, d.colptr, d.ncb, d.grid, d.G, d.T, d.W, d.ntx,
+    tile::halo_add_tile(d.halo_buf, d.halo_cells, nullptr, d.ncb, d.grid, d.G, d.T, d.W, d.ntx,
                         pt.y);
 }
 
@@ -307,6 +306,8 @@ struct Batch {
     int nitems = 0, n_mma = 0;
     int tc_off[kTcGroups + 1] = {};
     int* d_counter = nullptr;     // kTcGroups + 1 counters: the groups', the register-window one
+    int2* d_halo_items = nullptr; // the non-empty (ping, tile) items of halo-layout pings
+    int n_halo = 0;
     MmaPoly poly{};               // the window polynomials (every ping has the same w, sigma)
     int persistent_ctas_tc[kTcGroups] = {};
     unsigned* d_masks = nullptr;  // shared-memory FFT column-block masks of all pings
@@ -338,6 +339,7 @@ void release_batch(Batch* b) {
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_halo_items) cudaFree(b->d_halo_items);
     if (b->d_masks) cudaFree(b->d_masks);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
@@ -436,8 +438,8 @@ ftcg_status_t batch_spread(Batch& b, bool vbf, cudaStream_t s) {
         FTCG_TRY(launch_batch_window(b.d_desc, b.d_items + b.n_mma, b.nitems - b.n_mma,
                                      b.d_counter + kTcGroups, b.w, b.sigma, b.opts.kernel, vbf, abf,
                                      &b.persistent_ctas, s));
-    if (b.nitems > 0 && b.any_halo) {
-        k_halo_add_batch<<<b.nitems, 256, 0, s>>>(b.d_desc, b.d_items);
+    if (b.n_halo > 0) {
+        k_halo_add_batch<<<b.n_halo, 256, 0, s>>>(b.d_desc, b.d_halo_items);
         FTCG_CK(cudaGetLastError());
     }
     return FTCG_SUCCESS;
@@ -757,6 +759,17 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
     if (!it2.empty())
         FTCG_CK(cudaMemcpy(b.d_items, it2.data(), it2.size() * sizeof(int2), cudaMemcpyHostToDevice));
     FTCG_CK(cudaMalloc(&b.d_counter, (kTcGroups + 1) * sizeof(int)));
+    std::vector<int2> halo_it;      // the fix-up's items: non-empty tiles of halo-layout pings
+    for (const std::vector<Item>* list : {&items_mma, &items})
+        for (const Item& x : *list)
+            if (x.cnt > 0 && b.pings[x.ping]->bin.halo) halo_it.push_back(make_int2(x.ping, x.tile));
+    b.n_halo = (int)halo_it.size();
+    if (b.n_halo > 0) {
+        FTCG_CK(cudaMalloc(&b.d_halo_items, halo_it.size() * sizeof(int2)));
+        FTCG_CK(cudaMemcpy(b.d_halo_items, halo_it.data(), halo_it.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice));
+        b.device_bytes += (int64_t)(halo_it.size() * sizeof(int2));
+    }
     b.device_bytes += (int64_t)(it2.size() * sizeof(int2) + b.n * sizeof(PingDesc));
     return FTCG_SUCCESS;
 }

@@ -134,8 +134,9 @@ int blocks_for(int64_t n, int threads) {
 ftcg_status_t launch_halo_add(const Plan& p, float2* grid, cudaStream_t s) {
     const Binning& b = p.bin;
     if (!b.halo || b.n_nonempty == 0) return FTCG_SUCCESS;
+    // the first n_nonempty tiles of the launch order are the non-empty ones: no emptiness test
     FTCG_CK(launch_pdl(k_halo_add, dim3(b.n_nonempty), dim3(256), 0, s,
-                       (const float2*)b.halo_buf, b.halo_cells, (const int*)b.colptr,
+                       (const float2*)b.halo_buf, b.halo_cells, (const int*)nullptr,
                        (const int*)b.tile_order, b.ncb, grid, b.G, b.T, b.W, b.ntx));
     return FTCG_SUCCESS;
 }

@@ -301,12 +301,14 @@ __device__ __forceinline__ void spread_tile(const Entry* __restrict__ ent,
 
 // Adds the overflow strips of a halo-layout tile to the grid cells they belong to (wrapping mod
 // G). Cells receive at most three such additions (left, upper and upper-left tile), so float
-// atomics are cheap; the tiles' own cells were stored by the spreading kernel before.
+// atomics are cheap; the tiles' own cells were stored by the spreading kernel before. colptr:
+// the binning's, to skip an empty tile (it wrote no strips); nullptr when the caller launches
+// non-empty tiles only.
 __device__ __forceinline__ void halo_add_tile(const float2* __restrict__ halo_buf, int halo_cells,
                                               const int* __restrict__ colptr, int ncb,
                                               float2* __restrict__ grid, int G, int T, int W,
                                               int ntx, int tile) {
-    if (colptr[(int64_t)(tile + 1) * ncb] == colptr[(int64_t)tile * ncb]) return;   // empty
+    if (colptr && colptr[(int64_t)(tile + 1) * ncb] == colptr[(int64_t)tile * ncb]) return;
     const int tyi = tile / ntx, txi = tile - tyi * ntx;
     const int X0 = txi * T, Y0 = tyi * T;
     const int Tw = min(T, G - X0), Th = min(T, G - Y0);
