@@ -70,16 +70,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
 constexpr int kOffXShift = kSampleBits;
 constexpr int kOffYShift = kSampleBits + 3;
 
-// The staged form of raw slot e with its value v (index i of the chunk array, end = one past
-// the warp's last slot): its offsets, c = alpha v (zero for a padding slot or past the end), and
+// The staged form of raw slot e with its value v (in_range: the slot lies within the warp's
+// chunks): its offsets, c = alpha v (zero for a padding slot or past the end), and
 // its first tap's place in the block as q = 4 offx | (4 offy) << 16, so that
 // (lane + 32) * 0x10001 - q holds lane - 4 offx + 32 in its low half and lane - 4 offy + 32 in
 // its high half, both in 4..63 (no borrow between the halves).
 template <bool ABF>
-__device__ __forceinline__ void stage_block_slot(const MmaEntry& e, float2 v, int64_t i,
-                                                 int64_t end, StagedSlot& out, uint32_t& q) {
+__device__ __forceinline__ void stage_block_slot(const MmaEntry& e, float2 v, bool in_range,
+                                                 StagedSlot& out, uint32_t& q) {
     const float al = ABF ? tile::bf16_bits_to_float(e.alpha) : __uint_as_float(e.alpha);
-    const bool live = i < end && !(e.packed & kMmaPad);
+    const bool live = in_range && !(e.packed & kMmaPad);
     out.sx = e.sx;
     out.sy = e.sy;
     out.cr = live ? al * v.x : 0.0f;
@@ -170,23 +170,26 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
         // are copied by cp.async two batches ahead; the value gather of batch j + 1 is issued
         // before batch j is computed and staged after it, so that after the first batch neither
         // load is waited for.
-        const int64_t send = (int64_t)cb * kMmaChunk;
+        // this lane's slot of batch 0, and how many of the warp's slots remain from it (batch j's
+        // slot is live while 32 j < left; past the end the copy reads nothing and fills zeros)
+        const MmaEntry* src = cent + (int64_t)ca * kMmaChunk + lane;
+        const int left = (cb - ca) * kMmaChunk - lane;
+        const uint32_t* hsrc = chdr + ca;
         const int nb = (cb - ca + kStageChunks - 1) / kStageChunks;
         auto issue = [&](int j) {                // batch j's copies into ring stage j & 1
-            const int64_t i = ((int64_t)ca + kStageChunks * j) * kMmaChunk + lane;
-            cp_async16(raw + (j & 1) * kStageSlots + lane, cent + min(i, send - 1),
-                       i < send ? 16u : 0u);
+            const int o = kStageSlots * j;
+            cp_async16(raw + (j & 1) * kStageSlots + lane, src + min(o, left - 1),
+                       o < left ? 16u : 0u);
             if (lane < kStageChunks)
                 cp_async4(raw_hdr + (j & 1) * kStageChunks + lane,
-                          chdr + min(ca + kStageChunks * j + lane, cb - 1));
+                          hsrc + min(kStageChunks * j + lane, cb - ca - 1));
             cp_async_commit();
         };
         auto stage = [&](int j, float2 v) {      // batch j from its ring stage, with values v
             const MmaEntry e = raw[(j & 1) * kStageSlots + lane];
             StagedSlot sl;
             uint32_t q;
-            stage_block_slot<ABF>(e, v, ((int64_t)ca + kStageChunks * j) * kMmaChunk + lane, send,
-                                  sl, q);
+            stage_block_slot<ABF>(e, v, kStageSlots * j < left, sl, q);
             st_slot[lane] = sl;
             st_pos[lane] = q;
             if (lane < kStageChunks) st_hdr[lane] = raw_hdr[(j & 1) * kStageChunks + lane];
