@@ -88,3 +88,32 @@ def test_noalloc_at_the_size_limit(F):
     torch.cuda.synchronize()
     assert rel_l2(out.cpu().numpy(), ref) < TOL
 
+
+
+def test_noalloc_captured_in_cuda_graph(F):
+    """The entry point's main use: a call captured in a CUDA graph (after one warm call) and
+    replayed with new contents of the same value buffer; each replay against the plan-based
+    adjoint of those values."""
+    import torch
+    p = sasgen.tiny()
+    lam = torch.from_numpy(p.lam).cuda()
+    rng = np.random.default_rng(11)
+    alpha = torch.from_numpy(rng.uniform(0.3, 1.7, p.M)).cuda()
+    v = torch.zeros(p.M, dtype=torch.complex64, device="cuda")
+    out = torch.empty((p.N, p.N), dtype=torch.complex64, device="cuda")
+    assert _noalloc(F, lam, v, alpha, p.N, p.sigma, p.w, out) == 0        # warm call
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        st = _noalloc(F, lam, v, alpha, p.N, p.sigma, p.w, out)
+    assert st == 0
+    with F.Plan(lam, p.N, p.sigma, p.w) as plan:
+        plan.set_weights(alpha)
+        for seed in (1, 2):
+            r = np.random.default_rng(seed)
+            x = (r.standard_normal(p.M) + 1j * r.standard_normal(p.M)).astype(np.complex64)
+            v.copy_(torch.from_numpy(x))
+            g.replay()
+            torch.cuda.synchronize()
+            ref = plan.adjoint(torch.from_numpy(x).cuda()).cpu().numpy()
+            assert rel_l2(out.cpu().numpy(), ref) < TOL
