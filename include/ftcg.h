@@ -93,8 +93,18 @@ typedef struct {
     int32_t weight_width;  /* window width of the FP64 weight construction: 0 = 12, else 4..16 */
     int32_t layout;        /* FTCG_LAYOUT_AUTO (default), _DUPLICATE or _HALO                  */
     int32_t spread_kernel; /* FTCG_SPREAD_AUTO (default), _WINDOW, _TENSOR or _BLOCK            */
-    int32_t reserved[2];   /* must be zero                                                      */
+    int32_t deterministic; /* 1: adjoints bitwise reproducible (see below); 0 (default): fastest */
+    int32_t reserved;      /* must be zero                                                      */
 } ftcg_opts_t;
+/* opts.deterministic = 1 fixes every summation order of the spreading, for debugging and
+ * regression tests: the plan orders the samples of each first-tap cell by sample index, one
+ * warp per tile accumulates its block chunks in plan order (the block tensor-core kernel, halo
+ * layout, T = 32 unless opts.tile gives 64), and the overflow strips are added by one thread per
+ * cell in a fixed order (left, upper-left, upper neighbour) instead of by atomics. Two plans
+ * built from the same inputs then give bitwise equal adjoints (one warp per tile: slower than the
+ * default). Needs what the block kernel needs (w <= 8, see FTCG_SPREAD_BLOCK) and G = sigma N a
+ * multiple of the tile side; FTCG_ERR_NOT_SUPPORTED otherwise, and for batches. The FP64
+ * weights of ftcg_weights are not covered (their first step sums with atomics). */
 
 typedef struct {
     int64_t M;             /* samples                                                           */

@@ -86,6 +86,7 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
     FTCG_CK(pool_malloc(&p->deapod2, (size_t)p->N * sizeof(float2), s));
     bytes += (int64_t)p->N * sizeof(float2);
     FTCG_TRY(split_factors(p->deapod, p->deapod2, p->N, s));
+    p->bin.det = p->opts.deterministic != 0;
     FTCG_TRY(build_binning(p->bin, p->lambda, M, p->sigma, p->G, p->opts.tile, p->w,
                            p->opts.layout == FTCG_LAYOUT_HALO, p->status, p->samp, s, &bytes));
     if (p->bin.halo && p->opts.spread_kernel != FTCG_SPREAD_WINDOW && p->w <= kMmaMaxW) {
@@ -124,8 +125,27 @@ ftcg_status_t validate_plan_args(int64_t M, int32_t N, double sigma, int32_t w, 
         return invalid("ftcg_plan: sigma * N must be an even integer");
     if (G < 2 * w) return invalid("ftcg_plan: the grid must hold at least two windows (G >= 2 w)");
     ftcg_opts_t& o = *po;
-    for (int i = 0; i < 2; ++i)
-        if (o.reserved[i] != 0) return invalid("ftcg_plan: opts.reserved must be zero");
+    if (o.reserved != 0) return invalid("ftcg_plan: opts.reserved must be zero");
+    if (o.deterministic != 0 && o.deterministic != 1)
+        return invalid("ftcg_plan: opts.deterministic must be 0 or 1");
+    if (o.deterministic) {
+        // one fixed configuration: the block kernel, halo layout, T = 32 (or the given 64)
+        if (o.layout == FTCG_LAYOUT_DUPLICATE ||
+            (o.spread_kernel != FTCG_SPREAD_AUTO && o.spread_kernel != FTCG_SPREAD_BLOCK)) {
+            set_error("ftcg_plan: opts.deterministic runs the block kernel in the halo layout");
+            return FTCG_ERR_NOT_SUPPORTED;
+        }
+        o.layout = FTCG_LAYOUT_HALO;
+        o.spread_kernel = FTCG_SPREAD_BLOCK;
+        if (o.tile == 0) o.tile = 32;
+        if (o.tile != 0 && o.tile != 32 && o.tile != 64)
+            return invalid("ftcg_plan: opts.tile must be 0, 32 or 64");
+        if (G % o.tile != 0) {
+            set_error("ftcg_plan: opts.deterministic needs G = sigma N (%lld) to be a multiple "
+                      "of the tile side %d", G, o.tile);
+            return FTCG_ERR_NOT_SUPPORTED;
+        }
+    }
     if (o.layout < FTCG_LAYOUT_AUTO || o.layout > FTCG_LAYOUT_HALO)
         return invalid("ftcg_plan: opts.layout must be 0, 1 or 2");
     if (o.spread_kernel < FTCG_SPREAD_AUTO || o.spread_kernel > FTCG_SPREAD_BLOCK)

@@ -917,6 +917,10 @@ ftcg_status_t ftcg_plan_batch(ftcg_batch_t* out, int32_t n, const double* const*
     }
     ftcg_opts_t o{};
     if (opts) o = *opts;
+    if (o.deterministic) {
+        set_error("ftcg_plan_batch: opts.deterministic is for single plans (ftcg_plan)");
+        return FTCG_ERR_NOT_SUPPORTED;
+    }
     for (int i = 0; i < n; ++i) {
         if (M[i] < 0 || (M[i] > 0 && !d_lambda[i])) {
             set_error("ftcg_plan_batch: ping %d has a bad sample count or NULL coordinates", i);

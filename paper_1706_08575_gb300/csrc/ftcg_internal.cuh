@@ -177,6 +177,11 @@ struct Binning {
     bool halo = false;                  // FTCG_LAYOUT_HALO: one entry per sample + halo strips
     int halo_cells = 0;                 // halo cells per tile
     float2* halo_buf = nullptr;         // ntiles * halo_cells overflow values (halo layout)
+    // opts.deterministic: entries of one first-tap cell in sample order, one warp per tile, the
+    // strips gathered in a fixed order (k_halo_gather, which reads tile_full)
+    bool det = false;
+    unsigned char* tile_full = nullptr; // 1 per non-empty tile (deterministic halo plans)
+    std::vector<unsigned char> h_full;  // host copy
     // Tensor-core spreading (halo layout, w <= 8): each tile's entries regrouped into chunks of 8
     // samples of one column bin whose first-tap rows fit one 16-row window (spread_mma.cu).
     bool mma = false;
@@ -276,6 +281,9 @@ ftcg_status_t launch_spread_mma(const Plan& p, const void* vals, bool vbf, float
 ftcg_status_t launch_set_alpha_mma(const Plan& p, const void* alpha, int dtype, cudaStream_t s);
 // launch a plan's k_halo_add fix-up after a halo-layout spreading kernel (spread.cu)
 ftcg_status_t launch_halo_add(const Plan& p, float2* grid, cudaStream_t s);
+// deterministic plans: the strips gathered per receiving cell in a fixed order (spread.cu) over
+// the first nt tiles of the launch order
+ftcg_status_t launch_halo_gather(const Plan& p, float2* grid, cudaStream_t s, int nt);
 // occ[x] = 1 for every grid column x that some sample's taps reach
 ftcg_status_t column_occupancy(const Plan* p, cudaStream_t s, std::vector<unsigned char>* occ);
 ftcg_status_t build_pruned_fft(Plan* p, cudaStream_t s, int64_t* bytes);

@@ -111,6 +111,30 @@ __global__ void k_bin_count(const double* __restrict__ lam, int64_t M, double sc
     }
 }
 
+// Deterministic plans: the entries of each (tile, column bin, row) key in sample order (the
+// scatter's atomic cursors leave them in arrival order). One thread per key; a key holds the
+// few samples whose first tap is one cell, so an insertion sort. end: the cursors after the
+// scatter (one past each key's last entry), cnt: the key's count.
+__global__ void k_key_sort(const int* __restrict__ cnt, const int* __restrict__ end,
+                           int64_t nkeys, Entry* __restrict__ ent) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nkeys;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int n = cnt[k];
+        if (n < 2) continue;
+        Entry* e = ent + (end[k] - n);
+        for (int i = 1; i < n; ++i) {
+            const Entry x = e[i];
+            const uint32_t xi = x.packed & kSampleMask;
+            int j = i - 1;
+            while (j >= 0 && (e[j].packed & kSampleMask) > xi) {
+                e[j + 1] = e[j];
+                --j;
+            }
+            e[j + 1] = x;
+        }
+    }
+}
+
 __global__ void k_bin_scatter(const double* __restrict__ lam, int64_t M, double scale, int G,
                               int T, int W, int ntx, int ncb, bool halo,
                               int* __restrict__ cursor, Entry* __restrict__ ent) {
@@ -255,7 +279,9 @@ void free_binning(Binning& b) {
     if (b.colptr) cudaFree(b.colptr);
     if (b.tile_order) cudaFree(b.tile_order);
     if (b.halo_buf) cudaFree(b.halo_buf);
+    if (b.tile_full) cudaFree(b.tile_full);
     b.halo_buf = nullptr;
+    b.tile_full = nullptr;
     b.ent = nullptr;
     b.colptr = nullptr;
     b.tile_order = nullptr;
@@ -315,6 +341,13 @@ static ftcg_status_t order_tiles(Binning& b, cudaStream_t s, int64_t* bytes) {
         std::copy(skip.begin(), skip.end(), order.begin() + b.n_nonempty + read.size());
         b.n_read = b.n_nonempty + (int)read.size();
     }
+    if (b.det && b.halo) {
+        b.h_full.resize(b.ntiles);
+        for (int t = 0; t < b.ntiles; ++t) b.h_full[t] = b.tile_cnt[t] > 0 ? 1 : 0;
+        FTCG_CK(pool_malloc(&b.tile_full, b.ntiles, s));
+        *bytes += b.ntiles;
+        FTCG_CK(cudaMemcpyAsync(b.tile_full, b.h_full.data(), b.ntiles, cudaMemcpyHostToDevice, s));
+    }
     FTCG_CK(pool_malloc(&b.tile_order, b.ntiles * sizeof(int), s));
     *bytes += b.ntiles * sizeof(int);
     // the host order stays alive with the binning, so the copy needs no synchronisation here
@@ -366,6 +399,10 @@ ftcg_status_t build_binning(Binning& b, const double* d_lambda, int64_t M, doubl
         k_bin_scatter<<<grid_for(M), kThreads, 0, s>>>(d_lambda, M, scale, G, T, W, b.ntx, b.ncb,
                                                        halo, offs, b.ent);
         FTCG_CK(cudaGetLastError());
+        if (b.det) {
+            k_key_sort<<<grid_for(nkeys), kThreads, 0, s>>>(hist, offs, nkeys, b.ent);
+            FTCG_CK(cudaGetLastError());
+        }
     }
     FTCG_CK(pool_free(hist, s));
     FTCG_CK(pool_free(offs, s));

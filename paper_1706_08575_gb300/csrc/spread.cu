@@ -35,6 +35,55 @@ __global__ void __launch_bounds__(256)
                         tile_order[blockIdx.x]);
 }
 
+// Deterministic plans (every tile full): the overflow strips added without atomics, by one
+// thread per receiving cell in a fixed order. Cell (lx, ly) of tile (tx, ty) takes, when
+// lx < w - 1, the right strip of tile (tx - 1, ty) at row ly and, when also ly < w - 1, that of
+// tile (tx - 1, ty - 1) at row T + ly; then, when ly < w - 1, the bottom strip of tile
+// (tx, ty - 1) (neighbours mod G; only tiles that wrote strips, full[] = 1). One CTA per tile
+// of the spreading launch.
+__global__ void __launch_bounds__(256)
+    k_halo_gather(const float2* __restrict__ halo_buf, int halo_cells,
+                  const unsigned char* __restrict__ full, const int* __restrict__ tile_order,
+                  float2* __restrict__ grid, int G, int T, int W, int ntx) {
+    pdl_wait();                                // the spreading kernel's tiles and strips
+    pdl_allow_next();
+    const int tile = tile_order[blockIdx.x];
+    const int tyi = tile / ntx, txi = tile - tyi * ntx;
+    const int X0 = txi * T, Y0 = tyi * T;
+    const int W1 = W - 1, right = (T + W1) * W1;
+    const int txl = (txi == 0 ? ntx : txi) - 1, tyu = (tyi == 0 ? ntx : tyi) - 1;
+    const int tl = tyi * ntx + txl, tu = tyu * ntx + txi, tul = tyu * ntx + txl;
+    const bool fl = full[tl] != 0, fu = full[tu] != 0, ful = full[tul] != 0;
+    if (!fl && !fu && !ful) return;
+    // the receiving cells: the first w - 1 columns of every row, then the rest of the first
+    // w - 1 rows
+    const int ncol = T * W1, nrow = W1 * (T - W1);
+    for (int k = threadIdx.x; k < ncol + nrow; k += blockDim.x) {
+        int lx, ly;
+        if (k < ncol) {
+            ly = k / W1;
+            lx = k - ly * W1;
+        } else {
+            const int kk = k - ncol;
+            ly = kk / (T - W1);
+            lx = W1 + (kk - ly * (T - W1));
+        }
+        float2* c = grid + (int64_t)(Y0 + ly) * G + X0 + lx;
+        float2 v = *c;
+        auto add = [&](int t, int i) {
+            const float2 a = halo_buf[(int64_t)t * halo_cells + i];
+            v.x += a.x;
+            v.y += a.y;
+        };
+        if (lx < W1) {
+            if (fl) add(tl, ly * W1 + lx);
+            if (ly < W1 && ful) add(tul, (T + ly) * W1 + lx);
+        }
+        if (ly < W1 && fu) add(tu, right + ly * T + lx);
+        *c = v;
+    }
+}
+
 // ---- deapodisation and crop (the body is deapod_crop_block) -------------------------------------
 __global__ void __launch_bounds__(kDeapodThreads)
     k_deapod_crop(const float2* __restrict__ grid, float2* __restrict__ img,
@@ -138,6 +187,15 @@ ftcg_status_t launch_halo_add(const Plan& p, float2* grid, cudaStream_t s) {
     FTCG_CK(launch_pdl(k_halo_add, dim3(b.n_nonempty), dim3(256), 0, s,
                        (const float2*)b.halo_buf, b.halo_cells, (const int*)nullptr,
                        (const int*)b.tile_order, b.ncb, grid, b.G, b.T, b.W, b.ntx));
+    return FTCG_SUCCESS;
+}
+
+ftcg_status_t launch_halo_gather(const Plan& p, float2* grid, cudaStream_t s, int nt) {
+    const Binning& b = p.bin;
+    if (!b.halo || b.n_nonempty == 0) return FTCG_SUCCESS;
+    FTCG_CK(launch_pdl(k_halo_gather, dim3(nt), dim3(256), 0, s, (const float2*)b.halo_buf,
+                       b.halo_cells, (const unsigned char*)b.tile_full, (const int*)b.tile_order,
+                       grid, b.G, b.T, b.W, b.ntx));
     return FTCG_SUCCESS;
 }
 

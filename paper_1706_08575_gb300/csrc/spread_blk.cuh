@@ -88,8 +88,8 @@ __device__ __forceinline__ void stage_block_slot(const MmaEntry& e, float2 v, bo
 }
 
 // One halo-layout tile by the whole CTA (kThreads threads): its block chunks
-// [tile_chunk[tile], tile_chunk[tile + 1]) split into contiguous ranges, one per warp; then the
-// tile and its overflow strips are stored. smem: blk::tile_smem_bytes(T).
+// [tile_chunk[tile], tile_chunk[tile + 1]) split into contiguous ranges, one per warp (or all to
+// warp 0 with one_warp); then the tile and its overflow strips are stored. smem: blk::tile_smem_bytes(T).
 template <int T, bool VBF, bool ABF>
 __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                                             const uint32_t* __restrict__ chdr,
@@ -97,7 +97,8 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
                                             const void* __restrict__ vals,
                                             float2* __restrict__ grid, int G, int ntx, int W,
                                             const MmaPoly& poly, float2* __restrict__ halo_buf,
-                                            int halo_cells, int tile, float* smem) {
+                                            int halo_cells, int tile, float* smem,
+                                            bool one_warp = false) {
     constexpr int PR = mma::acc_rows(T);     // accumulator rows (a window reaches row T + 7)
     constexpr int LD = T + kMmaMaxW;         // row pitch (a window reaches column T + 7)
     float* s_re = smem;
@@ -122,8 +123,10 @@ __device__ __forceinline__ void spread_tile(const MmaEntry* __restrict__ cent,
     const int g = lane >> 2, t = lane & 3;     // MMA fragment row group and column pair
     const uint32_t cf_addr = (uint32_t)__cvta_generic_to_shared(s_cf + 8 * g);   // tap g's
     const int n = c1 - c0;
-    const int ca = c0 + (int)((int64_t)n * warp / kWarps);
-    const int cb = c0 + (int)((int64_t)n * (warp + 1) / kWarps);
+    // each warp a contiguous range of the tile's chunks; one_warp (deterministic plans): warp 0
+    // takes them all, in plan order
+    const int ca = one_warp ? (warp == 0 ? c0 : c1) : c0 + (int)((int64_t)n * warp / kWarps);
+    const int cb = one_warp ? c1 : c0 + (int)((int64_t)n * (warp + 1) / kWarps);
     // D fragments of the two column halves, real and imaginary plane: rows g (d[0], d[1]) and
     // g + 8 (d[2], d[3]), columns 8h + 2t and 8h + 2t + 1; they hold the partial sums S (rows
     // g + 8: S1x, half 1: Sx1)

@@ -317,11 +317,11 @@ __global__ void __launch_bounds__(mma::kThreads, mma::kMinBlocks)
                  const int* __restrict__ tile_chunk, const int* __restrict__ tile_order,
                  const void* __restrict__ vals, float2* __restrict__ grid, int G, int ntx, int W,
                  const __grid_constant__ MmaPoly poly, float2* __restrict__ halo_buf,
-                 int halo_cells) {
+                 int halo_cells, bool one_warp) {
     extern __shared__ float smem[];
     pdl_allow_next();                          // the fix-up may be scheduled during the tail
     blk::spread_tile<T, VBF, ABF>(cent, chdr, tile_chunk, vals, grid, G, ntx, W, poly, halo_buf,
-                                  halo_cells, tile_order[blockIdx.x], smem);
+                                  halo_cells, tile_order[blockIdx.x], smem, one_warp);
 }
 
 template <int T, bool VBF, bool ABF>
@@ -333,9 +333,9 @@ ftcg_status_t run_blk(const Plan& p, const void* vals, float2* grid, cudaStream_
     FTCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
     kern<<<nt, mma::kThreads, smem, s>>>(b.cent, b.chdr, b.tile_chunk, b.tile_order, vals, grid,
-                                       b.G, b.ntx, b.W, b.poly, b.halo_buf, b.halo_cells);
+                                       b.G, b.ntx, b.W, b.poly, b.halo_buf, b.halo_cells, b.det);
     FTCG_CK(cudaGetLastError());
-    return launch_halo_add(p, grid, s);
+    return b.det ? launch_halo_gather(p, grid, s, nt) : launch_halo_add(p, grid, s);
 }
 
 template <bool VBF, bool ABF>

@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("weight_width", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("spread_kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("deterministic", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -150,14 +150,15 @@ class Plan:
 
     def __init__(self, lam, N, sigma=2.0, w=8, tile=0, precision=PREC_FP32, weight_width=0,
                  stream=None, allow_numeric=False, layout=LAYOUT_AUTO, spread_kernel=SPREAD_AUTO,
-                 window=WINDOW_ES):
+                 window=WINDOW_ES, deterministic=False):
         import torch
         if lam.dtype != torch.float64 or lam.dim() != 2 or lam.shape[1] != 2 or not lam.is_cuda:
             raise TypeError("lam must be a CUDA float64 tensor of shape (M, 2)")
         lam = lam.contiguous()
         self.M, self.N, self.sigma, self.w = int(lam.shape[0]), int(N), float(sigma), int(w)
         self.device = lam.device
-        opts = Opts(window, precision, tile, weight_width, layout, spread_kernel)
+        opts = Opts(window, precision, tile, weight_width, layout, spread_kernel,
+                    1 if deterministic else 0)
         h = ctypes.c_void_p()
         st = lib().ftcg_plan(ctypes.byref(h), _ptr(lam), self.M, self.N, self.sigma, self.w,
                              ctypes.byref(opts), _stream(stream))

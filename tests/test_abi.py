@@ -73,8 +73,9 @@ def test_plan_rejects_opts(L):
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 3)) == 1              # layout
     assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 0, 4)) == 1           # spreading kernel
     o = ftcg.Opts(0, 0, 0, 0)
-    o.reserved[1] = 1
+    o.reserved = 1
     assert _plan(L, opts=o) == 1
+    assert _plan(L, opts=ftcg.Opts(0, 0, 0, 0, 0, 0, 2)) == 1        # deterministic is 0 or 1
 
 
 def test_null_plan_calls(L):
