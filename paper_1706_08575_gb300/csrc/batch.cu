@@ -312,7 +312,6 @@ struct Batch {
     int persistent_ctas_tc[kTcGroups] = {};
     unsigned* d_masks = nullptr;  // shared-memory FFT column-block masks of all pings
     int max_N = 0;
-    bool any_halo = false;
     int persistent_ctas = 0;
     int64_t entries = 0, device_bytes = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -668,7 +667,6 @@ ftcg_status_t plan_batch_impl(Batch& b, const double* const* d_lambda, const int
         d.tile_chunk = bn.tile_chunk;
         d.blk = bn.blk ? 1 : 0;
         if (bn.mma) b.poly = bn.poly;
-        b.any_halo = b.any_halo || bn.halo;
         std::vector<Item>& list = bn.mma ? items_mma : items;
         const int grp = bn.mma ? 2 * (bn.blk ? 1 : 0) + (bn.T == 64 ? 1 : 0) : 0;
         if (c.smem && bn.n_read > 0 && (int)bn.tile_cnt.size() == bn.ntiles &&
