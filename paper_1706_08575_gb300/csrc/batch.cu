@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kDeapodThreads) k_deapod_batch(const PingDesc*
 // Shared-memory FFT passes of a size class with power-of-two side L: the column pass over the
 // class's (ping, column block) items, then one CTA per (image row, ping of the class).
 template <int L>
-__global__ void __launch_bounds__(sfft::kColThreads)
+__global__ void __launch_bounds__(sfft::kColThreads, sfft::kColMinBlocks)
     k_fft_cols_batch(const PingDesc* __restrict__ desc, const int2* __restrict__ items,
                      const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];

@@ -28,7 +28,7 @@ namespace {
 using namespace sfft;
 
 template <int L>
-__global__ void __launch_bounds__(kColThreads)
+__global__ void __launch_bounds__(kColThreads, kColMinBlocks)
     k_fft_cols(float2* __restrict__ grid, const int* __restrict__ blocks,
                const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];

@@ -17,10 +17,14 @@ namespace {
 #define FTCG_FFT_COL_BLOCK 4
 #endif
 #ifndef FTCG_FFT_COL_THREADS
-#define FTCG_FFT_COL_THREADS 512
+#define FTCG_FFT_COL_THREADS 256
+#endif
+#ifndef FTCG_FFT_COL_MINB
+#define FTCG_FFT_COL_MINB 1
 #endif
 constexpr int kColBlock = FTCG_FFT_COL_BLOCK;
 constexpr int kColThreads = FTCG_FFT_COL_THREADS;
+constexpr int kColMinBlocks = FTCG_FFT_COL_MINB;   // resident pass-A CTAs per SM to reserve
 
 __host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
@@ -200,6 +204,101 @@ __device__ __forceinline__ void transform(float2* s, const float2* __restrict__ 
     }
 }
 
+// The first or last stage of the column pass with each thread on two adjacent columns of the
+// same butterfly index (columns c0 and c0 + 1, c0 even): the first reads both columns' values of
+// a row with one 16-byte ld4(c0, index), the last writes them with one st4(c0, index, a, b), so
+// the pass issues half the global memory instructions. Otherwise as stage().
+template <int L, int R, int NS, int CB, int NT, int S, bool FIRST, bool LAST, typename LD4,
+          typename ST4>
+__device__ __forceinline__ void stage_paired(float2* s, const float2* __restrict__ tw,
+                                             const LD4& ld4, const ST4& st4) {
+    static_assert(CB % 2 == 0 && (FIRST != LAST), "pairs of columns, first or last stage");
+    constexpr int NJ = L / R;
+    constexpr int HB = CB / 2;
+    constexpr int NP = HB * NJ;                       // (column pair, butterfly) items
+    constexpr int PPT = (NP + NT - 1) / NT;
+    constexpr int IN_STEP = padded(NJ);
+    constexpr int OUT_STEP = NS == 1 ? 1 : padded(NS);
+    static_assert(NJ % 16 == 0, "input stride must keep the padding linear");
+    static_assert(NS == 1 || NS % 16 == 0, "output stride must keep the padding linear");
+    float2 v[PPT][2][R];
+#pragma unroll
+    for (int b = 0; b < PPT; ++b) {
+        const int p = threadIdx.x + b * NT;
+        if (NP % NT == 0 || p < NP) {
+            const int c0 = 2 * (p % HB), j = p / HB;
+            if constexpr (FIRST) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float4 q = ld4(c0, j + r * NJ);
+                    v[b][0][r] = make_float2(q.x, q.y);
+                    v[b][1][r] = make_float2(q.z, q.w);
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2* src = s + (c0 + h) * col_stride(L) + padded(j);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[b][h][r] = src[r * IN_STEP];
+                }
+            }
+            if constexpr (NS > 1) {
+                const int k = j & (NS - 1);
+                const float2* t = tw + tw_offset(L, S) + k;
+                float2 w[R];
+#pragma unroll
+                for (int p2 = 1, i = 0; p2 < R; p2 *= 2, ++i) {
+                    w[p2] = __ldg(t + i * NS);
+#pragma unroll
+                    for (int q = 1; q < p2; ++q) w[p2 + q] = cmul(w[p2], w[q]);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[b][h][r] = cmul(v[b][h][r], w[r]);
+            }
+        }
+    }
+    if constexpr (!FIRST) __syncthreads();            // in place: every read before any write
+#pragma unroll
+    for (int b = 0; b < PPT; ++b) {
+        const int p = threadIdx.x + b * NT;
+        if (NP % NT == 0 || p < NP) {
+            const int c0 = 2 * (p % HB), j = p / HB;
+            const int k = j & (NS - 1);
+            dft<R>(v[b][0]);
+            dft<R>(v[b][1]);
+            if constexpr (LAST) {
+#pragma unroll
+                for (int q = 0; q < R; ++q) st4(c0, (j - k) * R + k + q * NS, v[b][0][q], v[b][1][q]);
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float2* dst = s + (c0 + h) * col_stride(L) + padded((j - k) * R + k);
+#pragma unroll
+                    for (int q = 0; q < R; ++q) dst[q * OUT_STEP] = v[b][h][q];
+                }
+            }
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+}
+
+// The column pass's sequence: paired first and last stages, stage() between them.
+template <int L, int CB, int NT, typename LD4, typename ST4, int S = 0, int NS = 1>
+__device__ __forceinline__ void transform_cols(float2* s, const float2* __restrict__ tw,
+                                               const LD4& ld4, const ST4& st4) {
+    if constexpr (S < num_stages(L)) {
+        constexpr int R = stage_radix(L, S);
+        constexpr bool first = S == 0, last = S + 1 == num_stages(L);
+        if constexpr (first || last)
+            stage_paired<L, R, NS, CB, NT, S, first, last>(s, tw, ld4, st4);
+        else
+            stage<L, R, NS, CB, NT, S, false, false>(s, tw, ld4, st4);
+        transform_cols<L, CB, NT, LD4, ST4, S + 1, NS * R>(s, tw, ld4, st4);
+    }
+}
+
 #ifndef FTCG_FFT_ROW_DIV
 #define FTCG_FFT_ROW_DIV 16
 #endif
@@ -209,15 +308,21 @@ __host__ __device__ constexpr int row_threads(int L) {
 }
 
 // pass A body: transform along y the kColBlock columns x0 .. x0 + kColBlock - 1 of the L x L grid,
-// in place: the first stage reads the columns from the grid, the last writes them back (each
-// warp access covers kColBlock adjacent cells of consecutive rows); the stages between exchange
-// through shared memory (sm: kColBlock * col_stride(L) elements).
+// in place: the first stage reads the columns from the grid, the last writes them back (a thread
+// takes two adjacent columns of a row per 16-byte access, a warp kColBlock columns of
+// 32 / (kColBlock / 2) consecutive rows); the stages between exchange through shared memory (sm: kColBlock *
+// col_stride(L) elements).
 template <int L>
 __device__ __forceinline__ void cols_body(float2* __restrict__ grid, int x0,
                                           const float2* __restrict__ tw, float2* sm) {
-    auto ld = [&](int c, int y) { return grid[(int64_t)y * L + x0 + c]; };
-    auto st = [&](int c, int y, float2 v) { grid[(int64_t)y * L + x0 + c] = v; };
-    transform<L, kColBlock, kColThreads>(sm, tw, ld, st);
+    // two adjacent cells per access (x0 is a multiple of kColBlock, c0 even: 16-byte aligned)
+    auto ld4 = [&](int c, int y) {
+        return *reinterpret_cast<const float4*>(grid + (int64_t)y * L + x0 + c);
+    };
+    auto st4 = [&](int c, int y, float2 a, float2 b) {
+        *reinterpret_cast<float4*>(grid + (int64_t)y * L + x0 + c) = make_float4(a.x, a.y, b.x, b.y);
+    };
+    transform_cols<L, kColBlock, kColThreads>(sm, tw, ld4, st4);
 }
 
 // pass B body: image row iy from grid row (iy - N/2) mod L, transformed along x; the first stage
