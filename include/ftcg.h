@@ -68,7 +68,7 @@ enum { FTCG_PREC_FP32 = 0, FTCG_PREC_BF16 = 1 };
 enum { FTCG_LAYOUT_AUTO = 0, FTCG_LAYOUT_DUPLICATE = 1, FTCG_LAYOUT_HALO = 2 };
 /* Which spreading kernel a plan uses (same result within the FP32 bound):
  *   AUTO:    where the autotuner runs (tile side or layout left to it), it times the kernels
- *            that apply and keeps the faster; with the tile side and layout given, the
+ *            that apply and keeps the faster; with the tile side and layout given, the block
  *            tensor-core kernel where it applies, otherwise the register-window kernel.
  *   WINDOW:  the register-window kernel (FP32 multiply-adds into a rolling window of rows).
  *   TENSOR:  the tensor-core kernel (per column bin, 8 samples x a 16-row window per

@@ -92,8 +92,9 @@ ftcg_status_t make_plan(Plan* p, const double* d_lambda, cudaStream_t s, bool ow
     if (p->bin.halo && p->opts.spread_kernel != FTCG_SPREAD_WINDOW && p->w <= kMmaMaxW) {
         double err = 0;
         if (mma_window_poly(p->w, p->win.beta, p->win.kind, &p->bin.poly, &err))
+            // AUTO (tile side and layout given, so no tuner): the block kernel, the faster one
             FTCG_TRY(build_chunks(p->bin, s, &bytes,
-                                  p->opts.spread_kernel == FTCG_SPREAD_BLOCK));
+                                  p->opts.spread_kernel != FTCG_SPREAD_TENSOR));
     }
     if (own_grid) {
         FTCG_CK(pool_malloc(&p->grid, (size_t)p->G * p->G * sizeof(float2), s));
